@@ -1,0 +1,493 @@
+"""Plain FP64 CPU oracle for sp-DBA (spectral dynamic block activation).
+
+TEST INFRASTRUCTURE ONLY: used by tests/, by the smoke check and by the
+benchmark's CPU-baseline and reference legs.  The CUDA path never imports it.
+
+Every function follows the paper's description step by step, in FP64, with
+numpy for elementwise arithmetic and the oracle's own C FFT
+(oracle_fft.c) for transforms.  Nothing is fused or reordered beyond what the
+cited passage states.
+
+Parity status of each piece (what pins it, see tests/test_oracle_*.py):
+  fftn / ifftn ................ brute-force DFT, Parseval, round trip
+  ch_regular_step ............. single-mode closed-form growth factor, k=0 conservation
+  block_measures / classify ... hand-built block maps with known dilations
+  sigma_field ................. closed form of the taper product (Eq. S.2, S.3)
+  masked steps ................ threshold 0 == Regular bit for bit; infinite threshold
+                                leaves every block but the k=0 block untouched
+  nls_* ....................... CW exact solution, dispersion-only closed form,
+                                unitarity, forward/backward recovery
+No function here is "parity unpinned".
+
+Paper conventions restated (section / equation of arXiv 2609.03922):
+  * Block partition of the transformed field into fixed B^d blocks (Methods,
+    "Spectral dynamic block activation").
+  * States: ACTIVE when the block's activation measure meets the threshold;
+    TRANSITION when not active but a neighbouring block is active; FROZEN
+    otherwise (Methods).
+  * Transition smoothing q_{n+1} = q_n + sigma(k) dq_raw with the taper
+    w(i) = (1 - cos(pi i / (B-1))) / 2 and sigma the product of w over the
+    faces whose neighbour is frozen (S1.1, Eq. S.1-S.3).
+  * The block holding the zero-frequency mode is kept active (S6.1).
+  * Periodic refresh activates every block every F steps (S1.3); a warm-up of
+    all-active steps precedes adaptive operation (S3.2).
+  * Semi-implicit Fourier update of a conserved (Cahn-Hilliard form) field
+    (S3.1 dynamics, S4.2 semi-implicit update with M = 1).
+  * Symmetric split-step Fourier with the linear operator applied in two
+    frequency-domain half-steps and the Kerr phase in the time domain (S5.1,
+    S5.2); recovery metrics NMSE and field correlation (S5.3).
+"""
+import ctypes
+import math
+
+import numpy as np
+
+from . import build_oracle
+
+STATE_FROZEN = 0
+STATE_TRANSITION = 1
+STATE_ACTIVE = 2
+
+MEASURE_MAXAMP = 0   # A_B = max_{k in B} |q(k)|              (S4.2 any-mode amplitude)
+MEASURE_ENERGY = 1   # ||q_B||_2 = sqrt(sum_{k in B} |q(k)|^2)  (Results 2.1 block energy)
+
+TAU_REL_MAX = 0      # tau = threshold * max |q(k)|  (k = 0 excluded for the conserved CH field)
+TAU_ABS = 1          # tau = threshold
+
+__all__ = [
+    "STATE_FROZEN", "STATE_TRANSITION", "STATE_ACTIVE", "MEASURE_MAXAMP", "MEASURE_ENERGY",
+    "TAU_REL_MAX", "TAU_ABS", "fftn", "ifftn", "fft_batch", "ifft_batch", "num_threads",
+    "wavenumbers", "k_squared", "taper", "block_counts", "block_measures", "global_max_sq",
+    "threshold_value", "classify", "sigma_field", "ch_regular_step", "ch_masked_step",
+    "ch_real_field", "ch_mass", "CHConfig", "run_ch", "nls_omega", "nls_half_factor",
+    "nls_kerr", "nls_masked_half", "nls_regular_step", "nls_masked_step", "NLSConfig",
+    "run_nls", "rel_l2", "nmse_db", "field_corr", "assess_states", "effective_states",
+]
+
+# --------------------------------------------------------------------------------------
+# FFT (the oracle's own C implementation)
+# --------------------------------------------------------------------------------------
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        lib = ctypes.CDLL(path)
+        lib.oracle_fftn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_long),
+                                    ctypes.c_int, ctypes.c_int]
+        lib.oracle_fftn.restype = ctypes.c_int
+        lib.oracle_fft1_batch.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_long,
+                                          ctypes.c_int, ctypes.c_int]
+        lib.oracle_fft1_batch.restype = ctypes.c_int
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's FFT uses."""
+    return int(_load().oracle_num_threads())
+
+
+def _fftn(x, sign, normalize):
+    a = np.array(x, dtype=np.complex128, order="C", copy=True)
+    dims = (ctypes.c_long * a.ndim)(*a.shape)
+    rc = _load().oracle_fftn(a.ctypes.data, a.ndim, dims, sign, 1 if normalize else 0)
+    if rc != 0:
+        raise RuntimeError("oracle_fftn failed (%d)" % rc)
+    return a
+
+
+def fftn(x):
+    """Forward DFT over every axis: X[k] = sum_n x[n] exp(-2 pi i n.k / N)."""
+    return _fftn(x, -1, False)
+
+
+def ifftn(x):
+    """Inverse DFT over every axis with the 1/N normalisation."""
+    return _fftn(x, +1, True)
+
+
+def _fft_batch(x, sign, normalize):
+    a = np.array(x, dtype=np.complex128, order="C", copy=True)
+    if a.ndim != 2:
+        raise ValueError("expected (batch, n)")
+    rc = _load().oracle_fft1_batch(a.ctypes.data, a.shape[0], a.shape[1], sign,
+                                   1 if normalize else 0)
+    if rc != 0:
+        raise RuntimeError("oracle_fft1_batch failed (%d)" % rc)
+    return a
+
+
+def fft_batch(x):
+    """Forward 1-D DFT of each row of a (batch, n) array."""
+    return _fft_batch(x, -1, False)
+
+
+def ifft_batch(x):
+    """Inverse 1-D DFT (with 1/n) of each row of a (batch, n) array."""
+    return _fft_batch(x, +1, True)
+
+
+# --------------------------------------------------------------------------------------
+# Grids, blocks and block states
+# --------------------------------------------------------------------------------------
+def wavenumbers(n, dx=1.0):
+    """Angular wavenumbers of a periodic axis in FFT order: 2 pi j/(n dx) for j <= n/2,
+    2 pi (j - n)/(n dx) above."""
+    j = np.arange(n, dtype=np.float64)
+    j = np.where(j <= n // 2, j, j - n)
+    return 2.0 * math.pi * j / (n * dx)
+
+
+def k_squared(dims, dx=1.0):
+    """|k|^2 on the full (complex) spectral grid, same shape as the field."""
+    k2 = np.zeros(tuple(dims), dtype=np.float64)
+    for axis, n in enumerate(dims):
+        shape = [1] * len(dims)
+        shape[axis] = n
+        k2 = k2 + wavenumbers(n, dx).reshape(shape) ** 2
+    return k2
+
+
+def taper(B):
+    """1-D transition taper w(i) = (1 - cos(pi i / (B-1))) / 2, i = 0..B-1 (S1.1, Eq. S.2)."""
+    if B < 2:
+        return np.ones(B)
+    i = np.arange(B, dtype=np.float64)
+    return 0.5 * (1.0 - np.cos(math.pi * i / (B - 1)))
+
+
+def block_counts(dims, block):
+    for n, b in zip(dims, block):
+        if b < 1 or n % b != 0:
+            raise ValueError("block edge %d does not divide %d" % (b, n))
+    return tuple(n // b for n, b in zip(dims, block))
+
+
+def _blockify(a, block):
+    """View a field of shape dims as (nb0, B0, nb1, B1, ...)."""
+    nbs = block_counts(a.shape, block)
+    shape = []
+    for nb, b in zip(nbs, block):
+        shape += [nb, b]
+    return a.reshape(shape)
+
+
+def _mode_sq(q):
+    """|q|^2 = re^2 + im^2 in FP64 (re^2 and im^2 rounded separately, then added)."""
+    re = np.real(q).astype(np.float64)
+    im = np.imag(q).astype(np.float64)
+    return re * re + im * im
+
+
+def block_measures(q, block):
+    """Per-block max |q|^2 and sum |q|^2 (FP64), shape = block grid."""
+    sq = _blockify(_mode_sq(q), block)
+    axes = tuple(range(1, sq.ndim, 2))
+    return sq.max(axis=axes), sq.sum(axis=axes)
+
+
+def global_max_sq(q, exclude_dc):
+    """max |q(k)|^2 over the whole field, optionally excluding k = 0."""
+    sq = _mode_sq(q)
+    if exclude_dc:
+        sq = sq.copy()
+        sq.flat[0] = 0.0
+    return float(sq.max())
+
+
+def threshold_value(q, threshold, tau_rule, exclude_dc):
+    """tau = threshold * max |q(k)| (REL_MAX) or tau = threshold (ABS)."""
+    if tau_rule == TAU_ABS:
+        return float(threshold)
+    return float(threshold) * math.sqrt(global_max_sq(q, exclude_dc))
+
+
+def classify(measure, tau, force_dc=False, transitions=True):
+    """Block states from per-block measures (Methods; S1.1).
+
+    ACTIVE iff measure >= tau; the block holding k = 0 is forced ACTIVE when
+    force_dc (S6.1).  With transitions, a non-active block with an ACTIVE face
+    neighbour (periodic wrap of the block index) is TRANSITION; the rest are
+    FROZEN.
+    """
+    active = np.asarray(measure, dtype=np.float64) >= tau
+    if force_dc:
+        active.flat[0] = True
+    states = np.where(active, STATE_ACTIVE, STATE_FROZEN).astype(np.uint8)
+    if transitions:
+        near = np.zeros_like(active)
+        for axis in range(active.ndim):
+            near |= np.roll(active, 1, axis=axis)
+            near |= np.roll(active, -1, axis=axis)
+        states[(~active) & near] = STATE_TRANSITION
+    return states
+
+
+def sigma_field(states, block):
+    """Per-mode weight sigma(k) (S1.1, Eq. S.1-S.3).
+
+    ACTIVE blocks: 1.  FROZEN blocks: 0 (never used: they are not updated).
+    TRANSITION blocks: product over the faces whose neighbouring block is
+    FROZEN of w(distance of the mode from that face), i.e. w(i) for the
+    lower face and w(B-1-i) for the upper face of each axis.
+    """
+    states = np.asarray(states)
+    d = states.ndim
+    nbs = states.shape
+    dims = tuple(nb * b for nb, b in zip(nbs, block))
+    sigma = np.zeros(dims, dtype=np.float64)
+    w = [taper(b) for b in block]
+    for bidx in np.ndindex(*nbs):
+        st = states[bidx]
+        sl = tuple(slice(i * b, (i + 1) * b) for i, b in zip(bidx, block))
+        if st == STATE_ACTIVE:
+            sigma[sl] = 1.0
+        elif st == STATE_TRANSITION:
+            local = np.ones(tuple(block), dtype=np.float64)
+            for axis in range(d):
+                shape = [1] * d
+                shape[axis] = block[axis]
+                lo = list(bidx)
+                lo[axis] = (bidx[axis] - 1) % nbs[axis]
+                hi = list(bidx)
+                hi[axis] = (bidx[axis] + 1) % nbs[axis]
+                if states[tuple(lo)] == STATE_FROZEN:
+                    local = local * w[axis].reshape(shape)
+                if states[tuple(hi)] == STATE_FROZEN:
+                    local = local * w[axis][::-1].reshape(shape)
+            sigma[sl] = local
+    return sigma
+
+
+def _state_field(states, block):
+    """Expand per-block states to per-mode states."""
+    out = np.asarray(states)
+    for axis, b in enumerate(block):
+        out = np.repeat(out, b, axis=axis)
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# Cahn-Hilliard semi-implicit Fourier step (conserved form, S3.1; semi-implicit, S4.2)
+# --------------------------------------------------------------------------------------
+def ch_real_field(c_hat):
+    """c = Re(IFFT(c_hat))."""
+    return np.real(ifftn(c_hat))
+
+
+def ch_mass(c_hat):
+    """Sum of c over the grid, in FP64."""
+    return float(np.sum(ch_real_field(c_hat)))
+
+
+def _ch_new(c_hat, k2, dt, kappa):
+    c = ch_real_field(c_hat)
+    g = c * c * c - c
+    g_hat = fftn(g)
+    return (c_hat - dt * k2 * g_hat) / (1.0 + dt * kappa * k2 * k2)
+
+
+def ch_regular_step(c_hat, k2, dt, kappa):
+    """Regular (dense) step: c_hat <- (c_hat - dt k^2 FFT(c^3 - c)) / (1 + dt kappa k^4)."""
+    return _ch_new(c_hat, k2, dt, kappa)
+
+
+def ch_masked_step(c_hat, states, block, k2, dt, kappa, sigma=None):
+    """sp-DBA step: ACTIVE modes take the Regular result, TRANSITION modes
+    c_hat + sigma (new - c_hat), FROZEN modes keep c_hat (S1.1, Eq. S.1)."""
+    new = _ch_new(c_hat, k2, dt, kappa)
+    if sigma is None:
+        sigma = sigma_field(states, block)
+    st = _state_field(states, block)
+    out = np.where(st == STATE_ACTIVE, new, c_hat)
+    tr = st == STATE_TRANSITION
+    out[tr] = c_hat[tr] + sigma[tr] * (new[tr] - c_hat[tr])
+    return out
+
+
+class CHConfig:
+    """Parameters of an adaptive Cahn-Hilliard run (all keyword-overridable)."""
+
+    def __init__(self, dims, block, threshold=1e-6, reassess=10, dt=0.01, kappa=1.0,
+                 mode=1, measure=MEASURE_MAXAMP, tau_rule=TAU_REL_MAX, transitions=True,
+                 refresh_every=0, warmup_steps=0, force_dc=True):
+        self.dims = tuple(int(x) for x in dims)
+        self.block = tuple(int(x) for x in block)
+        self.threshold = float(threshold)
+        self.reassess = int(reassess)
+        self.dt = float(dt)
+        self.kappa = float(kappa)
+        self.mode = int(mode)
+        self.measure = int(measure)
+        self.tau_rule = int(tau_rule)
+        self.transitions = bool(transitions)
+        self.refresh_every = int(refresh_every)
+        self.warmup_steps = int(warmup_steps)
+        self.force_dc = bool(force_dc)
+
+
+def assess_states(q, cfg, exclude_dc):
+    """Measure, threshold and classify a transformed field; returns (states, tau, measure)."""
+    maxsq, sumsq = block_measures(q, cfg.block)
+    measure = np.sqrt(maxsq if cfg.measure == MEASURE_MAXAMP else sumsq)
+    tau = threshold_value(q, cfg.threshold, cfg.tau_rule, exclude_dc)
+    states = classify(measure, tau, force_dc=cfg.force_dc, transitions=cfg.transitions)
+    return states, tau, measure
+
+
+def effective_states(assessed, step, cfg):
+    """All blocks ACTIVE on warm-up and refresh steps (S1.3, S3.2), else the last assessment."""
+    if step < cfg.warmup_steps or (cfg.refresh_every > 0 and step > 0
+                                   and step % cfg.refresh_every == 0):
+        return np.full_like(assessed, STATE_ACTIVE)
+    return assessed
+
+
+def run_ch(c0, cfg, steps, start_step=0, c_hat=None, on_assess=None):
+    """Advance a CH field `steps` steps.  Returns (c_hat, history) where history
+    lists (step, states, tau) at each reassessment.  `on_assess(step, c_hat)` may
+    return replacement states (lock-step mask parity)."""
+    k2 = k_squared(cfg.dims)
+    if c_hat is None:
+        c_hat = fftn(np.asarray(c0, dtype=np.float64))
+    history = []
+    states = None
+    for n in range(start_step, start_step + steps):
+        if cfg.mode == 0:
+            c_hat = ch_regular_step(c_hat, k2, cfg.dt, cfg.kappa)
+            continue
+        if states is None or n % cfg.reassess == 0:
+            states, tau, _ = assess_states(c_hat, cfg, exclude_dc=True)
+            if on_assess is not None:
+                repl = on_assess(n, c_hat, states, tau)
+                if repl is not None:
+                    states = repl
+            history.append((n, states.copy(), tau))
+        eff = effective_states(states, n, cfg)
+        c_hat = ch_masked_step(c_hat, eff, cfg.block, k2, cfg.dt, cfg.kappa)
+    return c_hat, history
+
+
+# --------------------------------------------------------------------------------------
+# Scalar NLS split-step Fourier (S5.1-S5.2 with M = 1, alpha = 0)
+# --------------------------------------------------------------------------------------
+def nls_omega(n, dt_sample):
+    """Angular frequency of each FFT bin: 2 pi j / (n dt) with j in FFT order."""
+    return wavenumbers(n, dt_sample)
+
+
+def nls_half_factor(omega, beta2, h):
+    """Linear half-step propagator exp((i beta2 omega^2 / 2) h / 2) for E(t) = (1/N) sum E~ e^{+i w t}
+    (S5.2, alpha = 0, no mode coupling)."""
+    return np.exp(1j * beta2 * omega * omega * h / 4.0)
+
+
+def nls_kerr(E, gamma, h):
+    """Time-domain Kerr step E exp(i gamma |E|^2 h) (scalar field: no Manakov 8/9)."""
+    p = np.real(E) ** 2 + np.imag(E) ** 2
+    return E * np.exp(1j * gamma * p * h)
+
+
+def nls_masked_half(Et, states, block, H, sigma=None):
+    """Blockwise linear half-step: ACTIVE E~ H, TRANSITION E~ + sigma (E~ H - E~), FROZEN E~."""
+    new = Et * H
+    if states is None:
+        return new
+    if sigma is None:
+        sigma = sigma_field(states, block)
+    st = _state_field(states, block)
+    out = np.where(st == STATE_ACTIVE, new, Et)
+    tr = st == STATE_TRANSITION
+    out[tr] = Et[tr] + sigma[tr] * (new[tr] - Et[tr])
+    return out
+
+
+def nls_regular_step(E, H, gamma, h):
+    """One symmetric split step, literal order: L/2 -> N -> L/2 with 4 transforms."""
+    return nls_masked_step(E, None, None, H, gamma, h)
+
+
+def nls_masked_step(E, states, block, H, gamma, h, sigma=None):
+    Et = fftn(E)
+    Et = nls_masked_half(Et, states, block, H, sigma)
+    E = ifftn(Et)
+    E = nls_kerr(E, gamma, h)
+    Et = fftn(E)
+    Et = nls_masked_half(Et, states, block, H, sigma)
+    return ifftn(Et)
+
+
+class NLSConfig:
+    def __init__(self, n, block, threshold=1e-6, reassess=10, beta2=-21.7, gamma=1.3, h=0.1,
+                 dt_sample=1.0, mode=1, measure=MEASURE_MAXAMP, tau_rule=TAU_REL_MAX,
+                 transitions=True, refresh_every=0, warmup_steps=0):
+        self.dims = (int(n),)
+        self.block = (int(block),)
+        self.threshold = float(threshold)
+        self.reassess = int(reassess)
+        self.beta2 = float(beta2)
+        self.gamma = float(gamma)
+        self.h = float(h)
+        self.dt_sample = float(dt_sample)
+        self.mode = int(mode)
+        self.measure = int(measure)
+        self.tau_rule = int(tau_rule)
+        self.transitions = bool(transitions)
+        self.refresh_every = int(refresh_every)
+        self.warmup_steps = int(warmup_steps)
+        self.force_dc = False
+
+
+def run_nls(E0, cfg, steps, on_assess=None):
+    """Propagate E0 by `steps` split steps; states are assessed on FFT(E) at the
+    start of a step, every `reassess` steps (S5.3: total spectral power, M = 1)."""
+    n = cfg.dims[0]
+    H = nls_half_factor(nls_omega(n, cfg.dt_sample), cfg.beta2, cfg.h)
+    E = np.asarray(E0, dtype=np.complex128)
+    history = []
+    states = None
+    for s in range(steps):
+        if cfg.mode == 0:
+            E = nls_regular_step(E, H, cfg.gamma, cfg.h)
+            continue
+        if states is None or s % cfg.reassess == 0:
+            states, tau, _ = assess_states(fftn(E), cfg, exclude_dc=False)
+            if on_assess is not None:
+                repl = on_assess(s, E, states, tau)
+                if repl is not None:
+                    states = repl
+            history.append((s, states.copy(), tau))
+        eff = effective_states(states, s, cfg)
+        E = nls_masked_step(E, eff, cfg.block, H, cfg.gamma, cfg.h)
+    return E, history
+
+
+# --------------------------------------------------------------------------------------
+# Metrics (S5.3)
+# --------------------------------------------------------------------------------------
+def rel_l2(x, ref):
+    """||x - ref||_2 / ||ref||_2 in FP64."""
+    x = np.asarray(x)
+    ref = np.asarray(ref)
+    num = np.sqrt(np.sum(np.abs(x.astype(np.complex128) - ref.astype(np.complex128)) ** 2))
+    den = np.sqrt(np.sum(np.abs(ref.astype(np.complex128)) ** 2))
+    return float(num / den)
+
+
+def nmse_db(E, E_tx):
+    """NMSE(dB) = 10 log10( sum |E - E_tx|^2 / sum |E_tx|^2 )."""
+    E = np.asarray(E, dtype=np.complex128)
+    E_tx = np.asarray(E_tx, dtype=np.complex128)
+    return float(10.0 * np.log10(np.sum(np.abs(E - E_tx) ** 2) / np.sum(np.abs(E_tx) ** 2)))
+
+
+def field_corr(E, E_tx):
+    """|sum E^H E_tx| / (||E|| ||E_tx||)."""
+    E = np.asarray(E, dtype=np.complex128)
+    E_tx = np.asarray(E_tx, dtype=np.complex128)
+    num = abs(np.sum(np.conj(E) * E_tx))
+    return float(num / math.sqrt(np.sum(np.abs(E) ** 2) * np.sum(np.abs(E_tx) ** 2)))
