@@ -1,0 +1,227 @@
+/*
+ * spdba.h - C ABI of the GB300 (sm_103a) sp-DBA library, libspdba.so.
+ *
+ * sp-DBA (spectral dynamic block activation, arXiv 2609.03922) runs a
+ * time-stepped transform-domain solver whose transformed field is cut into
+ * fixed blocks.  Each block gets an activity measure that is compared with a
+ * threshold; ACTIVE blocks run the model's update core, TRANSITION blocks
+ * (neighbours of active blocks) apply a tapered increment, FROZEN blocks keep
+ * their stored values (Methods; Supplementary S1.1).  The update sits between
+ * a forward and an inverse FFT, both written here as CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SPDBA_OK or an error code; no call aborts the process.
+ *     spdba_last_error() returns a human-readable message for the calling
+ *     thread's most recent failure.  A CUDA error seen by a plan is latched:
+ *     every later call on that plan returns SPDBA_ERR_CUDA.
+ *   - Arrays are row-major with the last axis fastest.  dims[0] is the slowest
+ *     axis.  Complex values are interleaved (re, im) pairs of float (C64) or
+ *     double (C128).
+ *   - Caller buffers are never retained past the call.  "device" pointers
+ *     must be CUDA device (or managed) memory on the current device; "host"
+ *     pointers are ordinary host memory (pinned host memory makes the copy
+ *     asynchronous with respect to the host thread up to the call's own sync).
+ *   - Work is enqueued on the stream given in spdba_options.stream (or, for
+ *     the kernel-level calls, the `stream` argument; NULL = legacy default).
+ */
+#ifndef SPDBA_H
+#define SPDBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPDBA_OK = 0,
+    SPDBA_ERR_ARG = 1,          /* NULL pointer, bad enum value, size mismatch          */
+    SPDBA_ERR_UNSUPPORTED = 2,  /* a length with a prime factor other than 2 or 3, a
+                                   block edge that does not divide the grid, a length
+                                   outside the supported range                           */
+    SPDBA_ERR_CUDA = 3,         /* a CUDA runtime call or kernel failed (latched)        */
+    SPDBA_ERR_OOM = 4,          /* device allocation failed                              */
+    SPDBA_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out                    */
+    SPDBA_ERR_STATE = 6         /* call not valid in the plan's current state            */
+} spdba_status;
+
+enum { SPDBA_MODEL_CH = 0, SPDBA_MODEL_NLS = 1 };
+enum { SPDBA_C64 = 0, SPDBA_C128 = 1 };
+/* spdba_apply(mode) of the paper (S2.1): 0 = Regular full update, 1 = sp-DBA */
+enum { SPDBA_MODE_REGULAR = 0, SPDBA_MODE_ADAPTIVE = 1 };
+/* Activation measure.  MAXAMP: A_B = max_{k in B} |q(k)| (S4.2, any-mode amplitude).
+   ENERGY: ||q_B||_2 = sqrt(sum_{k in B} |q(k)|^2) (Results, PFC block energy). */
+enum { SPDBA_MEASURE_MAXAMP = 0, SPDBA_MEASURE_ENERGY = 1 };
+/* Threshold rule.  REL_MAX: tau = threshold * max_k |q(k)|, with k = 0 left out of
+   the max for the conserved Cahn-Hilliard field.  ABS: tau = threshold. */
+enum { SPDBA_TAU_REL_MAX = 0, SPDBA_TAU_ABS = 1 };
+/* Block states as returned by spdba_get_mask (Methods). */
+enum { SPDBA_FROZEN = 0, SPDBA_TRANSITION = 1, SPDBA_ACTIVE = 2 };
+/* FFT direction: forward uses exp(-2 pi i n k / N), inverse exp(+...) and 1/N. */
+enum { SPDBA_FORWARD = -1, SPDBA_INVERSE = 1 };
+
+typedef struct spdba_options {
+    int32_t model;          /* SPDBA_MODEL_CH or SPDBA_MODEL_NLS                          */
+    int32_t precision;      /* SPDBA_C64 (FP32 bulk, FP64 norms) or SPDBA_C128 (FP64)     */
+    int32_t mode;           /* SPDBA_MODE_REGULAR or SPDBA_MODE_ADAPTIVE                  */
+    int32_t measure;        /* SPDBA_MEASURE_*                                            */
+    int32_t tau_rule;       /* SPDBA_TAU_*                                                */
+    int32_t transitions;    /* 1: transition blocks with boundary-aware smoothing (S1.1) */
+    int32_t force_dc;       /* 1: the block holding k = 0 is always ACTIVE (S6.1)         */
+    int32_t refresh_every;  /* F_refresh: all blocks ACTIVE every F steps, 0 = off (S1.3) */
+    int32_t warmup_steps;   /* all blocks ACTIVE for the first steps (S3.2), 0 = none     */
+    int32_t use_graph;      /* 1: replay captured CUDA graphs for runs of steps          */
+    double dt, kappa, dx;   /* Cahn-Hilliard: time step, gradient coefficient, spacing  */
+    double beta2, gamma, h, dt_sample; /* NLS: ps^2/km, 1/(W km), km step, ps sample     */
+    void* stream;           /* cudaStream_t the plan enqueues on                         */
+} spdba_options;
+
+/* Per-run statistics, refreshed at each reassessment. */
+typedef struct spdba_stats {
+    int64_t step;            /* steps taken so far                                       */
+    int64_t assessments;     /* reassessments done                                       */
+    int64_t nblocks;         /* blocks in the block map                                  */
+    int64_t n_active;        /* ACTIVE blocks at the last reassessment                  */
+    int64_t n_transition;    /* TRANSITION blocks at the last reassessment              */
+    double tau;              /* threshold value used at the last reassessment           */
+    double max_amp;          /* max |q(k)| at the last reassessment (k = 0 excluded, CH) */
+    double mass;             /* CH: FP64 sum of the real field at the last reassessment;
+                                NLS: FP64 sum |E(t)|^2                                    */
+    double active_ratio_sum; /* sum over steps of (ACTIVE + TRANSITION) / nblocks        */
+} spdba_stats;
+
+typedef struct spdba_plan spdba_plan;         /* opaque; owns all of its device buffers */
+typedef struct spdba_fft_plan spdba_fft_plan; /* opaque; owns its twiddle tables        */
+
+/* Fill *opt with the defaults: CH, C64, ADAPTIVE, MAXAMP, REL_MAX, transitions on,
+   force_dc on (CH) , refresh and warm-up off, graphs on, dt = 0.01, kappa = 1,
+   dx = 1, beta2 = -21.7, gamma = 1.3, h = 0.1, dt_sample = 1, default stream. */
+void spdba_options_default(spdba_options* opt);
+
+/*
+ * Create a plan for one field (spdba_init of S2.1).
+ *   ndim        1, 2 or 3 (NLS: 1; CH: 2 or 3)
+ *   dims[ndim]  grid extents, each of the form 2^a 3^b; CH axes 8..512, NLS 64..2^18
+ *   block[ndim] block edge per axis; must divide dims; the block map is
+ *               dims[a]/block[a] per axis, row-major, slowest axis first
+ *               (block b along an axis covers FFT indices [b*B, b*B + B - 1])
+ *   threshold   see tau_rule; reassess  steps between block-state reassessments (>= 1)
+ * The field starts at zero; set it with spdba_set_field.  *out receives the plan.
+ */
+spdba_status spdba_plan_create(spdba_plan** out, int32_t ndim, const int64_t* dims,
+                               const int32_t* block, double threshold, int32_t reassess,
+                               const spdba_options* opt);
+
+/*
+ * Create one plan holding `nruns` independent fields of possibly different sizes
+ * (an ensemble of CH runs or a batch of NLS signals) that step together.
+ *   dims   nruns * ndim extents, run-major
+ *   block  ndim block edges, or for NLS (block[0] <= 0) the block map has
+ *          -block[0] blocks per signal (block edge = n / -block[0])
+ */
+spdba_status spdba_batch_create(spdba_plan** out, int32_t nruns, int32_t ndim,
+                                const int64_t* dims, const int32_t* block, double threshold,
+                                int32_t reassess, const spdba_options* opt);
+
+/* Load run `run`'s field.  CH: real values (float for C64, double for C128),
+   prod(dims) of them.  NLS: complex time-domain samples.  src_on_device selects
+   a device or host source.  Resets the run's step counter, states and stats. */
+spdba_status spdba_set_field(spdba_plan* plan, int32_t run, const void* src, int32_t src_on_device);
+
+/* Advance every run by n steps (spdba_apply inside the time loop of S2.1).
+   Asynchronous on the plan's stream; returns after enqueueing. */
+spdba_status spdba_step(spdba_plan* plan, int64_t n);
+
+/* Copy run `run`'s real-space field (CH: Re(IFFT(c_hat)) as real values; NLS:
+   complex E(t)) to dst.  Synchronizes the plan's stream. */
+spdba_status spdba_get_field(spdba_plan* plan, int32_t run, void* dst, int32_t dst_on_device);
+
+/* Copy / overwrite run `run`'s transformed field (complex, full spectrum, FFT order).
+   get synchronizes; set resets nothing but the cached block measures. */
+spdba_status spdba_get_spectrum(spdba_plan* plan, int32_t run, void* dst, int32_t dst_on_device);
+spdba_status spdba_set_spectrum(spdba_plan* plan, int32_t run, const void* src, int32_t src_on_device);
+
+/* Copy run `run`'s block states at the last reassessment (uint8: 0 FROZEN,
+   1 TRANSITION, 2 ACTIVE; nblocks entries) to host memory.  Synchronizes. */
+spdba_status spdba_get_mask(spdba_plan* plan, int32_t run, uint8_t* dst, int64_t nblocks);
+
+/* Statistics of run `run`.  Synchronizes. */
+spdba_status spdba_get_stats(spdba_plan* plan, int32_t run, spdba_stats* out);
+
+/* Wait for all work enqueued by the plan. */
+spdba_status spdba_sync(spdba_plan* plan);
+
+/* Release the plan and its device memory (spdba_destroy of S2.1).  NULL is a no-op. */
+void spdba_plan_destroy(spdba_plan* plan);
+
+/* Kernel timing on the plan's stream (CUDA events around each launch of the
+   step path), for roofline reporting.  begin clears the record; end waits for
+   the stream and returns one entry per kernel kind (at most `capacity`), the
+   number of entries in *n_out, and the number of kernels the plan launched
+   since begin in *launches_out.  `bytes` is the algorithmic traffic of all
+   recorded launches of that kind (bytes read + written by its definition). */
+typedef struct spdba_kernel_time {
+    char name[40];
+    int64_t launches;
+    double total_ms;
+    double bytes;
+} spdba_kernel_time;
+spdba_status spdba_profile_begin(spdba_plan* plan);
+spdba_status spdba_profile_end(spdba_plan* plan, spdba_kernel_time* out, int32_t capacity, int32_t* n_out,
+                               int64_t* launches_out);
+
+const char* spdba_last_error(void);
+const char* spdba_status_string(spdba_status s);
+
+/* ------------------------------------------------------------------------------ */
+/* Kernel-level entry points (device pointers, caller-owned buffers).               */
+/* ------------------------------------------------------------------------------ */
+
+/*
+ * Batched multi-dimensional complex FFT (Stockham, shared-memory staged), the
+ * transform that surrounds every sp-DBA update (Methods, Fig. 1b).
+ * `batch` transforms of shape dims[0..ndim-1], contiguous one after another.
+ * Each axis must be 2^a 3^b; axes of 2-D/3-D transforms 8..512, 1-D lengths
+ * 8..2^18.  Twiddles are computed in FP64 once, at plan creation.
+ */
+spdba_status spdba_fft_plan_create(spdba_fft_plan** out, int32_t precision, int32_t ndim,
+                                   const int64_t* dims, int64_t batch);
+/* in and out may alias (in-place); direction SPDBA_FORWARD or SPDBA_INVERSE. */
+spdba_status spdba_fft_exec(spdba_fft_plan* plan, const void* in, void* out,
+                            int32_t direction, void* stream);
+void spdba_fft_plan_destroy(spdba_fft_plan* plan);
+
+/*
+ * Per-block activity of a transformed field q (device, complex, shape dims):
+ *   maxsq[b] = max_{k in B_b} |q(k)|^2,  sumsq[b] = sum_{k in B_b} |q(k)|^2
+ * and gmax[0] = max over all k, gmax[1] = max over k != 0 (FP64, device).
+ * |q|^2 is formed in FP64 as re*re + im*im (Methods: activation measure;
+ * Results 2.1 block energy; S4.2 any-mode amplitude).
+ */
+spdba_status spdba_block_activity(int32_t precision, int32_t ndim, const int64_t* dims,
+                                  const int32_t* block, const void* q, double* maxsq,
+                                  double* sumsq, double* gmax, void* stream);
+
+/*
+ * Block states and the compacted list of non-frozen blocks (Methods: state
+ * preparation; S1.1 frozen-neighbour pattern).
+ *   measure[nb]  block measure in amplitude units (device, FP64)
+ *   tau          device FP64 scalar: ACTIVE iff measure >= tau
+ *   force_dc     1: block 0 is ACTIVE regardless; transitions: 1 = dilate by face
+ *                neighbours (periodic) into TRANSITION
+ *   states[nb]   out: 0/1/2;   chi[nb]  out: bit (2a) set when the lower neighbour
+ *                along axis a is FROZEN, bit (2a+1) for the upper one (axis 0 slowest)
+ *   list[nb]     out: ids of non-frozen blocks in increasing order; count[0] their number
+ *   scratch      device buffer of at least spdba_classify_scratch_bytes(nb) bytes
+ */
+size_t spdba_classify_scratch_bytes(int64_t nb);
+spdba_status spdba_classify(int32_t ndim, const int64_t* nblocks, const double* measure,
+                            const double* tau, int32_t force_dc, int32_t transitions,
+                            uint8_t* states, uint8_t* chi, int32_t* list, int32_t* count,
+                            void* scratch, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPDBA_H */

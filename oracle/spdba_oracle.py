@@ -347,15 +347,15 @@ def effective_states(assessed, step, cfg):
     return assessed
 
 
-def run_ch(c0, cfg, steps, start_step=0, c_hat=None, on_assess=None):
+def run_ch(c0, cfg, steps, start_step=0, c_hat=None, on_assess=None, states=None):
     """Advance a CH field `steps` steps.  Returns (c_hat, history) where history
-    lists (step, states, tau) at each reassessment.  `on_assess(step, c_hat)` may
-    return replacement states (lock-step mask parity)."""
+    lists (step, states, tau) at each reassessment.  `on_assess(step, c_hat,
+    states, tau)` may return replacement states (lock-step mask parity).  To
+    continue a run, pass its c_hat, start_step and the states in force."""
     k2 = k_squared(cfg.dims)
     if c_hat is None:
         c_hat = fftn(np.asarray(c0, dtype=np.float64))
     history = []
-    states = None
     for n in range(start_step, start_step + steps):
         if cfg.mode == 0:
             c_hat = ch_regular_step(c_hat, k2, cfg.dt, cfg.kappa)

@@ -1,0 +1,280 @@
+// State preparation of sp-DBA on the device: per-block activity (FP64 norms),
+// the threshold, block states with transition dilation, the frozen-neighbour
+// bits used by the smoothing weight, and the ordered compaction of the
+// non-frozen block list (Methods: state preparation; S1.1).
+#include <math.h>
+
+#include "blocks.h"
+
+namespace spdba {
+
+spdba_status make_geom(Geom* g, int ndim, const int64_t* dims, const int32_t* block) {
+    if (ndim < 1 || ndim > 3 || !dims || !block) return fail(SPDBA_ERR_ARG, "bad geometry arguments");
+    Geom r;
+    r.ndim = ndim;
+    int off = 3 - ndim;
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 1 || block[a] < 1) return fail(SPDBA_ERR_ARG, "non-positive extent");
+        if (dims[a] % block[a] != 0)
+            return fail(SPDBA_ERR_UNSUPPORTED, "block edge %d does not divide %lld", block[a], (long long)dims[a]);
+        r.n[off + a] = dims[a];
+        r.b[off + a] = block[a];
+        r.nb[off + a] = dims[a] / block[a];
+    }
+    *g = r;
+    return SPDBA_OK;
+}
+
+// ------------------------------------------------------------------ activity
+// One CTA per block.  |q|^2 is formed in FP64 from the stored values
+// (exact squares of FP32 components), max- and sum-reduced per thread, then
+// across the warp with shuffles and across warps through shared memory.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T>* __restrict__ q,
+                                                            double* __restrict__ maxsq, double* __restrict__ sumsq,
+                                                            double* __restrict__ gmax) {
+    const long long blk = blockIdx.x;
+    const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
+    const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
+    const long long nmodes = (long long)B0 * B1 * B2;
+    double mx = 0.0, mxnd = 0.0, sm = 0.0;
+    for (long long m = threadIdx.x; m < nmodes; m += NT) {
+        int l2 = (int)(m % B2);
+        long long r = m / B2;
+        int l1 = (int)(r % B1), l0 = (int)(r / B1);
+        long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
+        double s = mode_sq(__ldg(q + idx));
+        mx = fmax(mx, s);
+        if (idx != 0) mxnd = fmax(mxnd, s);
+        sm += s;
+    }
+    mx = warp_max(mx);
+    mxnd = warp_max(mxnd);
+    sm = warp_sum(sm);
+    __shared__ double red[3][NT / 32];
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red[0][w] = mx; red[1][w] = mxnd; red[2][w] = sm; }
+    __syncthreads();
+    if (w == 0) {
+        mx = l < NT / 32 ? red[0][l] : 0.0;
+        mxnd = l < NT / 32 ? red[1][l] : 0.0;
+        sm = l < NT / 32 ? red[2][l] : 0.0;
+        mx = warp_max(mx);
+        mxnd = warp_max(mxnd);
+        sm = warp_sum(sm);
+        if (l == 0) {
+            maxsq[blk] = mx;
+            if (sumsq) sumsq[blk] = sm;
+            atomic_max_nonneg(&gmax[0], mx);
+            atomic_max_nonneg(&gmax[1], mxnd);
+        }
+    }
+}
+
+template <typename T>
+spdba_status launch_block_activity(const Geom& g, const cx_t<T>* q, double* maxsq, double* sumsq, double* gmax,
+                                   cudaStream_t st) {
+    constexpr int NT = 128;
+    long long nb = g.blocks();
+    block_activity_kernel<T, NT><<<(unsigned)nb, NT, 0, st>>>(g, q, maxsq, sumsq, gmax);
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
+}
+template spdba_status launch_block_activity<float>(const Geom&, const float2*, double*, double*, double*,
+                                                   cudaStream_t);
+template spdba_status launch_block_activity<double>(const Geom&, const double2*, double*, double*, double*,
+                                                    cudaStream_t);
+
+// ------------------------------------------------------------------ threshold
+__global__ void tau_kernel(const double* gmax, double threshold, int tau_rule, int exclude_dc, double* tau,
+                           DevStats* stats) {
+    double amax = sqrt(gmax[exclude_dc ? 1 : 0]);
+    double t = tau_rule == SPDBA_TAU_ABS ? threshold : threshold * amax;
+    *tau = t;
+    if (stats) {
+        stats->tau = t;
+        stats->max_amp = amax;
+    }
+}
+
+spdba_status launch_tau(const double* gmax, double threshold, int tau_rule, int exclude_dc, double* tau,
+                        DevStats* stats, cudaStream_t st) {
+    tau_kernel<<<1, 1, 0, st>>>(gmax, threshold, tau_rule, exclude_dc, tau, stats);
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
+}
+
+// ------------------------------------------------------------------ states
+constexpr int CLS_NT = 1024;
+
+__device__ __forceinline__ long long nbr(const Geom& g, long long b, int axis, int dir) {
+    long long c[3];
+    c[2] = b % g.nb[2];
+    c[1] = (b / g.nb[2]) % g.nb[1];
+    c[0] = b / (g.nb[2] * g.nb[1]);
+    c[axis] = (c[axis] + dir + g.nb[axis]) % g.nb[axis];
+    return (c[0] * g.nb[1] + c[1]) * g.nb[2] + c[2];
+}
+
+// ACTIVE iff the block's measure meets tau (>=), or forced.
+__global__ void active_kernel(Geom g, const double* __restrict__ msq, int msq_is_square, const double* tau,
+                              int force_dc, int all_active, uint8_t* __restrict__ active) {
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nb = g.blocks();
+    if (b >= nb) return;
+    double m = msq_is_square ? sqrt(msq[b]) : msq[b];
+    bool a = all_active || (force_dc && b == 0) || (m >= *tau);
+    active[b] = a ? 1 : 0;
+}
+
+__device__ __forceinline__ bool has_active_nbr(const Geom& g, const uint8_t* active, long long b) {
+    const int a0 = 3 - g.ndim;
+    for (int ax = a0; ax < 3; ++ax) {
+        if (active[nbr(g, b, ax, -1)] || active[nbr(g, b, ax, +1)]) return true;
+    }
+    return false;
+}
+
+// TRANSITION iff not active and a face neighbour (periodic) is active; chi bit
+// 2a / 2a+1 marks a FROZEN lower / upper neighbour along local axis a (axis 0
+// = slowest axis of the field).  One CTA-sized count per CTA goes to scratch.
+__global__ void __launch_bounds__(CLS_NT) state_kernel(Geom g, const uint8_t* __restrict__ active, int transitions,
+                                                       uint8_t* __restrict__ states, uint8_t* __restrict__ chi,
+                                                       int* __restrict__ cta_count, DevStats* stats) {
+    long long b = (long long)blockIdx.x * CLS_NT + threadIdx.x;
+    long long nb = g.blocks();
+    int st = 0;
+    uint8_t cb = 0;
+    if (b < nb) {
+        if (active[b]) st = SPDBA_ACTIVE;
+        else if (transitions && has_active_nbr(g, active, b)) st = SPDBA_TRANSITION;
+        const int a0 = 3 - g.ndim;
+        for (int ax = a0; ax < 3; ++ax) {
+            for (int d = 0; d < 2; ++d) {
+                long long n = nbr(g, b, ax, d == 0 ? -1 : +1);
+                bool frozen = !active[n] && !(transitions && has_active_nbr(g, active, n));
+                if (frozen) cb |= (uint8_t)(1u << (2 * (ax - a0) + d));
+            }
+        }
+        states[b] = (uint8_t)st;
+        chi[b] = cb;
+    }
+    unsigned nf = __ballot_sync(0xffffffffu, st != 0);
+    unsigned na = __ballot_sync(0xffffffffu, st == SPDBA_ACTIVE);
+    unsigned nt = __ballot_sync(0xffffffffu, st == SPDBA_TRANSITION);
+    __shared__ int s_nf, s_na, s_nt;
+    if (threadIdx.x == 0) { s_nf = 0; s_na = 0; s_nt = 0; }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_nf, __popc(nf));
+        atomicAdd(&s_na, __popc(na));
+        atomicAdd(&s_nt, __popc(nt));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cta_count[blockIdx.x] = s_nf;
+        if (stats) {
+            atomicAdd(&stats->n_active, (unsigned long long)s_na);
+            atomicAdd(&stats->n_transition, (unsigned long long)s_nt);
+        }
+    }
+}
+
+// Ordered compaction: CTA c starts at the sum of the counts of CTAs before it
+// and places its non-frozen ids with a warp-ballot prefix and a block scan.
+__global__ void __launch_bounds__(CLS_NT) compact_kernel(Geom g, const uint8_t* __restrict__ states,
+                                                         const int* __restrict__ cta_count, int ncta,
+                                                         int32_t* __restrict__ list, int32_t* __restrict__ count) {
+    __shared__ int s_base;
+    __shared__ int s_warp[CLS_NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 0) {
+        int acc = 0;
+        for (int c = lane; c < (int)blockIdx.x; c += 32) acc += cta_count[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_base = acc;
+    }
+    long long b = (long long)blockIdx.x * CLS_NT + threadIdx.x;
+    bool keep = b < g.blocks() && states[b] != 0;
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_warp[w] = __popc(m);
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < CLS_NT / 32 ? s_warp[lane] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane < CLS_NT / 32) s_warp[lane] = incl - v;
+        if (blockIdx.x == (unsigned)(ncta - 1) && lane == 31) *count = s_base + incl;
+    }
+    __syncthreads();
+    if (keep) {
+        int pos = s_base + s_warp[w] + __popc(m & ((1u << lane) - 1u));
+        list[pos] = (int32_t)b;
+    }
+}
+
+__global__ void zero_counts_kernel(DevStats* stats) {
+    stats->n_active = 0;
+    stats->n_transition = 0;
+    stats->assessments += 1;
+}
+
+size_t classify_scratch_bytes(long long nb) { return sizeof(int) * (size_t)((nb + CLS_NT - 1) / CLS_NT); }
+
+spdba_status launch_classify(const Geom& g, const double* msq, int msq_is_square, const double* tau, int force_dc,
+                             int transitions, int all_active, uint8_t* active, uint8_t* states, uint8_t* chi,
+                             int32_t* list, int32_t* count, void* scratch, DevStats* stats, cudaStream_t st) {
+    long long nb = g.blocks();
+    int ncta = (int)((nb + CLS_NT - 1) / CLS_NT);
+    if (stats) zero_counts_kernel<<<1, 1, 0, st>>>(stats);
+    active_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(g, msq, msq_is_square, tau, force_dc, all_active,
+                                                                 active);
+    state_kernel<<<ncta, CLS_NT, 0, st>>>(g, active, transitions, states, chi, (int*)scratch, stats);
+    compact_kernel<<<ncta, CLS_NT, 0, st>>>(g, states, (const int*)scratch, ncta, list, count);
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
+}
+
+}  // namespace spdba
+
+// ------------------------------------------------------------------ C ABI
+using namespace spdba;
+
+extern "C" spdba_status spdba_block_activity(int32_t precision, int32_t ndim, const int64_t* dims,
+                                             const int32_t* block, const void* q, double* maxsq, double* sumsq,
+                                             double* gmax, void* stream) {
+    if (!q || !maxsq || !gmax) return fail(SPDBA_ERR_ARG, "spdba_block_activity: NULL buffer");
+    Geom g;
+    spdba_status s = make_geom(&g, ndim, dims, block);
+    if (s != SPDBA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    SPDBA_CUDA(cudaMemsetAsync(gmax, 0, 2 * sizeof(double), st));
+    if (precision == SPDBA_C64) return launch_block_activity<float>(g, (const float2*)q, maxsq, sumsq, gmax, st);
+    if (precision == SPDBA_C128) return launch_block_activity<double>(g, (const double2*)q, maxsq, sumsq, gmax, st);
+    return fail(SPDBA_ERR_ARG, "bad precision %d", precision);
+}
+
+extern "C" size_t spdba_classify_scratch_bytes(int64_t nb) { return classify_scratch_bytes(nb) + (size_t)nb; }
+
+extern "C" spdba_status spdba_classify(int32_t ndim, const int64_t* nblocks, const double* measure,
+                                       const double* tau, int32_t force_dc, int32_t transitions, uint8_t* states,
+                                       uint8_t* chi, int32_t* list, int32_t* count, void* scratch, void* stream) {
+    if (!nblocks || !measure || !tau || !states || !chi || !list || !count || !scratch)
+        return fail(SPDBA_ERR_ARG, "spdba_classify: NULL argument");
+    int64_t dims[3];
+    int32_t one[3] = {1, 1, 1};
+    for (int a = 0; a < ndim && a < 3; ++a) dims[a] = nblocks[a];
+    Geom g;
+    spdba_status s = make_geom(&g, ndim, dims, one);
+    if (s != SPDBA_OK) return s;
+    // scratch layout: per-CTA counts, then one active flag per block
+    size_t cbytes = classify_scratch_bytes(g.blocks());
+    uint8_t* active = (uint8_t*)scratch + cbytes;
+    return launch_classify(g, measure, 0, tau, force_dc, transitions, 0, active, states, chi, list, count, scratch,
+                           nullptr, (cudaStream_t)stream);
+}

@@ -1,0 +1,67 @@
+// Block geometry and the launchers of the activity / state / update kernels.
+#pragma once
+#include "internal.h"
+
+namespace spdba {
+
+// Grid and block map padded to three axes (axis 0 slowest); unused leading
+// axes have extent 1.
+struct Geom {
+    int ndim = 0;
+    long long n[3] = {1, 1, 1};
+    int b[3] = {1, 1, 1};
+    long long nb[3] = {1, 1, 1};
+    __host__ __device__ long long modes() const { return n[0] * n[1] * n[2]; }
+    __host__ __device__ long long blocks() const { return nb[0] * nb[1] * nb[2]; }
+    __host__ __device__ long long block_modes() const { return (long long)b[0] * b[1] * b[2]; }
+};
+spdba_status make_geom(Geom* g, int ndim, const int64_t* dims, const int32_t* block);
+
+// Device statistics of one run (mirrors spdba_stats, accumulated on the device).
+struct DevStats {
+    double tau;
+    double max_amp;
+    double mass;
+    double ratio_sum;
+    unsigned long long n_active;
+    unsigned long long n_transition;
+    unsigned long long assessments;
+    double list_modes;   // modes touched by list-driven updates (for traffic accounting)
+};
+
+// maxsq / sumsq per block, gmax[0] = max over all modes, gmax[1] = max over k != 0.
+// gmax must be zeroed before the launch (the kernel max-reduces into it).
+template <typename T>
+spdba_status launch_block_activity(const Geom& g, const cx_t<T>* q, double* maxsq, double* sumsq, double* gmax,
+                                   cudaStream_t st);
+// tau = threshold (ABS) or threshold * sqrt(gmax[exclude_dc]) (REL_MAX); also
+// records tau and max amplitude in stats (may be null).
+spdba_status launch_tau(const double* gmax, double threshold, int tau_rule, int exclude_dc, double* tau,
+                        DevStats* stats, cudaStream_t st);
+// States, frozen-neighbour bits and the ordered list of non-frozen blocks.
+size_t classify_scratch_bytes(long long nb);
+spdba_status launch_classify(const Geom& g, const double* msq, int msq_is_square, const double* tau, int force_dc,
+                             int transitions, int all_active, uint8_t* active, uint8_t* states, uint8_t* chi,
+                             int32_t* list, int32_t* count, void* scratch, DevStats* stats, cudaStream_t st);
+
+// Cahn-Hilliard update.  k2 tables: per axis (padded to 3 axes) |k_a|^2 in T.
+template <typename T> struct CHUpdateArgs {
+    cx_t<T>* c_hat;
+    const cx_t<T>* g_hat;
+    const T* k2ax[3];
+    const T* taper[3];
+    const uint8_t* states;
+    const uint8_t* chi;
+    const int32_t* list;
+    const int32_t* count;
+    T dt, dtkappa;
+    DevStats* stats;
+    double inv_nblocks;
+};
+template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdateArgs<T>& a, int dense, cudaStream_t st);
+
+// Per-axis |k|^2 table and taper table, computed in FP64 on the host.
+template <typename T> std::vector<T> k2_table(long long n, double dx);
+template <typename T> std::vector<T> taper_table(int B);
+
+}  // namespace spdba

@@ -1,0 +1,71 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/spdba.h"
+#include "fft_core.cuh"
+
+namespace spdba {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+spdba_status fail(spdba_status s, const char* fmt, ...);
+spdba_status cuda_fail(cudaError_t e, const char* what);
+#define SPDBA_CUDA(call)                                              \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::spdba::cuda_fail(e_, #call);  \
+    } while (0)
+
+// ------------------------------------------------------------------ FFT passes
+bool length_ok(int64_t n);              // 2^a 3^b
+bool tile_length_supported(int64_t L);  // has a pass kernel
+
+// Owner of device twiddle tables of one precision: exp(-2 pi i m / n), m < n,
+// computed in FP64 on the device and rounded to the element type.
+template <typename T> struct TwiddleCache {
+    std::map<int64_t, cx_t<T>*> tables;
+    cx_t<T>* get(int64_t n, cudaStream_t st, spdba_status* err);
+    void release();
+};
+
+template <typename T> struct Pass {
+    const void* func = nullptr;
+    int nt = 0, smem = 0;
+    long long grid = 0;
+    PassParams<T> p{};
+};
+
+// Build a pass of length L over pencils (O, I) with the given strides.
+template <typename T>
+spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O, long long I,
+                       long long isO, long long isI, long long isJ, long long osO, long long osI,
+                       long long osJ, TwiddleCache<T>& tw, cudaStream_t st);
+template <typename T> spdba_status launch_pass(const Pass<T>& ps, const void* in, void* out, cudaStream_t st);
+
+// A complete transform: list of passes (forward and inverse), scratch for the
+// out-of-place four-step second pass.
+template <typename T> struct FftEngine {
+    int ndim = 0;
+    int64_t dims[3] = {1, 1, 1};
+    int64_t batch = 1;
+    int64_t total = 0;  // elements per transform * batch
+    std::vector<Pass<T>> fwd, inv;
+    std::vector<int> fwd_scratch_out, inv_scratch_out;  // 1 if the pass writes to scratch
+    cx_t<T>* scratch = nullptr;
+    spdba_status init(int ndim, const int64_t* dims, int64_t batch, TwiddleCache<T>& tw, cudaStream_t st);
+    spdba_status exec(const cx_t<T>* in, cx_t<T>* out, int direction, cudaStream_t st);
+    void release();
+};
+
+// Pass along axis `axis` of `batch` contiguous arrays of shape dims (in place).
+template <typename T>
+spdba_status make_axis_pass(Pass<T>* out, int ndim, const int64_t* dims, int64_t batch, int axis, int sign,
+                            int mode, TwiddleCache<T>& tw, cudaStream_t st);
+
+}  // namespace spdba

@@ -1,0 +1,11 @@
+// Lookup of compiled pass kernels by (length, direction, mode, orientation).
+#pragma once
+#include <stdint.h>
+
+namespace spdba {
+struct KernelInfo {
+    const void* func = nullptr;
+    int P = 0, NT = 0, smem = 0;
+};
+template <typename T> bool get_pass_kernel(int64_t L, int sign, int mode, bool loadp, bool storep, KernelInfo* ki);
+}  // namespace spdba

@@ -1,0 +1,133 @@
+// Cahn-Hilliard semi-implicit Fourier update (conserved CH-form dynamics of
+// S3.1, semi-implicit update of S4.2 with M = 1):
+//     new(k) = (c_hat(k) - dt k^2 g_hat(k)) / (1 + dt kappa k^4)
+// Regular mode runs it on every mode; sp-DBA mode runs it only on the listed
+// (non-frozen) blocks: ACTIVE modes take new(k), TRANSITION modes take
+// c_hat + sigma(k) (new - c_hat) (S1.1, Eq. S.1), FROZEN modes are never read.
+#include <math.h>
+
+#include "blocks.h"
+
+namespace spdba {
+
+template <typename T> std::vector<T> k2_table(long long n, double dx) {
+    std::vector<T> v((size_t)n);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long long j = 0; j < n; ++j) {
+        long long jj = j <= n / 2 ? j : j - n;
+        double k = two_pi * (double)jj / ((double)n * dx);
+        v[(size_t)j] = (T)(k * k);
+    }
+    return v;
+}
+template <typename T> std::vector<T> taper_table(int B) {
+    std::vector<T> v((size_t)B);
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int i = 0; i < B; ++i) v[(size_t)i] = B < 2 ? (T)1 : (T)(0.5 * (1.0 - std::cos(pi * i / (double)(B - 1))));
+    return v;
+}
+template std::vector<float> k2_table<float>(long long, double);
+template std::vector<double> k2_table<double>(long long, double);
+template std::vector<float> taper_table<float>(int);
+template std::vector<double> taper_table<double>(int);
+
+// Evaluation order is pinned with explicit fma so that the Regular and the
+// sp-DBA kernels produce bit-identical values for the same mode.
+__device__ __forceinline__ float2 ch_new(float2 c, float2 g, float k2, float dt, float dtkappa) {
+    float den = __fmaf_rn(dtkappa, __fmul_rn(k2, k2), 1.0f);
+    float inv = __frcp_rn(den);
+    float a = __fmul_rn(dt, k2);
+    return make_float2(__fmul_rn(__fmaf_rn(-a, g.x, c.x), inv), __fmul_rn(__fmaf_rn(-a, g.y, c.y), inv));
+}
+__device__ __forceinline__ double2 ch_new(double2 c, double2 g, double k2, double dt, double dtkappa) {
+    double den = __fma_rn(dtkappa, __dmul_rn(k2, k2), 1.0);
+    double a = __dmul_rn(dt, k2);
+    return make_double2(__ddiv_rn(__fma_rn(-a, g.x, c.x), den), __ddiv_rn(__fma_rn(-a, g.y, c.y), den));
+}
+
+// Regular: every mode, two consecutive modes per thread along the fast axis.
+template <typename T>
+__global__ void ch_dense_kernel(Geom g, CHUpdateArgs<T> a) {
+    const long long npairs = g.modes() / 2;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) a.stats->ratio_sum += 1.0;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < npairs;
+         u += (long long)gridDim.x * blockDim.x) {
+        long long e = 2 * u;
+        long long x = e % g.n[2];
+        long long r = e / g.n[2];
+        long long y = r % g.n[1], z = r / g.n[1];
+        T kzy = a.k2ax[0][z] + a.k2ax[1][y];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            T k2 = kzy + a.k2ax[2][x + h];
+            a.c_hat[e + h] = ch_new(a.c_hat[e + h], __ldg(a.g_hat + e + h), k2, a.dt, a.dtkappa);
+        }
+    }
+}
+
+// sp-DBA: one warp per listed block.
+template <typename T>
+__global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int cnt = *a.count;
+    const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
+    const long long nmodes = (long long)B0 * B1 * B2;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
+        a.stats->ratio_sum += (double)cnt * a.inv_nblocks;
+        a.stats->list_modes += (double)cnt * (double)nmodes;
+    }
+    for (long long w = warp0; w < cnt; w += nwarps) {
+        long long blk = a.list[w];
+        const int st = a.states[blk];
+        const unsigned ch = a.chi[blk];
+        const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
+        // chi bits are numbered from the field's first axis
+        const int a0 = 3 - g.ndim;
+        for (long long m = lane; m < nmodes; m += 32) {
+            int l2 = (int)(m % B2);
+            long long rr = m / B2;
+            int l1 = (int)(rr % B1), l0 = (int)(rr / B1);
+            long long z = b0 * B0 + l0, y = b1 * B1 + l1, x = b2 * B2 + l2;
+            long long e = (z * g.n[1] + y) * g.n[2] + x;
+            T k2 = a.k2ax[0][z] + a.k2ax[1][y] + a.k2ax[2][x];
+            cx_t<T> c = a.c_hat[e];
+            cx_t<T> nw = ch_new(c, __ldg(a.g_hat + e), k2, a.dt, a.dtkappa);
+            if (st == SPDBA_TRANSITION) {
+                T sg = (T)1;
+                int l[3] = {l0, l1, l2};
+                int Bs[3] = {B0, B1, B2};
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (ax < a0) continue;
+                    unsigned lo = (ch >> (2 * (ax - a0))) & 1u, hi = (ch >> (2 * (ax - a0) + 1)) & 1u;
+                    if (lo) sg *= a.taper[ax][l[ax]];
+                    if (hi) sg *= a.taper[ax][Bs[ax] - 1 - l[ax]];
+                }
+                nw = mk<cx_t<T>>(c.x + sg * (nw.x - c.x), c.y + sg * (nw.y - c.y));
+            }
+            a.c_hat[e] = nw;
+        }
+    }
+}
+
+template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdateArgs<T>& a, int dense, cudaStream_t st) {
+    if (dense) {
+        long long npairs = g.modes() / 2;
+        long long grid = (npairs + 255) / 256;
+        if (grid > 152 * 16) grid = 152 * 16;
+        ch_dense_kernel<T><<<(unsigned)grid, 256, 0, st>>>(g, a);
+    } else {
+        long long nb = g.blocks();
+        long long grid = (nb * 32 + 255) / 256;
+        if (grid > 152 * 16) grid = 152 * 16;
+        ch_list_kernel<T><<<(unsigned)grid, 256, 0, st>>>(g, a);
+    }
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
+}
+template spdba_status launch_ch_update<float>(const Geom&, const CHUpdateArgs<float>&, int, cudaStream_t);
+template spdba_status launch_ch_update<double>(const Geom&, const CHUpdateArgs<double>&, int, cudaStream_t);
+
+}  // namespace spdba

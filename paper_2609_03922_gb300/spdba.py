@@ -1,0 +1,288 @@
+"""Thin Python binding of libspdba.so (include/spdba.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels.  PyTorch supplies
+device memory and the stream.  If the shared library has not been built this
+module raises at load time; there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libspdba.so")
+
+SPDBA_OK, SPDBA_ERR_ARG, SPDBA_ERR_UNSUPPORTED, SPDBA_ERR_CUDA, SPDBA_ERR_OOM, SPDBA_ERR_TIMEOUT, SPDBA_ERR_STATE = range(7)
+SPDBA_MODEL_CH, SPDBA_MODEL_NLS = 0, 1
+SPDBA_C64, SPDBA_C128 = 0, 1
+SPDBA_MODE_REGULAR, SPDBA_MODE_ADAPTIVE = 0, 1
+SPDBA_MEASURE_MAXAMP, SPDBA_MEASURE_ENERGY = 0, 1
+SPDBA_TAU_REL_MAX, SPDBA_TAU_ABS = 0, 1
+SPDBA_FROZEN, SPDBA_TRANSITION, SPDBA_ACTIVE = 0, 1, 2
+SPDBA_FORWARD, SPDBA_INVERSE = -1, 1
+
+
+class spdba_options(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("measure", ctypes.c_int32), ("tau_rule", ctypes.c_int32), ("transitions", ctypes.c_int32),
+                ("force_dc", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
+                ("warmup_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("dx", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("gamma", ctypes.c_double), ("h", ctypes.c_double),
+                ("dt_sample", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class spdba_stats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("assessments", ctypes.c_int64), ("nblocks", ctypes.c_int64),
+                ("n_active", ctypes.c_int64), ("n_transition", ctypes.c_int64), ("tau", ctypes.c_double),
+                ("max_amp", ctypes.c_double), ("mass", ctypes.c_double), ("active_ratio_sum", ctypes.c_double)]
+
+
+class spdba_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+# Every symbol include/spdba.h declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_S = ctypes.c_int
+SIGNATURES = {
+    "spdba_options_default": (None, [ctypes.POINTER(spdba_options)]),
+    "spdba_plan_create": (_S, [_PP, ctypes.c_int32, _I64P, _I32P, ctypes.c_double, ctypes.c_int32,
+                               ctypes.POINTER(spdba_options)]),
+    "spdba_batch_create": (_S, [_PP, ctypes.c_int32, ctypes.c_int32, _I64P, _I32P, ctypes.c_double,
+                                ctypes.c_int32, ctypes.POINTER(spdba_options)]),
+    "spdba_set_field": (_S, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "spdba_step": (_S, [_P, ctypes.c_int64]),
+    "spdba_get_field": (_S, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "spdba_get_spectrum": (_S, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "spdba_set_spectrum": (_S, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "spdba_get_mask": (_S, [_P, ctypes.c_int32, _P, ctypes.c_int64]),
+    "spdba_get_stats": (_S, [_P, ctypes.c_int32, ctypes.POINTER(spdba_stats)]),
+    "spdba_sync": (_S, [_P]),
+    "spdba_profile_begin": (_S, [_P]),
+    "spdba_profile_end": (_S, [_P, ctypes.POINTER(spdba_kernel_time), ctypes.c_int32, _I32P,
+                              ctypes.POINTER(ctypes.c_int64)]),
+    "spdba_plan_destroy": (None, [_P]),
+    "spdba_last_error": (ctypes.c_char_p, []),
+    "spdba_status_string": (ctypes.c_char_p, [_S]),
+    "spdba_fft_plan_create": (_S, [_PP, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.c_int64]),
+    "spdba_fft_exec": (_S, [_P, _P, _P, ctypes.c_int32, _P]),
+    "spdba_fft_plan_destroy": (None, [_P]),
+    "spdba_block_activity": (_S, [ctypes.c_int32, ctypes.c_int32, _I64P, _I32P, _P, _P, _P, _P, _P]),
+    "spdba_classify_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "spdba_classify": (_S, [ctypes.c_int32, _I64P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                            _P, _P]),
+}
+
+_lib = None
+
+
+class SpdbaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("spdba error %d: %s" % (status, msg))
+        self.status = status
+
+
+def lib():
+    """Load libspdba.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libspdba.so is not built (%s); run __graft_entry__.build() first" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != SPDBA_OK:
+        raise SpdbaError(status, lib().spdba_last_error().decode())
+
+
+def _i64(vals):
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _i32(vals):
+    return (ctypes.c_int32 * len(vals))(*[int(v) for v in vals])
+
+
+def _ptr(x):
+    """(pointer, on_device) of a torch tensor or numpy array (contiguous)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    raise TypeError("expected a numpy array or torch tensor")
+
+
+def current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def options_default(**kw):
+    o = spdba_options()
+    lib().spdba_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError("unknown option %s" % k)
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """One sp-DBA plan (spdba_plan_create / spdba_batch_create)."""
+
+    def __init__(self, dims, block, threshold=1e-6, reassess=10, batch_dims=None, stream=None, **opts):
+        o = options_default(**opts)
+        o.stream = current_stream() if stream is None else stream
+        self.opts = o
+        self._p = ctypes.c_void_p()
+        if batch_dims is None:
+            self.ndim = len(dims)
+            self.run_dims = [tuple(int(d) for d in dims)]
+            check(lib().spdba_plan_create(ctypes.byref(self._p), self.ndim, _i64(dims), _i32(block),
+                                          float(threshold), int(reassess), ctypes.byref(o)))
+        else:
+            self.ndim = len(batch_dims[0])
+            self.run_dims = [tuple(int(d) for d in r) for r in batch_dims]
+            flat = [d for r in self.run_dims for d in r]
+            check(lib().spdba_batch_create(ctypes.byref(self._p), len(self.run_dims), self.ndim, _i64(flat),
+                                           _i32(block), float(threshold), int(reassess), ctypes.byref(o)))
+        self.block = tuple(block)
+        self.complex_dtype = np.complex64 if o.precision == SPDBA_C64 else np.complex128
+        self.real_dtype = np.float32 if o.precision == SPDBA_C64 else np.float64
+
+    def close(self):
+        if self._p:
+            lib().spdba_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_field(self, x, run=0):
+        p, dev = _ptr(x)
+        check(lib().spdba_set_field(self._p, run, p, dev))
+
+    def step(self, n=1):
+        check(lib().spdba_step(self._p, int(n)))
+
+    def sync(self):
+        check(lib().spdba_sync(self._p))
+
+    def field_dtype(self):
+        return self.real_dtype if self.opts.model == SPDBA_MODEL_CH else self.complex_dtype
+
+    def get_field(self, out=None, run=0):
+        if out is None:
+            out = np.empty(self.run_dims[run], dtype=self.field_dtype())
+        p, dev = _ptr(out)
+        check(lib().spdba_get_field(self._p, run, p, dev))
+        return out
+
+    def get_spectrum(self, out=None, run=0):
+        if out is None:
+            out = np.empty(self.run_dims[run], dtype=self.complex_dtype)
+        p, dev = _ptr(out)
+        check(lib().spdba_get_spectrum(self._p, run, p, dev))
+        return out
+
+    def set_spectrum(self, x, run=0):
+        p, dev = _ptr(x)
+        check(lib().spdba_set_spectrum(self._p, run, p, dev))
+
+    def nblocks_shape(self, run=0):
+        if self.opts.model == SPDBA_MODEL_NLS and self.block[0] <= 0:
+            return (-self.block[0],)
+        return tuple(d // b for d, b in zip(self.run_dims[run], self.block))
+
+    def get_mask(self, run=0):
+        shape = self.nblocks_shape(run)
+        out = np.empty(shape, dtype=np.uint8)
+        check(lib().spdba_get_mask(self._p, run, out.ctypes.data, out.size))
+        return out
+
+    def profile_begin(self):
+        check(lib().spdba_profile_begin(self._p))
+
+    def profile_end(self):
+        """Returns ({kind: {launches, total_ms, bytes}}, kernel launches since begin)."""
+        buf = (spdba_kernel_time * 16)()
+        n = ctypes.c_int32()
+        launches = ctypes.c_int64()
+        check(lib().spdba_profile_end(self._p, buf, 16, ctypes.byref(n), ctypes.byref(launches)))
+        out = {}
+        for i in range(n.value):
+            k = buf[i]
+            out[k.name.decode()] = {"launches": int(k.launches), "total_ms": float(k.total_ms), "bytes": float(k.bytes)}
+        return out, int(launches.value)
+
+    def get_stats(self, run=0):
+        s = spdba_stats()
+        check(lib().spdba_get_stats(self._p, run, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in spdba_stats._fields_}
+
+
+class FFTPlan:
+    """Batched multi-dimensional FFT (spdba_fft_plan_create / spdba_fft_exec)."""
+
+    def __init__(self, dims, batch=1, precision=SPDBA_C64):
+        self._p = ctypes.c_void_p()
+        check(lib().spdba_fft_plan_create(ctypes.byref(self._p), precision, len(dims), _i64(dims), int(batch)))
+
+    def exec(self, x, out, direction, stream=None):
+        pin, _ = _ptr(x)
+        pout, _ = _ptr(out)
+        check(lib().spdba_fft_exec(self._p, pin, pout, direction, current_stream() if stream is None else stream))
+
+    def close(self):
+        if self._p:
+            lib().spdba_fft_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def block_activity(q, block, maxsq, sumsq, gmax, precision=SPDBA_C64, stream=None):
+    check(lib().spdba_block_activity(precision, q.dim(), _i64(q.shape), _i32(block), q.data_ptr(),
+                                     maxsq.data_ptr(), sumsq.data_ptr() if sumsq is not None else None,
+                                     gmax.data_ptr(), current_stream() if stream is None else stream))
+
+
+def classify_scratch_bytes(nb):
+    return int(lib().spdba_classify_scratch_bytes(int(nb)))
+
+
+def classify(nblocks, measure, tau, force_dc, transitions, states, chi, lst, count, scratch, stream=None):
+    check(lib().spdba_classify(len(nblocks), _i64(nblocks), measure.data_ptr(), tau.data_ptr(), int(force_dc),
+                               int(transitions), states.data_ptr(), chi.data_ptr(), lst.data_ptr(),
+                               count.data_ptr(), scratch.data_ptr(),
+                               current_stream() if stream is None else stream))

@@ -1,0 +1,102 @@
+"""GPU block activity and classification/compaction against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _rand(shape, seed, dtype, scale_blocks=None):
+    r = np.random.default_rng(seed)
+    x = (r.standard_normal(shape) + 1j * r.standard_normal(shape))
+    if scale_blocks is not None:
+        # give blocks wildly different magnitudes, like a decaying spectrum
+        x = x * scale_blocks
+    return x.astype(dtype)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape,block", [((64, 64), (16, 16)), ((32, 32, 32), (8, 8, 8)), ((4096,), (64,)),
+                                         ((48, 96), (16, 8)), ((256, 256, 256), (8, 8, 8))])
+def test_block_activity_matches_oracle(shape, block, precision):
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    if precision == 1 and np.prod(shape) > 1 << 20:
+        pytest.skip("full-size case runs in complex64 only")
+    cdt = np.complex64 if precision == 0 else np.complex128
+    r = np.random.default_rng(3)
+    scale = np.exp(-6 * r.random(shape))
+    q = _rand(shape, 1, cdt, scale)
+    nb = tuple(s // b for s, b in zip(shape, block))
+    qd = torch.from_numpy(q).cuda()
+    maxsq = torch.empty(nb, dtype=torch.float64, device="cuda")
+    sumsq = torch.empty(nb, dtype=torch.float64, device="cuda")
+    gmax = torch.empty(2, dtype=torch.float64, device="cuda")
+    spdba.block_activity(qd, block, maxsq, sumsq, gmax, precision=precision)
+    torch.cuda.synchronize()
+    q64 = q.astype(np.complex128)
+    mx, sm = O.block_measures(q64, block)
+    assert np.array_equal(maxsq.cpu().numpy(), mx)            # same FP64 formula: bit-exact
+    assert np.allclose(sumsq.cpu().numpy(), sm, rtol=1e-12, atol=0)
+    g = gmax.cpu().numpy()
+    assert g[0] == O.global_max_sq(q64, exclude_dc=False)
+    assert g[1] == O.global_max_sq(q64, exclude_dc=True)
+
+
+def _expected_chi(states):
+    d = states.ndim
+    chi = np.zeros(states.shape, dtype=np.uint8)
+    for a in range(d):
+        lo = np.roll(states, 1, axis=a) == O.STATE_FROZEN
+        hi = np.roll(states, -1, axis=a) == O.STATE_FROZEN
+        chi |= (lo.astype(np.uint8) << (2 * a)) | (hi.astype(np.uint8) << (2 * a + 1))
+    return chi
+
+
+@pytest.mark.parametrize("nb", [(4, 4), (8, 8), (1, 8), (64,), (3, 5, 7), (32, 32, 32), (48, 48, 48)])
+@pytest.mark.parametrize("force_dc,transitions", [(1, 1), (0, 1), (1, 0)])
+def test_classify_matches_oracle(nb, force_dc, transitions):
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    r = np.random.default_rng(sum(nb))
+    meas = np.exp(-8 * r.random(nb))
+    tau = float(np.quantile(meas, 0.9))
+    meas.flat[r.integers(0, meas.size)] = tau          # an exact tie: >= makes it active
+    n = meas.size
+    md = torch.from_numpy(meas).cuda()
+    td = torch.tensor([tau], dtype=torch.float64, device="cuda")
+    states = torch.empty(n, dtype=torch.uint8, device="cuda")
+    chi = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lst = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+    scratch = torch.empty(spdba.classify_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    spdba.classify(nb, md, td, force_dc, transitions, states, chi, lst, cnt, scratch)
+    torch.cuda.synchronize()
+    ref = O.classify(meas, tau, force_dc=bool(force_dc), transitions=bool(transitions))
+    got = states.cpu().numpy().reshape(nb)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(chi.cpu().numpy().reshape(nb)[ref == O.STATE_TRANSITION],
+                          _expected_chi(ref)[ref == O.STATE_TRANSITION])
+    ids = np.flatnonzero(ref.ravel() != O.STATE_FROZEN)
+    c = int(cnt.item())
+    assert c == ids.size
+    assert np.array_equal(lst.cpu().numpy()[:c], ids)
+
+
+def test_classify_all_frozen_and_all_active():
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    nb = (16, 16)
+    n = 256
+    for tau, expect_count in [(np.inf, 0), (0.0, n)]:
+        md = torch.zeros(n, dtype=torch.float64, device="cuda")
+        td = torch.tensor([tau], dtype=torch.float64, device="cuda")
+        states = torch.empty(n, dtype=torch.uint8, device="cuda")
+        chi = torch.empty(n, dtype=torch.uint8, device="cuda")
+        lst = torch.empty(n, dtype=torch.int32, device="cuda")
+        cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+        scratch = torch.empty(spdba.classify_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+        spdba.classify(nb, md, td, 0, 1, states, chi, lst, cnt, scratch)
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == expect_count

@@ -1,0 +1,129 @@
+"""Adaptive and Regular Cahn-Hilliard on the GPU against the oracle, through the C ABI.
+
+Masks: at every reassessment the GPU's spectrum (promoted to FP64) goes
+through the oracle's classifier and must give the GPU's states, blocks in
+the 1e-6 tie band excepted (lock-step).  Fields: the oracle re-runs the same
+steps in FP64 with the GPU's (checked) states, so the comparison measures
+arithmetic error only.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from _helpers import states_within_tie_band
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(dims, block, steps, precision, c0, **kw):
+    from paper_2609_03922_gb300 import spdba
+    R = kw.pop("reassess", 10)
+    thr = kw.pop("threshold", 1e-6)
+    rdt = np.float32 if precision == 0 else np.float64
+    plan = spdba.Plan(dims, block, threshold=thr, reassess=R, precision=precision, **kw)
+    plan.set_field(np.ascontiguousarray(c0.astype(rdt)))
+    masks, spectra = {}, {}
+    mode = kw.get("mode", 1)
+    for s in range(steps):
+        if mode == 1 and s % R == 0:
+            spectra[s] = plan.get_spectrum()
+            plan.step(1)
+            masks[s] = plan.get_mask()
+        else:
+            plan.step(1)
+    field = plan.get_field()
+    stats = plan.get_stats()
+    spec = plan.get_spectrum()
+    plan.close()
+    return field, spec, masks, spectra, stats
+
+
+def oracle_cfg(dims, block, **kw):
+    kw = dict(kw)
+    kw.pop("precision", None)
+    kw.pop("use_graph", None)
+    return O.CHConfig(dims, block, **kw)
+
+
+def check_run(dims, block, steps, precision, c0, tol, **kw):
+    field, spec, masks, spectra, stats = run_gpu(dims, block, steps, precision, c0, **kw)
+    cfg = oracle_cfg(dims, block, **kw)
+    # lock-step masks on the GPU's own spectrum
+    for s, sp in spectra.items():
+        st, tau, meas = O.assess_states(sp.astype(np.complex128), cfg, exclude_dc=True)
+        ok, nties = states_within_tie_band(masks[s], meas, tau, cfg)
+        assert ok, "step %d: GPU block states differ from the oracle's (%d tie-band blocks)" % (s, nties)
+    # oracle with the GPU's states
+    rdt = np.float32 if precision == 0 else np.float64
+    c0r = c0.astype(rdt).astype(np.float64)
+    ref_hat, _ = O.run_ch(c0r, cfg, steps, on_assess=lambda n, ch, st, tau: masks[n] if n in masks else None)
+    ref = O.ch_real_field(ref_hat)
+    err = O.rel_l2(field, ref)
+    assert err <= tol, "rel-L2 %.3e > %.1e" % (err, tol)
+    return field, spec, stats, err, spectra
+
+
+def test_config1_2d_128_fp64_full_run():
+    """2-D CH 128^2, FP64, 16^2 blocks, tau = 1e-6 max|c_hat|, R = 10, 200 steps."""
+    dims, block = (128, 128), (16, 16)
+    c0 = W.ch_initial_condition(dims, mean=0.0, amplitude=0.05, seed=W.BASE_SEED)
+    check_run(dims, block, 200, 1, c0, 1e-10)
+
+
+@pytest.mark.parametrize("precision,tol1", [(0, 1e-5), (1, 1e-12)])
+def test_one_step_3d(precision, tol1):
+    dims, block = (64, 64, 64), (8, 8, 8)
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 1)
+    check_run(dims, block, 1, precision, c0, tol1)
+
+
+def test_3d_fp32_many_steps_with_fp64_norms():
+    dims, block = (64, 64, 64), (8, 8, 8)
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 2)
+    _, spec, stats, _, spectra = check_run(dims, block, 120, 0, c0, 1e-4)
+    # k = 0 is never touched by the update: bit-identical to its value after set_field
+    assert spec[0, 0, 0] == spectra[0][0, 0, 0]
+    c0r = c0.astype(np.float32).astype(np.float64)
+    assert abs(spec[0, 0, 0].real - np.sum(c0r)) <= 1e-6 * abs(np.sum(c0r))
+    # FP64 mass of the real field at the last reassessment
+    assert abs(stats["mass"] - np.sum(c0r)) <= 1e-6 * abs(np.sum(c0r))
+    assert stats["assessments"] == 12
+
+
+@pytest.mark.parametrize("opts", [dict(transitions=0), dict(measure=1), dict(reassess=1),
+                                  dict(refresh_every=7, warmup_steps=3), dict(force_dc=0, threshold=1e-3)])
+def test_options_2d(opts):
+    dims, block = (64, 128), (16, 16)
+    c0 = W.ch_initial_condition(dims, mean=0.2, seed=W.BASE_SEED + 3)
+    check_run(dims, block, 25, 1, c0, 1e-11, **opts)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_threshold_zero_equals_regular_on_gpu(precision):
+    dims, block = (32, 32, 32), (8, 8, 8)
+    c0 = W.ch_initial_condition(dims, mean=0.0, seed=W.BASE_SEED + 4)
+    a = run_gpu(dims, block, 15, precision, c0, threshold=0.0, reassess=4)
+    b = run_gpu(dims, block, 15, precision, c0, mode=0)
+    assert np.array_equal(a[1], b[1])
+    assert all(np.all(m == 2) for m in a[2].values())
+
+
+def test_zero_field_stays_zero():
+    dims, block = (32, 32), (8, 8)
+    field, spec, masks, _, stats = run_gpu(dims, block, 5, 0, np.zeros(dims))
+    assert not np.any(field) and not np.any(spec)
+    assert all(np.all(m == 2) for m in masks.values())   # tau = 0 * 0: every block meets it
+
+
+@pytest.mark.parametrize("shape,block", [((192, 384), (16, 16)), ((512, 512), (16, 16)), ((32, 192, 64), (8, 8, 8))])
+def test_ragged_radix3_and_large_2d(shape, block):
+    c0 = W.ch_initial_condition(shape, mean=0.05, seed=W.BASE_SEED + 5)
+    check_run(shape, block, 12, 0, c0, 1e-5)
+
+
+def test_full_size_256cubed_fp32():
+    """The benchmark workload: 3-D CH 256^3, complex64, 8^3 blocks, R = 10."""
+    dims, block = (256, 256, 256), (8, 8, 8)
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED)
+    check_run(dims, block, 11, 0, c0, 1e-5)
