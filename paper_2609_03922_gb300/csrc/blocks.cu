@@ -26,28 +26,15 @@ spdba_status make_geom(Geom* g, int ndim, const int64_t* dims, const int32_t* bl
 }
 
 // ------------------------------------------------------------------ activity
-// One CTA per block.  |q|^2 is formed in FP64 from the stored values
-// (exact squares of FP32 components), max- and sum-reduced per thread, then
-// across the warp with shuffles and across warps through shared memory.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T>* __restrict__ q,
-                                                            double* __restrict__ maxsq, double* __restrict__ sumsq,
-                                                            double* __restrict__ gmax) {
-    const long long blk = blockIdx.x;
-    const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
-    const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
-    const long long nmodes = (long long)B0 * B1 * B2;
-    double mx = 0.0, mxnd = 0.0, sm = 0.0;
-    for (long long m = threadIdx.x; m < nmodes; m += NT) {
-        int l2 = (int)(m % B2);
-        long long r = m / B2;
-        int l1 = (int)(r % B1), l0 = (int)(r / B1);
-        long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
-        double s = mode_sq(__ldg(q + idx));
-        mx = fmax(mx, s);
-        if (idx != 0) mxnd = fmax(mxnd, s);
-        sm += s;
-    }
+// One CTA per block.  The block max of |q|^2 is exact in FP64: an FP32 value
+// p32 = fma(re, re, im*im) (relative error below 2^-22) screens each mode, and
+// only modes whose p32 reaches (1 - 2^-20) times the running FP64 max are
+// evaluated exactly (re*re + im*im in FP64, the oracle's formula), so a mode
+// that is skipped cannot be the max.  The block sum (ENERGY) is accumulated in
+// FP64.  Results are reduced over the warp with shuffles and across warps in
+// shared memory.
+template <int NT> __device__ __forceinline__ void reduce_store(double mx, double mxnd, double sm, long long blk,
+                                                               double* maxsq, double* sumsq, double* gmax) {
     mx = warp_max(mx);
     mxnd = warp_max(mxnd);
     sm = warp_sum(sm);
@@ -71,12 +58,69 @@ __global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T
     }
 }
 
+__device__ __forceinline__ void screen_mode(float2 v, long long idx, bool energy, double& mx, double& mxnd,
+                                            float& cut, double& sm) {
+    if (energy) sm += mode_sq(v);
+    float p32 = fmaf(v.x, v.x, v.y * v.y);
+    if (idx == 0) {
+        mx = fmax(mx, mode_sq(v));
+    } else if (p32 >= cut) {
+        double e = mode_sq(v);
+        mx = fmax(mx, e);
+        mxnd = fmax(mxnd, e);
+        cut = (float)mxnd * (1.0f - 9.5367431640625e-07f);   // 1 - 2^-20
+    }
+}
+__device__ __forceinline__ void screen_mode(double2 v, long long idx, bool energy, double& mx, double& mxnd,
+                                            float& cut, double& sm) {
+    double e = mode_sq(v);
+    if (energy) sm += e;
+    mx = fmax(mx, e);
+    if (idx != 0) mxnd = fmax(mxnd, e);
+}
+
+template <typename T, int NT, bool ENERGY>
+__global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T>* __restrict__ q,
+                                                            double* __restrict__ maxsq, double* __restrict__ sumsq,
+                                                            double* __restrict__ gmax) {
+    const long long blk = blockIdx.x;
+    const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
+    const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
+    double mx = 0.0, mxnd = 0.0, sm = 0.0;
+    float cut = 0.0f;
+    if (sizeof(cx_t<T>) == 8 && (B2 & 1) == 0) {
+        // pairs along the fast axis as one 16-byte load
+        const int H = B2 / 2;
+        const long long npair = (long long)B0 * B1 * H;
+        for (long long m = threadIdx.x; m < npair; m += NT) {
+            int l2 = (int)(m % H) * 2;
+            long long r = m / H;
+            int l1 = (int)(r % B1), l0 = (int)(r / B1);
+            long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
+            float4 v = __ldg(reinterpret_cast<const float4*>(q + idx));
+            screen_mode(make_float2(v.x, v.y), idx, ENERGY, mx, mxnd, cut, sm);
+            screen_mode(make_float2(v.z, v.w), idx + 1, ENERGY, mx, mxnd, cut, sm);
+        }
+    } else {
+        const long long nmodes = (long long)B0 * B1 * B2;
+        for (long long m = threadIdx.x; m < nmodes; m += NT) {
+            int l2 = (int)(m % B2);
+            long long r = m / B2;
+            int l1 = (int)(r % B1), l0 = (int)(r / B1);
+            long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
+            screen_mode(__ldg(q + idx), idx, ENERGY, mx, mxnd, cut, sm);
+        }
+    }
+    reduce_store<NT>(mx, mxnd, sm, blk, maxsq, sumsq, gmax);
+}
+
 template <typename T>
 spdba_status launch_block_activity(const Geom& g, const cx_t<T>* q, double* maxsq, double* sumsq, double* gmax,
                                    cudaStream_t st) {
     constexpr int NT = 128;
     long long nb = g.blocks();
-    block_activity_kernel<T, NT><<<(unsigned)nb, NT, 0, st>>>(g, q, maxsq, sumsq, gmax);
+    if (sumsq) block_activity_kernel<T, NT, true><<<(unsigned)nb, NT, 0, st>>>(g, q, maxsq, sumsq, gmax);
+    else block_activity_kernel<T, NT, false><<<(unsigned)nb, NT, 0, st>>>(g, q, maxsq, nullptr, gmax);
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;
 }

@@ -94,10 +94,25 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     if (loadp && isI != 1) return fail(SPDBA_ERR_UNSUPPORTED, "pass without a unit-stride input direction");
     if (storep && osI != 1) return fail(SPDBA_ERR_UNSUPPORTED, "pass without a unit-stride output direction");
     KernelInfo ki;
-    if (!get_pass_kernel<T>(L, sign, mode, loadp, storep, &ki))
+    // the tile size depends only on (T, L); ask once to learn P
+    if (!get_pass_kernel<T>(L, sign, mode, loadp, storep, true, &ki))
+        return fail(SPDBA_ERR_UNSUPPORTED, "no FFT pass kernel for length %lld (mode %d)", (long long)L, mode);
+    const bool generic = (I % ki.P) != 0;
+    if (!get_pass_kernel<T>(L, sign, mode, loadp, storep, generic, &ki))
         return fail(SPDBA_ERR_UNSUPPORTED, "no FFT pass kernel for length %lld (mode %d)", (long long)L, mode);
     spdba_status s = ensure_smem_attr(ki.func, ki.smem);
     if (s != SPDBA_OK) return s;
+    long long ntiles = (O * I + ki.P - 1) / ki.P;
+    long long grid = ntiles;
+    if (ki.pipe) {
+        int per_sm = 0, nsm = 0, dev = 0;
+        SPDBA_CUDA(cudaGetDevice(&dev));
+        SPDBA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        SPDBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.func, ki.NT, ki.smem));
+        if (per_sm < 1) per_sm = 1;
+        long long resident = (long long)per_sm * nsm;
+        if (grid > resident) grid = resident;
+    }
     s = SPDBA_OK;
     cx_t<T>* t = tw.get(L, st, &s);
     if (!t) return s;
@@ -105,7 +120,7 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     ps.func = ki.func;
     ps.nt = ki.NT;
     ps.smem = ki.smem;
-    ps.grid = (O * I + ki.P - 1) / ki.P;
+    ps.grid = grid;
     ps.p.O = O; ps.p.I = I;
     ps.p.isO = isO; ps.p.isI = isI; ps.p.isJ = isJ;
     ps.p.osO = osO; ps.p.osI = osI; ps.p.osJ = osJ;
@@ -113,7 +128,7 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     ps.p.tw4 = nullptr;
     ps.p.n4 = 1;
     ps.p.scale = (T)1;
-    ps.p.generic = (I % ki.P) != 0;
+    ps.p.generic = generic;
     ps.p.nl_scale = (T)1;
     ps.p.mass = nullptr;
     *out = ps;

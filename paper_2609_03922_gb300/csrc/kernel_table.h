@@ -6,6 +6,9 @@ namespace spdba {
 struct KernelInfo {
     const void* func = nullptr;
     int P = 0, NT = 0, smem = 0;
+    bool pipe = false;  // persistent, double-buffered kernel: grid = resident CTAs
 };
-template <typename T> bool get_pass_kernel(int64_t L, int sign, int mode, bool loadp, bool storep, KernelInfo* ki);
+// generic: the pencil count is not a multiple of the tile (simple kernel only)
+template <typename T>
+bool get_pass_kernel(int64_t L, int sign, int mode, bool loadp, bool storep, bool generic, KernelInfo* ki);
 }  // namespace spdba

@@ -214,7 +214,8 @@ template <typename T> static spdba_status run_assess(spdba_plan* p, Run<T>& r) {
     double* gmax = r.dbl;
     double* tau = r.dbl + 2;
     zero_double_kernel<<<1, 32, 0, st>>>(gmax, 2);
-    if ((s = launch_block_activity<T>(r.g, r.c_hat, r.maxsq, r.sumsq, gmax, st)) != SPDBA_OK) return s;
+    double* sumsq = p->opt.measure == SPDBA_MEASURE_ENERGY ? r.sumsq : nullptr;
+    if ((s = launch_block_activity<T>(r.g, r.c_hat, r.maxsq, sumsq, gmax, st)) != SPDBA_OK) return s;
     int exclude_dc = p->opt.model == SPDBA_MODEL_CH ? 1 : 0;
     if ((s = launch_tau(gmax, p->threshold, p->opt.tau_rule, exclude_dc, tau, r.stats, st)) != SPDBA_OK) return s;
     const double* msq = p->opt.measure == SPDBA_MEASURE_ENERGY ? r.sumsq : r.maxsq;

@@ -45,6 +45,19 @@ __device__ __forceinline__ double2 ch_new(double2 c, double2 g, double k2, doubl
     return make_double2(__ddiv_rn(__fma_rn(-a, g.x, c.x), den), __ddiv_rn(__fma_rn(-a, g.y, c.y), den));
 }
 
+// Two consecutive modes along the fast axis move together (one 16-byte access
+// for complex64).
+__device__ __forceinline__ void load2(const float2* p, float2& a, float2& b) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void store2(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void load2(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
+__device__ __forceinline__ void store2(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
+
 // Regular: every mode, two consecutive modes per thread along the fast axis.
 template <typename T>
 __global__ void ch_dense_kernel(Geom g, CHUpdateArgs<T> a) {
@@ -57,15 +70,32 @@ __global__ void ch_dense_kernel(Geom g, CHUpdateArgs<T> a) {
         long long r = e / g.n[2];
         long long y = r % g.n[1], z = r / g.n[1];
         T kzy = a.k2ax[0][z] + a.k2ax[1][y];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            T k2 = kzy + a.k2ax[2][x + h];
-            a.c_hat[e + h] = ch_new(a.c_hat[e + h], __ldg(a.g_hat + e + h), k2, a.dt, a.dtkappa);
-        }
+        cx_t<T> c0, c1, g0, g1;
+        load2(a.c_hat + e, c0, c1);
+        load2(a.g_hat + e, g0, g1);
+        c0 = ch_new(c0, g0, kzy + a.k2ax[2][x], a.dt, a.dtkappa);
+        c1 = ch_new(c1, g1, kzy + a.k2ax[2][x + 1], a.dt, a.dtkappa);
+        store2(a.c_hat + e, c0, c1);
     }
 }
 
-// sp-DBA: one warp per listed block.
+template <typename T>
+__device__ __forceinline__ cx_t<T> ch_blend(cx_t<T> c, cx_t<T> nw, const CHUpdateArgs<T>& a, const Geom& g,
+                                            unsigned ch, int l0, int l1, int l2) {
+    const int a0 = 3 - g.ndim;
+    int l[3] = {l0, l1, l2};
+    T sg = (T)1;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax < a0) continue;
+        unsigned lo = (ch >> (2 * (ax - a0))) & 1u, hi = (ch >> (2 * (ax - a0) + 1)) & 1u;
+        if (lo) sg *= a.taper[ax][l[ax]];
+        if (hi) sg *= a.taper[ax][g.b[ax] - 1 - l[ax]];
+    }
+    return mk<cx_t<T>>(c.x + sg * (nw.x - c.x), c.y + sg * (nw.y - c.y));
+}
+
+// sp-DBA: one warp per listed block, mode pairs along the fast axis.
 template <typename T>
 __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
     const int lane = threadIdx.x & 31;
@@ -78,36 +108,30 @@ __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
         a.stats->ratio_sum += (double)cnt * a.inv_nblocks;
         a.stats->list_modes += (double)cnt * (double)nmodes;
     }
+    const int H = B2 / 2;
+    const long long npair = nmodes / 2;
     for (long long w = warp0; w < cnt; w += nwarps) {
         long long blk = a.list[w];
         const int st = a.states[blk];
         const unsigned ch = a.chi[blk];
         const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
-        // chi bits are numbered from the field's first axis
-        const int a0 = 3 - g.ndim;
-        for (long long m = lane; m < nmodes; m += 32) {
-            int l2 = (int)(m % B2);
-            long long rr = m / B2;
+        for (long long m = lane; m < npair; m += 32) {
+            int l2 = (int)(m % H) * 2;
+            long long rr = m / H;
             int l1 = (int)(rr % B1), l0 = (int)(rr / B1);
             long long z = b0 * B0 + l0, y = b1 * B1 + l1, x = b2 * B2 + l2;
             long long e = (z * g.n[1] + y) * g.n[2] + x;
-            T k2 = a.k2ax[0][z] + a.k2ax[1][y] + a.k2ax[2][x];
-            cx_t<T> c = a.c_hat[e];
-            cx_t<T> nw = ch_new(c, __ldg(a.g_hat + e), k2, a.dt, a.dtkappa);
+            T kzy = a.k2ax[0][z] + a.k2ax[1][y];
+            cx_t<T> c0, c1, g0, g1;
+            load2(a.c_hat + e, c0, c1);
+            load2(a.g_hat + e, g0, g1);
+            cx_t<T> n0 = ch_new(c0, g0, kzy + a.k2ax[2][x], a.dt, a.dtkappa);
+            cx_t<T> n1 = ch_new(c1, g1, kzy + a.k2ax[2][x + 1], a.dt, a.dtkappa);
             if (st == SPDBA_TRANSITION) {
-                T sg = (T)1;
-                int l[3] = {l0, l1, l2};
-                int Bs[3] = {B0, B1, B2};
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    if (ax < a0) continue;
-                    unsigned lo = (ch >> (2 * (ax - a0))) & 1u, hi = (ch >> (2 * (ax - a0) + 1)) & 1u;
-                    if (lo) sg *= a.taper[ax][l[ax]];
-                    if (hi) sg *= a.taper[ax][Bs[ax] - 1 - l[ax]];
-                }
-                nw = mk<cx_t<T>>(c.x + sg * (nw.x - c.x), c.y + sg * (nw.y - c.y));
+                n0 = ch_blend<T>(c0, n0, a, g, ch, l0, l1, l2);
+                n1 = ch_blend<T>(c1, n1, a, g, ch, l0, l1, l2 + 1);
             }
-            a.c_hat[e] = nw;
+            store2(a.c_hat + e, n0, n1);
         }
     }
 }

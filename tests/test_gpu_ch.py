@@ -127,3 +127,37 @@ def test_full_size_256cubed_fp32():
     dims, block = (256, 256, 256), (8, 8, 8)
     c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED)
     check_run(dims, block, 11, 0, c0, 1e-5)
+
+
+def test_fp32_full_step_count_at_64cubed():
+    """Precision form over the configuration's full 2000 steps (at 64^3, where the
+    FP64 oracle finishes): rel-L2 <= 1e-4 against FP64 with the same states."""
+    dims, block = (64, 64, 64), (8, 8, 8)
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 7)
+    check_run(dims, block, 2000, 0, c0, 1e-4)
+
+
+def test_uneven_ensemble_plan_matches_per_run_oracle():
+    """One plan holding runs of different sizes (the ensemble form) steps each run
+    exactly like the oracle would."""
+    from paper_2609_03922_gb300 import spdba
+    sizes = [(128, 128), (192, 192), (256, 256)]
+    means = [0.1, -0.15, 0.0]
+    c0s = [W.ch_initial_condition(s, mean=m, seed=W.BASE_SEED + 10 + i) for i, (s, m) in enumerate(zip(sizes, means))]
+    plan = spdba.Plan(None, (16, 16), threshold=1e-6, reassess=5, batch_dims=sizes, precision=0)
+    for r, c0 in enumerate(c0s):
+        plan.set_field(np.ascontiguousarray(c0.astype(np.float32)), run=r)
+    steps = 20
+    masks = [dict() for _ in sizes]
+    for s in range(steps):
+        plan.step(1)
+        if s % 5 == 0:
+            for r in range(len(sizes)):
+                masks[r][s] = plan.get_mask(run=r)
+    for r, (dims, c0) in enumerate(zip(sizes, c0s)):
+        got = plan.get_field(run=r)
+        cfg = O.CHConfig(dims, (16, 16), threshold=1e-6, reassess=5)
+        ref_hat, hist = O.run_ch(c0.astype(np.float32).astype(np.float64), cfg, steps,
+                                 on_assess=lambda n, ch, st, tau, r=r: masks[r][n])
+        assert O.rel_l2(got, O.ch_real_field(ref_hat)) <= 1e-5
+    plan.close()
