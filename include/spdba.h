@@ -221,6 +221,31 @@ spdba_status spdba_classify(int32_t ndim, const int64_t* nblocks, const double* 
                             uint8_t* states, uint8_t* chi, int32_t* list, int32_t* count,
                             void* scratch, void* stream);
 
+/*
+ * spdba_classify without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- for
+ * example code that runs under a framework which owns every device buffer and
+ * hands out only the inputs and outputs, or a fixed-footprint service loop
+ * where any cudaMalloc is forbidden after start-up.
+ *
+ * Same arguments and results as spdba_classify, minus `scratch`: the scratch
+ * is a fixed array of about 1 MiB compiled into the library (every GPU that
+ * loads the library holds it until the process exits).  At most
+ * SPDBA_CLASSIFY_STATIC_MAX_BLOCKS blocks; larger maps return
+ * SPDBA_ERR_UNSUPPORTED.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Calls never call cudaMalloc or
+ * cudaFree.  All calls share the one array and it keeps the previous call's
+ * contents (nothing in it needs to start at zero: each call writes what it
+ * reads), so calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race: serialize them.
+ */
+#define SPDBA_CLASSIFY_STATIC_MAX_BLOCKS (1 << 20)
+spdba_status spdba_classify_static(int32_t ndim, const int64_t* nblocks, const double* measure,
+                                   const double* tau, int32_t force_dc, int32_t transitions,
+                                   uint8_t* states, uint8_t* chi, int32_t* list, int32_t* count,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -322,3 +322,62 @@ extern "C" spdba_status spdba_classify(int32_t ndim, const int64_t* nblocks, con
     return launch_classify(g, measure, 0, tau, force_dc, transitions, 0, active, states, chi, list, count, scratch,
                            nullptr, (cudaStream_t)stream);
 }
+
+// ------------------------------------------------------------------ classify without allocation
+// Variant of spdba_classify whose scratch (per-CTA counts and one flag per
+// block) lives in a fixed array compiled into the library, for callers that
+// cannot allocate device memory.  The array is a file-scope __device__
+// variable; host code obtains its device address with cudaGetSymbolAddress
+// once per device (the name itself is only a host-side stand-in).
+#include <mutex>
+
+#define SPDBA_STATIC_SCRATCH_BYTES ((size_t)SPDBA_CLASSIFY_STATIC_MAX_BLOCKS + \
+                                    sizeof(int) * (size_t)(SPDBA_CLASSIFY_STATIC_MAX_BLOCKS / 1024))
+
+static __device__ __align__(256) unsigned char g_classify_scratch[SPDBA_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+static spdba_status static_scratch_for_current_device(void** out) {
+    int dev = 0;
+    SPDBA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SPDBA_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_classify_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(classify scratch)");
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return SPDBA_OK;
+}
+
+extern "C" spdba_status spdba_classify_static(int32_t ndim, const int64_t* nblocks, const double* measure,
+                                              const double* tau, int32_t force_dc, int32_t transitions,
+                                              uint8_t* states, uint8_t* chi, int32_t* list, int32_t* count,
+                                              void* stream) {
+    if (!nblocks || !measure || !tau || !states || !chi || !list || !count)
+        return fail(SPDBA_ERR_ARG, "spdba_classify_static: NULL argument");
+    int64_t dims[3];
+    int32_t one[3] = {1, 1, 1};
+    for (int a = 0; a < ndim && a < 3; ++a) dims[a] = nblocks[a];
+    Geom g;
+    spdba_status s = make_geom(&g, ndim, dims, one);
+    if (s != SPDBA_OK) return s;
+    if (g.blocks() > SPDBA_CLASSIFY_STATIC_MAX_BLOCKS)
+        return fail(SPDBA_ERR_UNSUPPORTED, "spdba_classify_static: %lld blocks exceed the fixed capacity of %d",
+                    g.blocks(), SPDBA_CLASSIFY_STATIC_MAX_BLOCKS);
+    void* scratch = nullptr;
+    if ((s = static_scratch_for_current_device(&scratch)) != SPDBA_OK) return s;
+    // layout as in spdba_classify: per-CTA counts first, then one flag per block;
+    // every byte a call reads is written earlier in the same call
+    size_t cbytes = classify_scratch_bytes(g.blocks());
+    uint8_t* active = (uint8_t*)scratch + cbytes;
+    return launch_classify(g, measure, 0, tau, force_dc, transitions, 0, active, states, chi, list, count, scratch,
+                           nullptr, (cudaStream_t)stream);
+}

@@ -76,6 +76,8 @@ SIGNATURES = {
     "spdba_classify_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "spdba_classify": (_S, [ctypes.c_int32, _I64P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
                             _P, _P]),
+    "spdba_classify_static": (_S, [ctypes.c_int32, _I64P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+                                   _P, _P]),
 }
 
 _lib = None
@@ -286,3 +288,14 @@ def classify(nblocks, measure, tau, force_dc, transitions, states, chi, lst, cou
                                int(transitions), states.data_ptr(), chi.data_ptr(), lst.data_ptr(),
                                count.data_ptr(), scratch.data_ptr(),
                                current_stream() if stream is None else stream))
+
+
+CLASSIFY_STATIC_MAX_BLOCKS = 1 << 20
+
+
+def classify_static(nblocks, measure, tau, force_dc, transitions, states, chi, lst, count, stream=None):
+    """spdba_classify with the library's fixed scratch array (no allocation)."""
+    check(lib().spdba_classify_static(len(nblocks), _i64(nblocks), measure.data_ptr(), tau.data_ptr(),
+                                      int(force_dc), int(transitions), states.data_ptr(), chi.data_ptr(),
+                                      lst.data_ptr(), count.data_ptr(),
+                                      current_stream() if stream is None else stream))
