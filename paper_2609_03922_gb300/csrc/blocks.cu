@@ -25,6 +25,16 @@ spdba_status make_geom(Geom* g, int ndim, const int64_t* dims, const int32_t* bl
     return SPDBA_OK;
 }
 
+spdba_status make_geom_batched(Geom* g, int ndim, const int64_t* dims, const int32_t* block, long long batch) {
+    spdba_status s = make_geom(g, ndim, dims, block);
+    if (s != SPDBA_OK) return s;
+    if (batch < 1 || (batch > 1 && ndim > 2)) return fail(SPDBA_ERR_ARG, "batched geometry needs ndim <= 2");
+    int ax = 2 - ndim;   // the padded axis just above the field's axes
+    g->n[ax] = batch;
+    g->nb[ax] = batch;
+    return SPDBA_OK;
+}
+
 // ------------------------------------------------------------------ activity
 // One CTA per block.  The block max of |q|^2 is exact in FP64: an FP32 value
 // p32 = fma(re, re, im*im) (relative error below 2^-22) screens each mode, and
@@ -34,7 +44,8 @@ spdba_status make_geom(Geom* g, int ndim, const int64_t* dims, const int32_t* bl
 // FP64.  Results are reduced over the warp with shuffles and across warps in
 // shared memory.
 template <int NT> __device__ __forceinline__ void reduce_store(double mx, double mxnd, double sm, long long blk,
-                                                               double* maxsq, double* sumsq, double* gmax) {
+                                                               double* maxsq, double* sumsq, double* gmax,
+                                                               long long run) {
     mx = warp_max(mx);
     mxnd = warp_max(mxnd);
     sm = warp_sum(sm);
@@ -52,8 +63,8 @@ template <int NT> __device__ __forceinline__ void reduce_store(double mx, double
         if (l == 0) {
             maxsq[blk] = mx;
             if (sumsq) sumsq[blk] = sm;
-            atomic_max_nonneg(&gmax[0], mx);
-            atomic_max_nonneg(&gmax[1], mxnd);
+            atomic_max_nonneg(&gmax[2 * run], mx);
+            atomic_max_nonneg(&gmax[2 * run + 1], mxnd);
         }
     }
 }
@@ -86,6 +97,8 @@ __global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T
     const long long blk = blockIdx.x;
     const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
     const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
+    const long long run = blk / g.bpr();
+    const long long fm = g.fmodes();
     double mx = 0.0, mxnd = 0.0, sm = 0.0;
     float cut = 0.0f;
     if (sizeof(cx_t<T>) == 8 && (B2 & 1) == 0) {
@@ -98,8 +111,8 @@ __global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T
             int l1 = (int)(r % B1), l0 = (int)(r / B1);
             long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
             float4 v = __ldg(reinterpret_cast<const float4*>(q + idx));
-            screen_mode(make_float2(v.x, v.y), idx, ENERGY, mx, mxnd, cut, sm);
-            screen_mode(make_float2(v.z, v.w), idx + 1, ENERGY, mx, mxnd, cut, sm);
+            screen_mode(make_float2(v.x, v.y), idx % fm, ENERGY, mx, mxnd, cut, sm);
+            screen_mode(make_float2(v.z, v.w), (idx + 1) % fm, ENERGY, mx, mxnd, cut, sm);
         }
     } else {
         const long long nmodes = (long long)B0 * B1 * B2;
@@ -108,10 +121,10 @@ __global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T
             long long r = m / B2;
             int l1 = (int)(r % B1), l0 = (int)(r / B1);
             long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
-            screen_mode(__ldg(q + idx), idx, ENERGY, mx, mxnd, cut, sm);
+            screen_mode(__ldg(q + idx), idx % fm, ENERGY, mx, mxnd, cut, sm);
         }
     }
-    reduce_store<NT>(mx, mxnd, sm, blk, maxsq, sumsq, gmax);
+    reduce_store<NT>(mx, mxnd, sm, blk, maxsq, sumsq, gmax, run);
 }
 
 template <typename T>
@@ -130,20 +143,22 @@ template spdba_status launch_block_activity<double>(const Geom&, const double2*,
                                                     cudaStream_t);
 
 // ------------------------------------------------------------------ threshold
-__global__ void tau_kernel(const double* gmax, double threshold, int tau_rule, int exclude_dc, double* tau,
-                           DevStats* stats) {
-    double amax = sqrt(gmax[exclude_dc ? 1 : 0]);
-    double t = tau_rule == SPDBA_TAU_ABS ? threshold : threshold * amax;
-    *tau = t;
-    if (stats) {
-        stats->tau = t;
-        stats->max_amp = amax;
+__global__ void tau_kernel(const double* gmax, int nruns, double threshold, int tau_rule, int exclude_dc,
+                           double* tau, DevStats* stats) {
+    for (int r = threadIdx.x; r < nruns; r += blockDim.x) {
+        double amax = sqrt(gmax[2 * r + (exclude_dc ? 1 : 0)]);
+        double t = tau_rule == SPDBA_TAU_ABS ? threshold : threshold * amax;
+        tau[r] = t;
+        if (stats) {
+            stats[r].tau = t;
+            stats[r].max_amp = amax;
+        }
     }
 }
 
-spdba_status launch_tau(const double* gmax, double threshold, int tau_rule, int exclude_dc, double* tau,
+spdba_status launch_tau(const double* gmax, int nruns, double threshold, int tau_rule, int exclude_dc, double* tau,
                         DevStats* stats, cudaStream_t st) {
-    tau_kernel<<<1, 1, 0, st>>>(gmax, threshold, tau_rule, exclude_dc, tau, stats);
+    tau_kernel<<<1, 256, 0, st>>>(gmax, nruns, threshold, tau_rule, exclude_dc, tau, stats);
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;
 }
@@ -167,7 +182,8 @@ __global__ void active_kernel(Geom g, const double* __restrict__ msq, int msq_is
     long long nb = g.blocks();
     if (b >= nb) return;
     double m = msq_is_square ? sqrt(msq[b]) : msq[b];
-    bool a = all_active || (force_dc && b == 0) || (m >= *tau);
+    const long long run = b / g.bpr();
+    bool a = all_active || (force_dc && b == run * g.bpr()) || (m >= tau[run]);
     active[b] = a ? 1 : 0;
 }
 
@@ -206,22 +222,27 @@ __global__ void __launch_bounds__(CLS_NT) state_kernel(Geom g, const uint8_t* __
     unsigned nf = __ballot_sync(0xffffffffu, st != 0);
     unsigned na = __ballot_sync(0xffffffffu, st == SPDBA_ACTIVE);
     unsigned nt = __ballot_sync(0xffffffffu, st == SPDBA_TRANSITION);
-    __shared__ int s_nf, s_na, s_nt;
-    if (threadIdx.x == 0) { s_nf = 0; s_na = 0; s_nt = 0; }
+    __shared__ int s_nf;
+    if (threadIdx.x == 0) s_nf = 0;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&s_nf, __popc(nf));
-        atomicAdd(&s_na, __popc(na));
-        atomicAdd(&s_nt, __popc(nt));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cta_count[blockIdx.x] = s_nf;
-        if (stats) {
-            atomicAdd(&stats->n_active, (unsigned long long)s_na);
-            atomicAdd(&stats->n_transition, (unsigned long long)s_nt);
+    const long long bpr = g.bpr();
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_nf, __popc(nf));
+    if (stats) {
+        // per-run counts: one atomic per warp when a warp never straddles runs
+        if (bpr % 32 == 0) {
+            if ((threadIdx.x & 31) == 0 && b < nb) {
+                long long run = b / bpr;
+                if (na) atomicAdd(&stats[run].n_active, (unsigned long long)__popc(na));
+                if (nt) atomicAdd(&stats[run].n_transition, (unsigned long long)__popc(nt));
+            }
+        } else if (b < nb) {
+            long long run = b / bpr;
+            if (st == SPDBA_ACTIVE) atomicAdd(&stats[run].n_active, 1ull);
+            if (st == SPDBA_TRANSITION) atomicAdd(&stats[run].n_transition, 1ull);
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) cta_count[blockIdx.x] = s_nf;
 }
 
 // Ordered compaction: CTA c starts at the sum of the counts of CTAs before it
@@ -262,10 +283,12 @@ __global__ void __launch_bounds__(CLS_NT) compact_kernel(Geom g, const uint8_t* 
     }
 }
 
-__global__ void zero_counts_kernel(DevStats* stats) {
-    stats->n_active = 0;
-    stats->n_transition = 0;
-    stats->assessments += 1;
+__global__ void zero_counts_kernel(DevStats* stats, long long nruns) {
+    for (long long r = threadIdx.x; r < nruns; r += blockDim.x) {
+        stats[r].n_active = 0;
+        stats[r].n_transition = 0;
+        stats[r].assessments += 1;
+    }
 }
 
 size_t classify_scratch_bytes(long long nb) { return sizeof(int) * (size_t)((nb + CLS_NT - 1) / CLS_NT); }
@@ -275,7 +298,7 @@ spdba_status launch_classify(const Geom& g, const double* msq, int msq_is_square
                              int32_t* list, int32_t* count, void* scratch, DevStats* stats, cudaStream_t st) {
     long long nb = g.blocks();
     int ncta = (int)((nb + CLS_NT - 1) / CLS_NT);
-    if (stats) zero_counts_kernel<<<1, 1, 0, st>>>(stats);
+    if (stats) zero_counts_kernel<<<1, 256, 0, st>>>(stats, g.runs());
     active_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(g, msq, msq_is_square, tau, force_dc, all_active,
                                                                  active);
     state_kernel<<<ncta, CLS_NT, 0, st>>>(g, active, transitions, states, chi, (int*)scratch, stats);

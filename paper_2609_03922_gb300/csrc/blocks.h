@@ -14,8 +14,20 @@ struct Geom {
     __host__ __device__ long long modes() const { return n[0] * n[1] * n[2]; }
     __host__ __device__ long long blocks() const { return nb[0] * nb[1] * nb[2]; }
     __host__ __device__ long long block_modes() const { return (long long)b[0] * b[1] * b[2]; }
+    // A group stores several equal fields along the unused leading axis (or
+    // axes): blocks [r*bpr, (r+1)*bpr) and modes [r*fmodes, (r+1)*fmodes)
+    // belong to run r.  Neighbour relations never cross runs.
+    __host__ __device__ long long bpr() const {
+        return ndim == 3 ? nb[0] * nb[1] * nb[2] : ndim == 2 ? nb[1] * nb[2] : nb[2];
+    }
+    __host__ __device__ long long fmodes() const {
+        return ndim == 3 ? n[0] * n[1] * n[2] : ndim == 2 ? n[1] * n[2] : n[2];
+    }
+    __host__ __device__ long long runs() const { return blocks() / bpr(); }
 };
 spdba_status make_geom(Geom* g, int ndim, const int64_t* dims, const int32_t* block);
+// `batch` equal fields of ndim <= 2 dims stacked along the leading padded axis.
+spdba_status make_geom_batched(Geom* g, int ndim, const int64_t* dims, const int32_t* block, long long batch);
 
 // Device statistics of one run (mirrors spdba_stats, accumulated on the device).
 struct DevStats {
@@ -29,14 +41,15 @@ struct DevStats {
     double list_modes;   // modes touched by list-driven updates (for traffic accounting)
 };
 
-// maxsq / sumsq per block, gmax[0] = max over all modes, gmax[1] = max over k != 0.
-// gmax must be zeroed before the launch (the kernel max-reduces into it).
+// maxsq / sumsq per block; per run r, gmax[2r] = max over all its modes and
+// gmax[2r+1] = max over its modes k != 0.  gmax must be zeroed before the
+// launch (the kernel max-reduces into it).
 template <typename T>
 spdba_status launch_block_activity(const Geom& g, const cx_t<T>* q, double* maxsq, double* sumsq, double* gmax,
                                    cudaStream_t st);
-// tau = threshold (ABS) or threshold * sqrt(gmax[exclude_dc]) (REL_MAX); also
-// records tau and max amplitude in stats (may be null).
-spdba_status launch_tau(const double* gmax, double threshold, int tau_rule, int exclude_dc, double* tau,
+// Per run r: tau[r] = threshold (ABS) or threshold * sqrt(gmax[2r + exclude_dc])
+// (REL_MAX); also records tau and the max amplitude in stats[r] (may be null).
+spdba_status launch_tau(const double* gmax, int nruns, double threshold, int tau_rule, int exclude_dc, double* tau,
                         DevStats* stats, cudaStream_t st);
 // States, frozen-neighbour bits and the ordered list of non-frozen blocks.
 size_t classify_scratch_bytes(long long nb);
@@ -55,8 +68,7 @@ template <typename T> struct CHUpdateArgs {
     const int32_t* list;
     const int32_t* count;
     T dt, dtkappa;
-    DevStats* stats;
-    double inv_nblocks;
+    DevStats* stats;   // one per run
 };
 template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdateArgs<T>& a, int dense, cudaStream_t st);
 

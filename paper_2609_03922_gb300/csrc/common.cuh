@@ -145,8 +145,11 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
-// atomic max of a non-negative double through its bit pattern
+// atomic max of a non-negative double through its bit pattern; the atomic is
+// skipped when a plain read already shows a value at least as large (the max
+// only grows), which keeps many CTAs from serializing on one address.
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+    if (v <= *reinterpret_cast<volatile double*>(addr)) return;
     atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 

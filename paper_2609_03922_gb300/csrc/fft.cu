@@ -78,10 +78,13 @@ template <typename T> void TwiddleCache<T>::release() {
 static std::mutex g_attr_mu;
 static std::set<const void*> g_attr_done;
 
-static spdba_status ensure_smem_attr(const void* f, int smem) {
+static spdba_status ensure_smem_attr(const void* f, int smem, bool max_carveout) {
     std::lock_guard<std::mutex> lk(g_attr_mu);
     if (g_attr_done.count(f)) return SPDBA_OK;
     if (smem > 48 * 1024) SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // row-major (pencil-fastest) pipelined tiles stream through shared memory
+    // only; give them the whole carveout so three CTAs fit per SM
+    if (max_carveout) SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     g_attr_done.insert(f);
     return SPDBA_OK;
 }
@@ -100,7 +103,7 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     const bool generic = (I % ki.P) != 0;
     if (!get_pass_kernel<T>(L, sign, mode, loadp, storep, generic, &ki))
         return fail(SPDBA_ERR_UNSUPPORTED, "no FFT pass kernel for length %lld (mode %d)", (long long)L, mode);
-    spdba_status s = ensure_smem_attr(ki.func, ki.smem);
+    spdba_status s = ensure_smem_attr(ki.func, ki.smem, ki.pipe && loadp);
     if (s != SPDBA_OK) return s;
     long long ntiles = (O * I + ki.P - 1) / ki.P;
     long long grid = ntiles;

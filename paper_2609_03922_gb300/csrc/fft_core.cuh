@@ -72,8 +72,10 @@ template <typename T> struct PassParams {
     T scale;                              // multiply on store (1 = none)
     int generic;                          // 1: I % P != 0, per-pencil address arithmetic
     // CH nonlinearity fused between the inverse and forward x transforms
-    T nl_scale;                           // 1 / (number of grid points)
-    double* mass;                         // FP64 sum of c, or null
+    T nl_scale;                           // 1 / (number of grid points of one field)
+    double* mass;                         // FP64 sum of c per field (strided), or null
+    int mass_stride;                      // doubles between consecutive fields' accumulators
+    long long mass_ppr;                   // pencils per field
 };
 
 // Address of element (p, j) of the tile starting at pencil q0.
@@ -368,7 +370,7 @@ __device__ __forceinline__ void tile_body(cx_t<T>* sm, const PassParams<T>& a, l
         if (a.mass != nullptr) {
             double ms = (double)msum;
             ms = warp_sum(ms);
-            if ((threadIdx.x & 31) == 0) atomicAdd(a.mass, ms);
+            if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);
         }
         __syncthreads();
         run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
@@ -393,8 +395,13 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(PassParams<T> a) {
 // Pipelined kernel: persistent CTAs walk the tiles; the next tile streams into
 // the second shared buffer with cp.async while the current one is transformed.
 // Requires I % P == 0 and in/out with the same orientation.
+// Resident CTAs per SM the pipelined kernel is compiled for (register budget).
+template <typename T, int L, int MODE> struct PipeOcc {
+    static constexpr int value = (sizeof(T) == 4 && L <= 256 && MODE == PASS_PLAIN) ? 3 : 1;
+};
+
 template <typename T, int L, int P, int NT, int SIGN, int MODE, bool PFAST>
-__global__ void __launch_bounds__(NT) fft_pass_pipe_kernel(PassParams<T> a) {
+__global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE>::value) fft_pass_pipe_kernel(PassParams<T> a) {
     using C = cx_t<T>;
     using LY = typename std::conditional<PFAST, LayoutB<L, P>, LayoutA<L, P, true>>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -1,0 +1,39 @@
+// NLS split-step kernels: arguments and launchers.
+#pragma once
+#include "internal.h"
+
+namespace spdba {
+
+// Linear half-step factor H(w) as a pair hi + lo whose sum carries FP64
+// accuracy (lo = 0 for the FP64 path), so that the per-step FP32 rounding of
+// H does not accumulate into a systematic phase drift.
+template <typename T> struct HPair {
+    cx_t<T> hi, lo;
+};
+
+template <typename T> struct NLSArgs {
+    cx_t<T>* S;                 // spectra of `batch` signals of n samples
+    const HPair<T>* H;          // natural frequency order, n entries
+    const uint8_t* states;      // batch * nblk
+    const uint8_t* chi;
+    const T* taper;             // B entries
+    const cx_t<T>* tw;          // stage twiddles of the pass length
+    const cx_t<T>* tw4;         // exp(-2 pi i m / n), m < n (long signals)
+    long long n, n1;            // n = n1 * 512 for long signals
+    long long batch;
+    int B, nblk;                // block edge (bins) and blocks per signal
+    int dense;                  // 1: every bin ACTIVE (Regular)
+    T gamma_h, inv_n;
+    double* power;              // per-signal FP64 sum |E|^2 accumulators (strided) or null
+    int power_stride;
+    int do_fwd, do_close, do_open, do_inv, do_kerr;
+};
+
+template <typename T> spdba_status nls_small_step(const NLSArgs<T>& a, cudaStream_t st);
+template <typename T> spdba_status nls_row_pass(const NLSArgs<T>& a, cudaStream_t st);
+template <typename T> spdba_status nls_col_pass(const NLSArgs<T>& a, cudaStream_t st);
+template <typename T>
+spdba_status nls_permute(const cx_t<T>* in, cx_t<T>* out, long long n, long long n1, long long batch, int to_natural,
+                         cudaStream_t st);
+
+}  // namespace spdba

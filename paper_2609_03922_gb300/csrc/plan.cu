@@ -1,8 +1,13 @@
-// sp-DBA plan: owns the device buffers of one or more fields and runs the
-// time loop of the paper's solver integration (S2.1): per step a pre-update
-// (inverse transform, real-space nonlinearity, forward transform), then the
-// update dispatched by mode (Regular: every mode; sp-DBA: state preparation at
-// each reassessment, then the blockwise update of the listed blocks).
+// sp-DBA plan: owns the device buffers of one or more runs and drives the time
+// loop of the paper's solver integration (S2.1): per step the pre-update
+// (model terms and transforms), the update dispatched by mode (Regular: every
+// mode; sp-DBA: state preparation at each reassessment, then the blockwise
+// update of the non-frozen blocks), and the post-update transforms.
+//
+// Runs of equal size are stored contiguously as one "group" and step together
+// with one launch per kernel per group: the batched form of an ensemble of
+// Cahn-Hilliard fields or of a set of NLS signals.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -10,6 +15,7 @@
 #include <vector>
 
 #include "blocks.h"
+#include "nls.h"
 
 namespace spdba {
 
@@ -22,8 +28,20 @@ template <typename T> __global__ void complex_real_part_kernel(const cx_t<T>* __
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         r[i] = c[i].x;
 }
-__global__ void zero_double_kernel(double* p, int n) {
-    if ((int)threadIdx.x < n) p[threadIdx.x] = 0.0;
+__global__ void zero_strided_kernel(double* p, long long n, int stride) {
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) p[i * stride] = 0.0;
+}
+__global__ void zero_double_kernel(double* p, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0.0;
+}
+// per-run share of non-frozen blocks for one step (1 on all-active steps)
+__global__ void ratio_kernel(DevStats* stats, long long nruns, long long bpr, long long bmodes, int dense) {
+    for (long long r = threadIdx.x; r < nruns; r += blockDim.x) {
+        double nf = dense ? (double)bpr : (double)(stats[r].n_active + stats[r].n_transition);
+        stats[r].ratio_sum += nf / (double)bpr;
+        if (!dense) stats[r].list_modes += nf * (double)bmodes;
+    }
 }
 
 static unsigned grid_for(long long n, int nt) {
@@ -33,33 +51,45 @@ static unsigned grid_for(long long n, int nt) {
     return (unsigned)g;
 }
 
-// ------------------------------------------------------------------ one field
-template <typename T> struct Run {
+// ------------------------------------------------------------------ one group of equal runs
+template <typename T> struct Group {
     using C = cx_t<T>;
-    Geom g;
+    Geom g;                 // block geometry of the group (runs stacked on a padded axis)
+    Geom gT;                // long NLS signals: block geometry in the transposed storage order
     int ndim = 0;
     int64_t dims[3] = {1, 1, 1};
-    long long n = 0;
-    C* c_hat = nullptr;     // transformed field (the solver state)
-    C* work = nullptr;      // transform workspace: c, g, g_hat
-    T* real = nullptr;      // real-space staging for set/get_field
+    long long batch = 1;
+    long long n = 0;        // modes per run
+    bool long_nls = false;
+    long long n1 = 0;
+    C* c_hat = nullptr;     // transformed fields (the solver state), batch * n
+    C* work = nullptr;      // transform workspace, batch * n
+    T* real = nullptr;      // real-space staging of one run (CH)
     double* maxsq = nullptr;
     double* sumsq = nullptr;
-    double* dbl = nullptr;  // gmax[2], tau
+    double* gmax = nullptr; // 2 per run
+    double* tau = nullptr;  // 1 per run
     uint8_t* active = nullptr;
     uint8_t* states = nullptr;
     uint8_t* chi = nullptr;
     int32_t* list = nullptr;
     int32_t* count = nullptr;
     void* scratch = nullptr;
-    DevStats* stats = nullptr;
+    DevStats* stats = nullptr;  // 1 per run
+    // CH
     T* k2ax[3] = {nullptr, nullptr, nullptr};
     T* taper[3] = {nullptr, nullptr, nullptr};
-    // CH pre-update passes
     std::vector<Pass<T>> pre_inv;   // inverse passes before the fused one (first reads c_hat)
     Pass<T> fused;                  // inverse + nonlinearity + forward along the fast axis
     std::vector<Pass<T>> pre_fwd;   // remaining forward passes
-    FftEngine<T> fft;               // full transforms for set/get_field
+    FftEngine<T> fft1;              // one run's transforms for set/get_field
+    // NLS
+    HPair<T>* H = nullptr;
+    T* ntaper = nullptr;
+    const C* tw_row = nullptr;      // stage twiddles: n (short) or 512 (long rows)
+    const C* tw_col = nullptr;      // stage twiddles of n1 (long columns)
+    const C* tw4 = nullptr;         // exp(-2 pi i m / n)
+    int B = 1, nblk = 1;
     int64_t step = 0;
     bool assessed = false;
     std::vector<void*> allocs;
@@ -75,7 +105,7 @@ template <typename T> struct Run {
     void release() {
         for (void* p : allocs) cudaFree(p);
         allocs.clear();
-        fft.release();
+        fft1.release();
     }
 };
 
@@ -83,13 +113,20 @@ template <typename T> struct Run {
 
 using namespace spdba;
 
-enum ProfKind { K_FFT_PASS = 0, K_FUSED_NL, K_UPDATE_DENSE, K_UPDATE_LIST, K_ASSESS, K_COUNT };
-static const char* kProfName[K_COUNT] = {"fft_pass", "fft_fused_nl", "update_dense", "update_list", "assess"};
+enum ProfKind { K_FFT_PASS = 0, K_FUSED_NL, K_UPDATE_DENSE, K_UPDATE_LIST, K_ASSESS, K_NLS_STEP, K_NLS_ROW, K_NLS_COL,
+                K_COUNT };
+static const char* kProfName[K_COUNT] = {"fft_pass", "fft_fused_nl", "update_dense", "update_list", "assess",
+                                         "nls_step", "nls_row", "nls_col"};
 
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
     double bytes;
+};
+
+struct RunRef {
+    int group;
+    long long sub;
 };
 
 struct spdba_plan {
@@ -99,17 +136,18 @@ struct spdba_plan {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     long long launches = 0;
-    std::vector<double> prof_list_modes0;
+    double prof_list_bytes0 = 0;
     double threshold = 0;
     int reassess = 1;
     int precision = SPDBA_C64;
     cudaStream_t st = 0;
     spdba_status latched = SPDBA_OK;
-    std::vector<std::unique_ptr<Run<float>>> r32;
-    std::vector<std::unique_ptr<Run<double>>> r64;
+    std::vector<std::unique_ptr<Group<float>>> g32;
+    std::vector<std::unique_ptr<Group<double>>> g64;
+    std::vector<RunRef> runs;
     TwiddleCache<float> tw32;
     TwiddleCache<double> tw64;
-    int nruns() const { return precision == SPDBA_C64 ? (int)r32.size() : (int)r64.size(); }
+    int nruns() const { return (int)runs.size(); }
 };
 
 namespace spdba {
@@ -141,101 +179,184 @@ struct ProfScope {
     }
 };
 
-template <typename T> static std::vector<std::unique_ptr<Run<T>>>& runs(spdba_plan* p);
-template <> std::vector<std::unique_ptr<Run<float>>>& runs<float>(spdba_plan* p) { return p->r32; }
-template <> std::vector<std::unique_ptr<Run<double>>>& runs<double>(spdba_plan* p) { return p->r64; }
+template <typename T> static std::vector<std::unique_ptr<Group<T>>>& groups(spdba_plan* p);
+template <> std::vector<std::unique_ptr<Group<float>>>& groups<float>(spdba_plan* p) { return p->g32; }
+template <> std::vector<std::unique_ptr<Group<double>>>& groups<double>(spdba_plan* p) { return p->g64; }
 template <typename T> static TwiddleCache<T>& twc(spdba_plan* p);
 template <> TwiddleCache<float>& twc<float>(spdba_plan* p) { return p->tw32; }
 template <> TwiddleCache<double>& twc<double>(spdba_plan* p) { return p->tw64; }
 
-template <typename T>
-static spdba_status upload(Run<T>& r, T** dst, const std::vector<T>& v, cudaStream_t st) {
-    spdba_status s = r.alloc(dst, sizeof(T) * v.size());
+template <typename T, typename V>
+static spdba_status upload(Group<T>& r, V** dst, const std::vector<V>& v, cudaStream_t st) {
+    spdba_status s = r.alloc(dst, sizeof(V) * v.size());
     if (s != SPDBA_OK) return s;
-    SPDBA_CUDA(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+    SPDBA_CUDA(cudaMemcpyAsync(*dst, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice, st));
+    SPDBA_CUDA(cudaStreamSynchronize(st));   // v is a temporary
     return SPDBA_OK;
 }
 
-template <typename T>
-static spdba_status run_init(spdba_plan* p, Run<T>& r, int ndim, const int64_t* dims, const int32_t* block) {
+// H(w) = exp(i beta2 w^2 h / 4) per bin in FP64, split into hi + lo of type T
+template <typename T> static std::vector<HPair<T>> half_step_table(long long n, double beta2, double h, double dts) {
+    std::vector<HPair<T>> v((size_t)n);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long long k = 0; k < n; ++k) {
+        long long kk = k <= n / 2 ? k : k - n;
+        double w = two_pi * (double)kk / ((double)n * dts);
+        double phi = beta2 * w * w * h / 4.0;
+        double c = cos(phi), s = sin(phi);
+        HPair<T> e;
+        e.hi.x = (T)c;
+        e.hi.y = (T)s;
+        e.lo.x = (T)(c - (double)e.hi.x);
+        e.lo.y = (T)(s - (double)e.hi.y);
+        v[(size_t)k] = e;
+    }
+    return v;
+}
+
+// Common buffers of a group.
+template <typename T> static spdba_status group_buffers(spdba_plan* p, Group<T>& r) {
     cudaStream_t st = p->st;
-    spdba_status s = make_geom(&r.g, ndim, dims, block);
-    if (s != SPDBA_OK) return s;
-    r.ndim = ndim;
-    r.n = 1;
-    for (int a = 0; a < ndim; ++a) { r.dims[a] = dims[a]; r.n *= dims[a]; }
+    spdba_status s;
     const long long nb = r.g.blocks();
-    if ((s = r.alloc(&r.c_hat, sizeof(cx_t<T>) * r.n)) != SPDBA_OK) return s;
-    if ((s = r.alloc(&r.work, sizeof(cx_t<T>) * r.n)) != SPDBA_OK) return s;
+    const long long tot = r.batch * r.n;
+    if ((s = r.alloc(&r.c_hat, sizeof(cx_t<T>) * tot)) != SPDBA_OK) return s;
+    if ((s = r.alloc(&r.work, sizeof(cx_t<T>) * tot)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.real, sizeof(T) * r.n)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.maxsq, sizeof(double) * nb)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.sumsq, sizeof(double) * nb)) != SPDBA_OK) return s;
-    if ((s = r.alloc(&r.dbl, sizeof(double) * 4)) != SPDBA_OK) return s;
+    if ((s = r.alloc(&r.gmax, sizeof(double) * 2 * r.batch)) != SPDBA_OK) return s;
+    if ((s = r.alloc(&r.tau, sizeof(double) * r.batch)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.active, nb)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.states, nb)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.chi, nb)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.list, sizeof(int32_t) * nb)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.count, sizeof(int32_t) * 2)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.scratch, classify_scratch_bytes(nb))) != SPDBA_OK) return s;
-    if ((s = r.alloc(&r.stats, sizeof(DevStats))) != SPDBA_OK) return s;
-    SPDBA_CUDA(cudaMemsetAsync(r.c_hat, 0, sizeof(cx_t<T>) * r.n, st));
-    SPDBA_CUDA(cudaMemsetAsync(r.stats, 0, sizeof(DevStats), st));
+    if ((s = r.alloc(&r.stats, sizeof(DevStats) * r.batch)) != SPDBA_OK) return s;
+    SPDBA_CUDA(cudaMemsetAsync(r.c_hat, 0, sizeof(cx_t<T>) * tot, st));
+    SPDBA_CUDA(cudaMemsetAsync(r.stats, 0, sizeof(DevStats) * r.batch, st));
     SPDBA_CUDA(cudaMemsetAsync(r.states, SPDBA_ACTIVE, nb, st));
+    SPDBA_CUDA(cudaMemsetAsync(r.chi, 0, nb, st));
+    return SPDBA_OK;
+}
+
+template <typename T>
+static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const int64_t* dims, const int32_t* block,
+                                  long long batch) {
+    cudaStream_t st = p->st;
+    spdba_status s = ndim == 3 ? make_geom(&r.g, ndim, dims, block)
+                               : make_geom_batched(&r.g, ndim, dims, block, batch);
+    if (s != SPDBA_OK) return s;
+    r.ndim = ndim;
+    r.batch = batch;
+    r.n = 1;
+    for (int a = 0; a < ndim; ++a) { r.dims[a] = dims[a]; r.n *= dims[a]; }
+    if ((s = group_buffers<T>(p, r)) != SPDBA_OK) return s;
+    const int a0 = 3 - ndim;
     for (int ax = 0; ax < 3; ++ax) {
-        if ((s = upload<T>(r, &r.k2ax[ax], k2_table<T>(r.g.n[ax], p->opt.dx), st)) != SPDBA_OK) return s;
-        if ((s = upload<T>(r, &r.taper[ax], taper_table<T>(r.g.b[ax]), st)) != SPDBA_OK) return s;
+        std::vector<T> k2 = ax < a0 ? std::vector<T>((size_t)r.g.n[ax], (T)0) : k2_table<T>(r.g.n[ax], p->opt.dx);
+        if ((s = upload(r, &r.k2ax[ax], k2, st)) != SPDBA_OK) return s;
+        if ((s = upload(r, &r.taper[ax], taper_table<T>(r.g.b[ax]), st)) != SPDBA_OK) return s;
     }
     TwiddleCache<T>& tw = twc<T>(p);
-    if ((s = r.fft.init(ndim, dims, 1, tw, st)) != SPDBA_OK) return s;
-    if (p->opt.model == SPDBA_MODEL_CH) {
-        // inverse along axes 0..d-2, fused inverse/NL/forward along d-1, forward d-2..0
-        for (int a = 0; a < ndim - 1; ++a) {
-            Pass<T> ps;
-            if ((s = make_axis_pass<T>(&ps, ndim, dims, 1, a, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
-            r.pre_inv.push_back(ps);
-        }
-        if ((s = make_axis_pass<T>(&r.fused, ndim, dims, 1, ndim - 1, -1, PASS_CH_NL, tw, st)) != SPDBA_OK) return s;
-        r.fused.p.nl_scale = (T)(1.0 / (double)r.n);
-        for (int a = ndim - 2; a >= 0; --a) {
-            Pass<T> ps;
-            if ((s = make_axis_pass<T>(&ps, ndim, dims, 1, a, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
-            r.pre_fwd.push_back(ps);
-        }
+    if ((s = r.fft1.init(ndim, dims, 1, tw, st)) != SPDBA_OK) return s;
+    // inverse along axes 0..d-2, fused inverse/NL/forward along d-1, forward d-2..0
+    for (int a = 0; a < ndim - 1; ++a) {
+        Pass<T> ps;
+        if ((s = make_axis_pass<T>(&ps, ndim, dims, batch, a, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+        r.pre_inv.push_back(ps);
+    }
+    if ((s = make_axis_pass<T>(&r.fused, ndim, dims, batch, ndim - 1, -1, PASS_CH_NL, tw, st)) != SPDBA_OK) return s;
+    r.fused.p.nl_scale = (T)(1.0 / (double)r.n);
+    r.fused.p.mass_stride = (int)(sizeof(DevStats) / sizeof(double));
+    r.fused.p.mass_ppr = r.n / dims[ndim - 1];
+    for (int a = ndim - 2; a >= 0; --a) {
+        Pass<T> ps;
+        if ((s = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+        r.pre_fwd.push_back(ps);
     }
     return SPDBA_OK;
 }
 
-// State preparation (Methods): activity, threshold, states, list.
-template <typename T> static spdba_status run_assess(spdba_plan* p, Run<T>& r) {
+template <typename T>
+static spdba_status group_init_nls(spdba_plan* p, Group<T>& r, long long n, int nblk, long long batch) {
     cudaStream_t st = p->st;
-    spdba_status s;
-    ProfScope ps(p, K_ASSESS, (double)sizeof(cx_t<T>) * (double)r.n);
-    p->launches += 7;
-    double* gmax = r.dbl;
-    double* tau = r.dbl + 2;
-    zero_double_kernel<<<1, 32, 0, st>>>(gmax, 2);
-    double* sumsq = p->opt.measure == SPDBA_MEASURE_ENERGY ? r.sumsq : nullptr;
-    if ((s = launch_block_activity<T>(r.g, r.c_hat, r.maxsq, sumsq, gmax, st)) != SPDBA_OK) return s;
-    int exclude_dc = p->opt.model == SPDBA_MODEL_CH ? 1 : 0;
-    if ((s = launch_tau(gmax, p->threshold, p->opt.tau_rule, exclude_dc, tau, r.stats, st)) != SPDBA_OK) return s;
-    const double* msq = p->opt.measure == SPDBA_MEASURE_ENERGY ? r.sumsq : r.maxsq;
-    return launch_classify(r.g, msq, 1, tau, p->opt.force_dc, p->opt.transitions, 0, r.active, r.states, r.chi,
-                           r.list, r.count, r.scratch, r.stats, st);
+    if (nblk < 1 || n % nblk != 0) return fail(SPDBA_ERR_UNSUPPORTED, "%d blocks do not divide %lld bins", nblk, n);
+    const int64_t d[1] = {n};
+    const int32_t b[1] = {(int32_t)(n / nblk)};
+    spdba_status s = make_geom_batched(&r.g, 1, d, b, batch);
+    if (s != SPDBA_OK) return s;
+    r.ndim = 1;
+    r.dims[0] = n;
+    r.batch = batch;
+    r.n = n;
+    r.B = (int)(n / nblk);
+    r.nblk = nblk;
+    r.long_nls = n > 4096;
+    TwiddleCache<T>& tw = twc<T>(p);
+    if (r.long_nls) {
+        if (n % 512 != 0 || 512 % nblk != 0)
+            return fail(SPDBA_ERR_UNSUPPORTED, "NLS length %lld / %d blocks not supported", n, nblk);
+        r.n1 = n / 512;
+        if (!(r.n1 == 16 || r.n1 == 32 || r.n1 == 64 || r.n1 == 128 || r.n1 == 256 || r.n1 == 512))
+            return fail(SPDBA_ERR_UNSUPPORTED, "NLS length %lld not supported", n);
+        const int64_t dT[2] = {r.n1, 512};
+        const int32_t bT[2] = {(int32_t)r.n1, 512 / nblk};
+        if ((s = make_geom_batched(&r.gT, 2, dT, bT, batch)) != SPDBA_OK) return s;
+        s = SPDBA_OK;
+        if (!(r.tw_row = tw.get(512, st, &s))) return s;
+        if (!(r.tw_col = tw.get(r.n1, st, &s))) return s;
+        if (!(r.tw4 = tw.get(n, st, &s))) return s;
+    } else {
+        if (!(n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || n == 2048 || n == 4096))
+            return fail(SPDBA_ERR_UNSUPPORTED, "NLS length %lld not supported", n);
+        s = SPDBA_OK;
+        if (!(r.tw_row = tw.get(n, st, &s))) return s;
+        if ((s = r.fft1.init(1, d, 1, tw, st)) != SPDBA_OK) return s;
+    }
+    if ((s = group_buffers<T>(p, r)) != SPDBA_OK) return s;
+    if ((s = upload(r, &r.H, half_step_table<T>(n, p->opt.beta2, p->opt.h, p->opt.dt_sample), st)) != SPDBA_OK)
+        return s;
+    if ((s = upload(r, &r.ntaper, taper_table<T>(r.B), st)) != SPDBA_OK) return s;
+    return SPDBA_OK;
 }
 
-template <typename T> static spdba_status run_ch_step(spdba_plan* p, Run<T>& r) {
+// State preparation (Methods): activity, threshold, states, list.
+template <typename T> static spdba_status group_assess(spdba_plan* p, Group<T>& r) {
+    cudaStream_t st = p->st;
+    spdba_status s;
+    ProfScope ps(p, K_ASSESS, (double)sizeof(cx_t<T>) * (double)(r.batch * r.n));
+    const bool ch = p->opt.model == SPDBA_MODEL_CH;
+    zero_double_kernel<<<1, 256, 0, st>>>(r.gmax, 2 * r.batch);
+    double* sumsq = p->opt.measure == SPDBA_MEASURE_ENERGY ? r.sumsq : nullptr;
+    const Geom& ga = r.long_nls ? r.gT : r.g;   // same block numbering in both orders
+    if ((s = launch_block_activity<T>(ga, r.c_hat, r.maxsq, sumsq, r.gmax, st)) != SPDBA_OK) return s;
+    if ((s = launch_tau(r.gmax, (int)r.batch, p->threshold, p->opt.tau_rule, ch ? 1 : 0, r.tau, r.stats, st)) !=
+        SPDBA_OK)
+        return s;
+    const double* msq = sumsq ? r.sumsq : r.maxsq;
+    const int force_dc = ch ? p->opt.force_dc : 0;
+    if ((s = launch_classify(r.g, msq, 1, r.tau, force_dc, p->opt.transitions, 0, r.active, r.states, r.chi, r.list,
+                             r.count, r.scratch, r.stats, st)) != SPDBA_OK)
+        return s;
+    p->launches += 7;
+    r.assessed = true;
+    return SPDBA_OK;
+}
+
+static bool all_active_step(const spdba_plan* p, int64_t step) {
+    return step < p->opt.warmup_steps || (p->opt.refresh_every > 0 && step > 0 && step % p->opt.refresh_every == 0);
+}
+
+template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>& r) {
     cudaStream_t st = p->st;
     spdba_status s;
     const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
     const bool reassess = adaptive && (!r.assessed || r.step % p->reassess == 0);
-    const bool all_active = r.step < p->opt.warmup_steps ||
-                            (p->opt.refresh_every > 0 && r.step > 0 && r.step % p->opt.refresh_every == 0);
-    if (reassess) {
-        if ((s = run_assess<T>(p, r)) != SPDBA_OK) return s;
-        r.assessed = true;
-    }
+    if (reassess && (s = group_assess<T>(p, r)) != SPDBA_OK) return s;
     // pre-update: c = Re(IFFT(c_hat)), g = c^3 - c, g_hat = FFT(g)
-    const double pass_bytes = 2.0 * sizeof(cx_t<T>) * (double)r.n;
+    const double pass_bytes = 2.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n);
     const cx_t<T>* src = r.c_hat;
     for (auto& ps : r.pre_inv) {
         ProfScope pr(p, K_FFT_PASS, pass_bytes);
@@ -245,8 +366,8 @@ template <typename T> static spdba_status run_ch_step(spdba_plan* p, Run<T>& r) 
     }
     Pass<T> fused = r.fused;
     if (reassess) {
-        fused.p.mass = &r.stats->mass;
-        zero_double_kernel<<<1, 32, 0, st>>>(&r.stats->mass, 1);
+        fused.p.mass = &r.stats[0].mass;
+        zero_strided_kernel<<<1, 256, 0, st>>>(&r.stats[0].mass, r.batch, fused.p.mass_stride);
         p->launches += 1;
     }
     {
@@ -271,11 +392,11 @@ template <typename T> static spdba_status run_ch_step(spdba_plan* p, Run<T>& r) 
     a.dt = (T)p->opt.dt;
     a.dtkappa = (T)(p->opt.dt * p->opt.kappa);
     a.stats = r.stats;
-    a.inv_nblocks = 1.0 / (double)r.g.blocks();
-    const int dense = !adaptive || all_active;
+    const int dense = !adaptive || all_active_step(p, r.step);
     {
         // list-update traffic is known only on the device; it is added at profile end
-        ProfScope pr(p, dense ? K_UPDATE_DENSE : K_UPDATE_LIST, dense ? 3.0 * sizeof(cx_t<T>) * (double)r.n : 0.0);
+        ProfScope pr(p, dense ? K_UPDATE_DENSE : K_UPDATE_LIST,
+                     dense ? 3.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n) : 0.0);
         if ((s = launch_ch_update<T>(r.g, a, dense, st)) != SPDBA_OK) return s;
         p->launches += 1;
     }
@@ -283,49 +404,190 @@ template <typename T> static spdba_status run_ch_step(spdba_plan* p, Run<T>& r) 
     return SPDBA_OK;
 }
 
+template <typename T> static NLSArgs<T> nls_args(spdba_plan* p, Group<T>& r, cx_t<T>* S, long long batch, int dense) {
+    NLSArgs<T> a{};
+    a.S = S;
+    a.H = r.H;
+    a.states = r.states;
+    a.chi = r.chi;
+    a.taper = r.ntaper;
+    a.tw = r.tw_row;
+    a.tw4 = r.tw4;
+    a.n = r.n;
+    a.n1 = r.n1;
+    a.batch = batch;
+    a.B = r.B;
+    a.nblk = r.nblk;
+    a.dense = dense;
+    a.gamma_h = (T)(p->opt.gamma * p->opt.h);
+    a.inv_n = (T)(1.0 / (double)r.n);
+    a.power = nullptr;
+    a.power_stride = (int)(sizeof(DevStats) / sizeof(double));
+    return a;
+}
+
+template <typename T> static spdba_status row_pass(spdba_plan* p, NLSArgs<T> a, int fwd, int close, int open, int inv) {
+    a.do_fwd = fwd; a.do_close = close; a.do_open = open; a.do_inv = inv;
+    ProfScope pr(p, K_NLS_ROW, 2.0 * sizeof(cx_t<T>) * (double)(a.batch * a.n));
+    p->launches += 1;
+    return nls_row_pass<T>(a, p->st);
+}
+template <typename T> static spdba_status col_pass(spdba_plan* p, NLSArgs<T> a, int inv, int kerr, int fwd) {
+    a.do_inv = inv; a.do_kerr = kerr; a.do_fwd = fwd;
+    ProfScope pr(p, K_NLS_COL, 2.0 * sizeof(cx_t<T>) * (double)(a.batch * a.n));
+    p->launches += 1;
+    return nls_col_pass<T>(a, p->st);
+}
+
+// n steps of an NLS group.  Between calls S is the spectrum at a step boundary.
+template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T>& r, int64_t nsteps) {
+    cudaStream_t st = p->st;
+    spdba_status s;
+    const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
+    int prev_dense = 1;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const bool reassess = adaptive && (!r.assessed || r.step % p->reassess == 0);
+        const int dense = !adaptive || all_active_step(p, r.step);
+        NLSArgs<T> a = nls_args<T>(p, r, r.c_hat, r.batch, dense);
+        if (r.long_nls) {
+            // close the previous step unless this step's row pass can take it over
+            const bool merge = i > 0 && !reassess && prev_dense == dense;
+            if (i > 0 && !merge) {
+                NLSArgs<T> c = nls_args<T>(p, r, r.c_hat, r.batch, prev_dense);
+                if ((s = row_pass<T>(p, c, 1, 1, 0, 0)) != SPDBA_OK) return s;
+            }
+            if (reassess && (s = group_assess<T>(p, r)) != SPDBA_OK) return s;
+            if ((s = row_pass<T>(p, a, merge ? 1 : 0, merge ? 1 : 0, 1, 1)) != SPDBA_OK) return s;
+            NLSArgs<T> c = a;
+            c.tw = r.tw_col;
+            if (reassess) {
+                zero_strided_kernel<<<1, 256, 0, st>>>(&r.stats[0].mass, r.batch, a.power_stride);
+                c.power = &r.stats[0].mass;
+            }
+            if ((s = col_pass<T>(p, c, 1, 1, 1)) != SPDBA_OK) return s;
+        } else {
+            if (reassess && (s = group_assess<T>(p, r)) != SPDBA_OK) return s;
+            if (reassess) {
+                zero_strided_kernel<<<1, 256, 0, st>>>(&r.stats[0].mass, r.batch, a.power_stride);
+                a.power = &r.stats[0].mass;
+            }
+            ProfScope pr(p, K_NLS_STEP, 2.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n));
+            if ((s = nls_small_step<T>(a, st)) != SPDBA_OK) return s;
+            p->launches += 1;
+        }
+        ratio_kernel<<<1, 256, 0, st>>>(r.stats, r.batch, r.g.bpr(), r.g.block_modes(), dense);
+        SPDBA_CUDA(cudaGetLastError());
+        p->launches += 1;
+        prev_dense = dense;
+        r.step += 1;
+    }
+    if (r.long_nls && nsteps > 0) {
+        NLSArgs<T> c = nls_args<T>(p, r, r.c_hat, r.batch, prev_dense);
+        if ((s = row_pass<T>(p, c, 1, 1, 0, 0)) != SPDBA_OK) return s;
+    }
+    return SPDBA_OK;
+}
+
 template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
-    auto& rs = runs<T>(p);
+    auto& gs = groups<T>(p);
+    if (p->opt.model == SPDBA_MODEL_NLS) {
+        for (auto& g : gs) {
+            spdba_status s = group_nls_steps<T>(p, *g, n);
+            if (s != SPDBA_OK) return s;
+        }
+        return SPDBA_OK;
+    }
     for (int64_t i = 0; i < n; ++i) {
-        for (auto& r : rs) {
-            spdba_status s = SPDBA_OK;
-            if (p->opt.model == SPDBA_MODEL_CH) s = run_ch_step<T>(p, *r);
-            else s = fail(SPDBA_ERR_UNSUPPORTED, "model %d not built", p->opt.model);
+        for (auto& g : gs) {
+            spdba_status s = group_ch_step<T>(p, *g);
             if (s != SPDBA_OK) return s;
         }
     }
     return SPDBA_OK;
 }
 
-template <typename T> static spdba_status run_set_field(spdba_plan* p, Run<T>& r, const void* src, int on_dev) {
+template <typename T>
+static spdba_status run_set_field(spdba_plan* p, Group<T>& r, long long sub, const void* src, int on_dev) {
     cudaStream_t st = p->st;
+    spdba_status s;
+    cx_t<T>* slot = r.c_hat + sub * r.n;
+    cx_t<T>* wslot = r.work + sub * r.n;
+    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (p->opt.model == SPDBA_MODEL_CH) {
-        SPDBA_CUDA(cudaMemcpyAsync(r.real, src, sizeof(T) * r.n, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        real_to_complex_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(r.real, r.work, r.n);
-        spdba_status s = r.fft.exec(r.work, r.c_hat, SPDBA_FORWARD, st);
-        if (s != SPDBA_OK) return s;
+        SPDBA_CUDA(cudaMemcpyAsync(r.real, src, sizeof(T) * r.n, kind, st));
+        real_to_complex_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(r.real, wslot, r.n);
+        if ((s = r.fft1.exec(wslot, slot, SPDBA_FORWARD, st)) != SPDBA_OK) return s;
+    } else if (!r.long_nls) {
+        SPDBA_CUDA(cudaMemcpyAsync(wslot, src, sizeof(cx_t<T>) * r.n, kind, st));
+        if ((s = r.fft1.exec(wslot, slot, SPDBA_FORWARD, st)) != SPDBA_OK) return s;
     } else {
-        SPDBA_CUDA(cudaMemcpyAsync(r.work, src, sizeof(cx_t<T>) * r.n, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        spdba_status s = r.fft.exec(r.work, r.c_hat, SPDBA_FORWARD, st);
-        if (s != SPDBA_OK) return s;
+        // E (natural time order) -> column pass (forward) -> row pass (forward): S in transposed order
+        SPDBA_CUDA(cudaMemcpyAsync(slot, src, sizeof(cx_t<T>) * r.n, kind, st));
+        NLSArgs<T> a = nls_args<T>(p, r, slot, 1, 1);
+        a.tw = r.tw_col;
+        a.do_inv = 0; a.do_kerr = 0; a.do_fwd = 1;
+        if ((s = nls_col_pass<T>(a, st)) != SPDBA_OK) return s;
+        a.tw = r.tw_row;
+        a.do_fwd = 1; a.do_close = 0; a.do_open = 0; a.do_inv = 0;
+        if ((s = nls_row_pass<T>(a, st)) != SPDBA_OK) return s;
     }
     r.step = 0;
     r.assessed = false;
-    SPDBA_CUDA(cudaMemsetAsync(r.stats, 0, sizeof(DevStats), st));
-    SPDBA_CUDA(cudaMemsetAsync(r.states, SPDBA_ACTIVE, r.g.blocks(), st));
+    SPDBA_CUDA(cudaMemsetAsync(r.stats + sub, 0, sizeof(DevStats), st));
+    SPDBA_CUDA(cudaMemsetAsync(r.states + sub * r.g.bpr(), SPDBA_ACTIVE, r.g.bpr(), st));
     return SPDBA_OK;
 }
 
-template <typename T> static spdba_status run_get_field(spdba_plan* p, Run<T>& r, void* dst, int on_dev) {
+template <typename T>
+static spdba_status run_get_field(spdba_plan* p, Group<T>& r, long long sub, void* dst, int on_dev) {
     cudaStream_t st = p->st;
-    spdba_status s = r.fft.exec(r.c_hat, r.work, SPDBA_INVERSE, st);
-    if (s != SPDBA_OK) return s;
+    spdba_status s;
+    cx_t<T>* slot = r.c_hat + sub * r.n;
+    cx_t<T>* wslot = r.work + sub * r.n;
+    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (p->opt.model == SPDBA_MODEL_CH) {
-        complex_real_part_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(r.work, r.real, r.n);
-        SPDBA_CUDA(cudaMemcpyAsync(dst, r.real, sizeof(T) * r.n, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        if ((s = r.fft1.exec(slot, wslot, SPDBA_INVERSE, st)) != SPDBA_OK) return s;
+        complex_real_part_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(wslot, r.real, r.n);
+        SPDBA_CUDA(cudaMemcpyAsync(dst, r.real, sizeof(T) * r.n, kind, st));
+    } else if (!r.long_nls) {
+        if ((s = r.fft1.exec(slot, wslot, SPDBA_INVERSE, st)) != SPDBA_OK) return s;
+        SPDBA_CUDA(cudaMemcpyAsync(dst, wslot, sizeof(cx_t<T>) * r.n, kind, st));
     } else {
-        SPDBA_CUDA(cudaMemcpyAsync(dst, r.work, sizeof(cx_t<T>) * r.n, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        SPDBA_CUDA(cudaMemcpyAsync(wslot, slot, sizeof(cx_t<T>) * r.n, cudaMemcpyDeviceToDevice, st));
+        NLSArgs<T> a = nls_args<T>(p, r, wslot, 1, 1);
+        a.tw = r.tw_row;
+        a.do_fwd = 0; a.do_close = 0; a.do_open = 0; a.do_inv = 1;
+        if ((s = nls_row_pass<T>(a, st)) != SPDBA_OK) return s;
+        a.tw = r.tw_col;
+        a.do_inv = 1; a.do_kerr = 0; a.do_fwd = 0;
+        if ((s = nls_col_pass<T>(a, st)) != SPDBA_OK) return s;
+        SPDBA_CUDA(cudaMemcpyAsync(dst, wslot, sizeof(cx_t<T>) * r.n, kind, st));
     }
     SPDBA_CUDA(cudaStreamSynchronize(st));
+    return SPDBA_OK;
+}
+
+template <typename T>
+static spdba_status copy_spectrum(spdba_plan* p, Group<T>& r, long long sub, void* buf, int on_dev, bool get) {
+    cudaStream_t st = p->st;
+    size_t bytes = sizeof(cx_t<T>) * (size_t)r.n;
+    cx_t<T>* slot = r.c_hat + sub * r.n;
+    cx_t<T>* wslot = r.work + sub * r.n;
+    spdba_status s;
+    if (get) {
+        const cx_t<T>* from = slot;
+        if (r.long_nls) {
+            if ((s = nls_permute<T>(slot, wslot, r.n, r.n1, 1, 1, st)) != SPDBA_OK) return s;
+            from = wslot;
+        }
+        SPDBA_CUDA(cudaMemcpyAsync(buf, from, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        SPDBA_CUDA(cudaStreamSynchronize(st));
+    } else {
+        cx_t<T>* to = r.long_nls ? wslot : slot;
+        SPDBA_CUDA(cudaMemcpyAsync(to, buf, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        if (r.long_nls && (s = nls_permute<T>(wslot, slot, r.n, r.n1, 1, 0, st)) != SPDBA_OK) return s;
+        r.assessed = false;
+    }
     return SPDBA_OK;
 }
 
@@ -336,9 +598,9 @@ static spdba_status latch(spdba_plan* p, spdba_status s) {
     if (s == SPDBA_ERR_CUDA && p) p->latched = s;
     return s;
 }
-#define PLAN_CHECK(p)                                                                  \
-    do {                                                                               \
-        if (!(p)) return fail(SPDBA_ERR_ARG, "NULL plan");                             \
+#define PLAN_CHECK(p)                                                                             \
+    do {                                                                                          \
+        if (!(p)) return fail(SPDBA_ERR_ARG, "NULL plan");                                        \
         if ((p)->latched != SPDBA_OK) return fail((p)->latched, "plan has a latched CUDA error"); \
     } while (0)
 
@@ -367,13 +629,56 @@ extern "C" void spdba_options_default(spdba_options* o) {
 
 static spdba_status check_opts(const spdba_options* o, int ndim) {
     if (o->model != SPDBA_MODEL_CH && o->model != SPDBA_MODEL_NLS) return fail(SPDBA_ERR_ARG, "bad model %d", o->model);
-    if (o->precision != SPDBA_C64 && o->precision != SPDBA_C128) return fail(SPDBA_ERR_ARG, "bad precision %d", o->precision);
+    if (o->precision != SPDBA_C64 && o->precision != SPDBA_C128)
+        return fail(SPDBA_ERR_ARG, "bad precision %d", o->precision);
     if (o->mode != SPDBA_MODE_REGULAR && o->mode != SPDBA_MODE_ADAPTIVE) return fail(SPDBA_ERR_ARG, "bad mode %d", o->mode);
     if (o->measure != SPDBA_MEASURE_MAXAMP && o->measure != SPDBA_MEASURE_ENERGY) return fail(SPDBA_ERR_ARG, "bad measure");
     if (o->tau_rule != SPDBA_TAU_REL_MAX && o->tau_rule != SPDBA_TAU_ABS) return fail(SPDBA_ERR_ARG, "bad tau rule");
     if (o->refresh_every < 0 || o->warmup_steps < 0) return fail(SPDBA_ERR_ARG, "negative refresh/warm-up");
     if (o->model == SPDBA_MODEL_CH && (ndim < 2 || ndim > 3)) return fail(SPDBA_ERR_UNSUPPORTED, "CH plans are 2-D or 3-D");
     if (o->model == SPDBA_MODEL_NLS && ndim != 1) return fail(SPDBA_ERR_UNSUPPORTED, "NLS plans are 1-D");
+    return SPDBA_OK;
+}
+
+template <typename T>
+static spdba_status build_groups(spdba_plan* p, int nruns, int ndim, const int64_t* dims, const int32_t* block) {
+    auto& gs = groups<T>(p);
+    // runs of equal extents share a group (3-D CH fields stay alone)
+    std::vector<std::vector<int>> members;
+    for (int r = 0; r < nruns; ++r) {
+        const int64_t* d = dims + (size_t)r * ndim;
+        int found = -1;
+        if (!(p->opt.model == SPDBA_MODEL_CH && ndim == 3)) {
+            for (size_t gi = 0; gi < members.size(); ++gi) {
+                const int64_t* e = dims + (size_t)members[gi][0] * ndim;
+                bool same = true;
+                for (int a = 0; a < ndim; ++a) same = same && d[a] == e[a];
+                if (same) { found = (int)gi; break; }
+            }
+        }
+        if (found < 0) {
+            found = (int)members.size();
+            members.push_back({});
+        }
+        members[found].push_back(r);
+    }
+    p->runs.assign(nruns, RunRef{0, 0});
+    for (size_t gi = 0; gi < members.size(); ++gi) {
+        const int64_t* d = dims + (size_t)members[gi][0] * ndim;
+        long long batch = (long long)members[gi].size();
+        gs.emplace_back(new Group<T>());
+        spdba_status s;
+        if (p->opt.model == SPDBA_MODEL_NLS) {
+            if (block[0] > 0 && d[0] % block[0] != 0)
+                return fail(SPDBA_ERR_UNSUPPORTED, "block edge %d does not divide %lld", block[0], (long long)d[0]);
+            int nblk = block[0] <= 0 ? -block[0] : (int)(d[0] / block[0]);
+            s = group_init_nls<T>(p, *gs.back(), d[0], nblk, batch);
+        } else {
+            s = group_init_ch<T>(p, *gs.back(), ndim, d, block, batch);
+        }
+        if (s != SPDBA_OK) return s;
+        for (size_t k = 0; k < members[gi].size(); ++k) p->runs[members[gi][k]] = RunRef{(int)gi, (long long)k};
+    }
     return SPDBA_OK;
 }
 
@@ -398,19 +703,8 @@ extern "C" spdba_status spdba_batch_create(spdba_plan** out, int32_t nruns, int3
     p->reassess = reassess;
     p->precision = o.precision;
     p->st = (cudaStream_t)o.stream;
-    for (int r = 0; r < nruns && s == SPDBA_OK; ++r) {
-        const int64_t* d = dims + (size_t)r * ndim;
-        int32_t blk[3];
-        for (int a = 0; a < ndim; ++a) blk[a] = block[a];
-        if (o.model == SPDBA_MODEL_NLS && block[0] <= 0) blk[0] = (int32_t)(d[0] / (-block[0]));
-        if (p->precision == SPDBA_C64) {
-            p->r32.emplace_back(new Run<float>());
-            s = run_init<float>(p, *p->r32.back(), ndim, d, blk);
-        } else {
-            p->r64.emplace_back(new Run<double>());
-            s = run_init<double>(p, *p->r64.back(), ndim, d, blk);
-        }
-    }
+    s = p->precision == SPDBA_C64 ? build_groups<float>(p, nruns, ndim, dims, block)
+                                  : build_groups<double>(p, nruns, ndim, dims, block);
     if (s == SPDBA_OK) {
         cudaError_t e = cudaStreamSynchronize(p->st);
         if (e != cudaSuccess) s = cuda_fail(e, "plan setup");
@@ -431,8 +725,8 @@ extern "C" spdba_status spdba_plan_create(spdba_plan** out, int32_t ndim, const 
 extern "C" void spdba_plan_destroy(spdba_plan* p) {
     if (!p) return;
     cudaStreamSynchronize(p->st);
-    for (auto& r : p->r32) r->release();
-    for (auto& r : p->r64) r->release();
+    for (auto& g : p->g32) g->release();
+    for (auto& g : p->g64) g->release();
     p->tw32.release();
     p->tw64.release();
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -441,12 +735,17 @@ extern "C" void spdba_plan_destroy(spdba_plan* p) {
 
 static bool run_ok(spdba_plan* p, int32_t run) { return run >= 0 && run < p->nruns(); }
 
+// Calls F(group, sub) with the run's group of the plan's precision.
+template <typename F> static spdba_status with_run(spdba_plan* p, int32_t run, F f) {
+    const RunRef& rr = p->runs[run];
+    if (p->precision == SPDBA_C64) return f(*p->g32[rr.group], rr.sub);
+    return f(*p->g64[rr.group], rr.sub);
+}
+
 extern "C" spdba_status spdba_set_field(spdba_plan* p, int32_t run, const void* src, int32_t on_dev) {
     PLAN_CHECK(p);
     if (!src || !run_ok(p, run)) return fail(SPDBA_ERR_ARG, "spdba_set_field: bad arguments");
-    spdba_status s = p->precision == SPDBA_C64 ? run_set_field<float>(p, *p->r32[run], src, on_dev)
-                                               : run_set_field<double>(p, *p->r64[run], src, on_dev);
-    return latch(p, s);
+    return latch(p, with_run(p, run, [&](auto& G, long long sub) { return run_set_field(p, G, sub, src, on_dev); }));
 }
 
 extern "C" spdba_status spdba_step(spdba_plan* p, int64_t n) {
@@ -459,42 +758,26 @@ extern "C" spdba_status spdba_step(spdba_plan* p, int64_t n) {
 extern "C" spdba_status spdba_get_field(spdba_plan* p, int32_t run, void* dst, int32_t on_dev) {
     PLAN_CHECK(p);
     if (!dst || !run_ok(p, run)) return fail(SPDBA_ERR_ARG, "spdba_get_field: bad arguments");
-    spdba_status s = p->precision == SPDBA_C64 ? run_get_field<float>(p, *p->r32[run], dst, on_dev)
-                                               : run_get_field<double>(p, *p->r64[run], dst, on_dev);
-    return latch(p, s);
-}
-
-template <typename T> static spdba_status copy_spectrum(spdba_plan* p, Run<T>& r, void* buf, int on_dev, bool get) {
-    size_t bytes = sizeof(cx_t<T>) * (size_t)r.n;
-    if (get) {
-        SPDBA_CUDA(cudaMemcpyAsync(buf, r.c_hat, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->st));
-        SPDBA_CUDA(cudaStreamSynchronize(p->st));
-    } else {
-        SPDBA_CUDA(cudaMemcpyAsync(r.c_hat, buf, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->st));
-        r.assessed = false;
-    }
-    return SPDBA_OK;
+    return latch(p, with_run(p, run, [&](auto& G, long long sub) { return run_get_field(p, G, sub, dst, on_dev); }));
 }
 
 extern "C" spdba_status spdba_get_spectrum(spdba_plan* p, int32_t run, void* dst, int32_t on_dev) {
     PLAN_CHECK(p);
     if (!dst || !run_ok(p, run)) return fail(SPDBA_ERR_ARG, "spdba_get_spectrum: bad arguments");
-    spdba_status s = p->precision == SPDBA_C64 ? copy_spectrum<float>(p, *p->r32[run], dst, on_dev, true)
-                                               : copy_spectrum<double>(p, *p->r64[run], dst, on_dev, true);
-    return latch(p, s);
+    return latch(p, with_run(p, run, [&](auto& G, long long sub) { return copy_spectrum(p, G, sub, dst, on_dev, true); }));
 }
 
 extern "C" spdba_status spdba_set_spectrum(spdba_plan* p, int32_t run, const void* src, int32_t on_dev) {
     PLAN_CHECK(p);
     if (!src || !run_ok(p, run)) return fail(SPDBA_ERR_ARG, "spdba_set_spectrum: bad arguments");
-    spdba_status s = p->precision == SPDBA_C64 ? copy_spectrum<float>(p, *p->r32[run], (void*)src, on_dev, false)
-                                               : copy_spectrum<double>(p, *p->r64[run], (void*)src, on_dev, false);
-    return latch(p, s);
+    return latch(p, with_run(p, run,
+                             [&](auto& G, long long sub) { return copy_spectrum(p, G, sub, (void*)src, on_dev, false); }));
 }
 
-template <typename T> static spdba_status get_mask_t(spdba_plan* p, Run<T>& r, uint8_t* dst, int64_t nb) {
-    if (nb != r.g.blocks()) return fail(SPDBA_ERR_ARG, "mask size %lld != %lld blocks", (long long)nb, r.g.blocks());
-    SPDBA_CUDA(cudaMemcpyAsync(dst, r.states, (size_t)nb, cudaMemcpyDeviceToHost, p->st));
+template <typename T>
+static spdba_status get_mask_t(spdba_plan* p, Group<T>& r, long long sub, uint8_t* dst, int64_t nb) {
+    if (nb != r.g.bpr()) return fail(SPDBA_ERR_ARG, "mask size %lld != %lld blocks", (long long)nb, r.g.bpr());
+    SPDBA_CUDA(cudaMemcpyAsync(dst, r.states + sub * r.g.bpr(), (size_t)nb, cudaMemcpyDeviceToHost, p->st));
     SPDBA_CUDA(cudaStreamSynchronize(p->st));
     return SPDBA_OK;
 }
@@ -502,18 +785,16 @@ template <typename T> static spdba_status get_mask_t(spdba_plan* p, Run<T>& r, u
 extern "C" spdba_status spdba_get_mask(spdba_plan* p, int32_t run, uint8_t* dst, int64_t nb) {
     PLAN_CHECK(p);
     if (!dst || !run_ok(p, run)) return fail(SPDBA_ERR_ARG, "spdba_get_mask: bad arguments");
-    spdba_status s = p->precision == SPDBA_C64 ? get_mask_t<float>(p, *p->r32[run], dst, nb)
-                                               : get_mask_t<double>(p, *p->r64[run], dst, nb);
-    return latch(p, s);
+    return latch(p, with_run(p, run, [&](auto& G, long long sub) { return get_mask_t(p, G, sub, dst, nb); }));
 }
 
-template <typename T> static spdba_status get_stats_t(spdba_plan* p, Run<T>& r, spdba_stats* out) {
+template <typename T> static spdba_status get_stats_t(spdba_plan* p, Group<T>& r, long long sub, spdba_stats* out) {
     DevStats d;
-    SPDBA_CUDA(cudaMemcpyAsync(&d, r.stats, sizeof d, cudaMemcpyDeviceToHost, p->st));
+    SPDBA_CUDA(cudaMemcpyAsync(&d, r.stats + sub, sizeof d, cudaMemcpyDeviceToHost, p->st));
     SPDBA_CUDA(cudaStreamSynchronize(p->st));
     out->step = r.step;
     out->assessments = (int64_t)d.assessments;
-    out->nblocks = r.g.blocks();
+    out->nblocks = r.g.bpr();
     out->n_active = (int64_t)d.n_active;
     out->n_transition = (int64_t)d.n_transition;
     out->tau = d.tau;
@@ -526,18 +807,16 @@ template <typename T> static spdba_status get_stats_t(spdba_plan* p, Run<T>& r, 
 extern "C" spdba_status spdba_get_stats(spdba_plan* p, int32_t run, spdba_stats* out) {
     PLAN_CHECK(p);
     if (!out || !run_ok(p, run)) return fail(SPDBA_ERR_ARG, "spdba_get_stats: bad arguments");
-    spdba_status s = p->precision == SPDBA_C64 ? get_stats_t<float>(p, *p->r32[run], out)
-                                               : get_stats_t<double>(p, *p->r64[run], out);
-    return latch(p, s);
+    return latch(p, with_run(p, run, [&](auto& G, long long sub) { return get_stats_t(p, G, sub, out); }));
 }
 
-template <typename T> static spdba_status list_modes_now(spdba_plan* p, std::vector<double>* out) {
-    out->clear();
-    for (auto& r : runs<T>(p)) {
-        DevStats d;
-        SPDBA_CUDA(cudaMemcpyAsync(&d, r->stats, sizeof d, cudaMemcpyDeviceToHost, p->st));
+template <typename T> static spdba_status list_bytes_now(spdba_plan* p, double* out) {
+    *out = 0;
+    for (auto& g : groups<T>(p)) {
+        std::vector<DevStats> d((size_t)g->batch);
+        SPDBA_CUDA(cudaMemcpyAsync(d.data(), g->stats, sizeof(DevStats) * d.size(), cudaMemcpyDeviceToHost, p->st));
         SPDBA_CUDA(cudaStreamSynchronize(p->st));
-        out->push_back(d.list_modes);
+        for (auto& x : d) *out += 3.0 * sizeof(cx_t<T>) * x.list_modes;
     }
     return SPDBA_OK;
 }
@@ -547,8 +826,8 @@ extern "C" spdba_status spdba_profile_begin(spdba_plan* p) {
     p->prof_recs.clear();
     p->ev_used = 0;
     p->launches = 0;
-    spdba_status s = p->precision == SPDBA_C64 ? list_modes_now<float>(p, &p->prof_list_modes0)
-                                               : list_modes_now<double>(p, &p->prof_list_modes0);
+    spdba_status s = p->precision == SPDBA_C64 ? list_bytes_now<float>(p, &p->prof_list_bytes0)
+                                               : list_bytes_now<double>(p, &p->prof_list_bytes0);
     if (s != SPDBA_OK) return latch(p, s);
     p->prof = true;
     return SPDBA_OK;
@@ -571,12 +850,10 @@ extern "C" spdba_status spdba_profile_end(spdba_plan* p, spdba_kernel_time* out,
         agg[r.kind].total_ms += ms;
         agg[r.kind].bytes += r.bytes;
     }
-    std::vector<double> lm;
-    spdba_status s = p->precision == SPDBA_C64 ? list_modes_now<float>(p, &lm) : list_modes_now<double>(p, &lm);
+    double lb = 0;
+    spdba_status s = p->precision == SPDBA_C64 ? list_bytes_now<float>(p, &lb) : list_bytes_now<double>(p, &lb);
     if (s != SPDBA_OK) return latch(p, s);
-    double esz = p->precision == SPDBA_C64 ? 8.0 : 16.0;
-    for (size_t i = 0; i < lm.size() && i < p->prof_list_modes0.size(); ++i)
-        agg[K_UPDATE_LIST].bytes += 3.0 * esz * (lm[i] - p->prof_list_modes0[i]);
+    agg[K_UPDATE_LIST].bytes += lb - p->prof_list_bytes0;
     int n = 0;
     for (int k = 0; k < K_COUNT && n < capacity; ++k)
         if (agg[k].launches > 0 && out) out[n++] = agg[k];

@@ -62,7 +62,8 @@ __device__ __forceinline__ void store2(double2* p, double2 a, double2 b) { p[0] 
 template <typename T>
 __global__ void ch_dense_kernel(Geom g, CHUpdateArgs<T> a) {
     const long long npairs = g.modes() / 2;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) a.stats->ratio_sum += 1.0;
+    if (blockIdx.x == 0 && a.stats)
+        for (long long r = threadIdx.x; r < g.runs(); r += blockDim.x) a.stats[r].ratio_sum += 1.0;
     for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < npairs;
          u += (long long)gridDim.x * blockDim.x) {
         long long e = 2 * u;
@@ -104,9 +105,13 @@ __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
     const int cnt = *a.count;
     const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
     const long long nmodes = (long long)B0 * B1 * B2;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
-        a.stats->ratio_sum += (double)cnt * a.inv_nblocks;
-        a.stats->list_modes += (double)cnt * (double)nmodes;
+    if (blockIdx.x == 0 && a.stats) {
+        const double inv = 1.0 / (double)g.bpr();
+        for (long long r = threadIdx.x; r < g.runs(); r += blockDim.x) {
+            double nf = (double)(a.stats[r].n_active + a.stats[r].n_transition);
+            a.stats[r].ratio_sum += nf * inv;
+            a.stats[r].list_modes += nf * (double)nmodes;
+        }
     }
     const int H = B2 / 2;
     const long long npair = nmodes / 2;

@@ -1,0 +1,123 @@
+"""Split-step NLS on the GPU against the oracle, through the C ABI.
+
+Masks are checked in lock-step on the GPU's own spectrum (promoted to FP64);
+the oracle then re-runs the steps with the GPU's states so that the field
+comparison measures arithmetic error only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from _helpers import states_within_tie_band
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_nls(lengths, signals, steps, precision=0, nblk=64, R=10, thr=1e-6, lockstep=True, **kw):
+    from paper_2609_03922_gb300 import spdba
+    cdt = np.complex64 if precision == 0 else np.complex128
+    plan = spdba.Plan(None, (-nblk,), threshold=thr, reassess=R, batch_dims=[(n,) for n in lengths],
+                      model=spdba.SPDBA_MODEL_NLS, precision=precision, **kw)
+    for r, E in enumerate(signals):
+        plan.set_field(np.ascontiguousarray(E.astype(cdt)), run=r)
+    masks = [dict() for _ in lengths]
+    spectra = [dict() for _ in lengths]
+    mode = kw.get("mode", 1)
+    for s in range(steps):
+        if mode == 1 and s % R == 0 and lockstep:
+            for r in range(len(lengths)):
+                spectra[r][s] = plan.get_spectrum(run=r)
+            plan.step(1)
+            for r in range(len(lengths)):
+                masks[r][s] = plan.get_mask(run=r)
+        else:
+            plan.step(1)
+    fields = [plan.get_field(run=r) for r in range(len(lengths))]
+    stats = [plan.get_stats(run=r) for r in range(len(lengths))]
+    plan.close()
+    return fields, masks, spectra, stats
+
+
+def check_nls(lengths, signals, steps, tol, precision=0, R=10, thr=1e-6, **kw):
+    fields, masks, spectra, stats = gpu_nls(lengths, signals, steps, precision=precision, R=R, thr=thr, **kw)
+    cdt = np.complex64 if precision == 0 else np.complex128
+    errs = []
+    for r, (n, E0) in enumerate(zip(lengths, signals)):
+        cfg = O.NLSConfig(n, n // 64, threshold=thr, reassess=R, mode=kw.get("mode", 1),
+                          transitions=bool(kw.get("transitions", 1)))
+        for s, sp in spectra[r].items():
+            st, tau, meas = O.assess_states(sp.astype(np.complex128), cfg, exclude_dc=False)
+            ok, nties = states_within_tie_band(masks[r][s], meas, tau, cfg)
+            assert ok, "signal %d step %d: states differ (%d tie-band blocks)" % (r, s, nties)
+        ref, _ = O.run_nls(E0.astype(cdt).astype(np.complex128), cfg, steps,
+                           on_assess=lambda s, E, st, tau, r=r: masks[r].get(s))
+        err = O.rel_l2(fields[r], ref)
+        errs.append(err)
+        assert err <= tol, "signal %d (n=%d): rel-L2 %.3e > %.1e" % (r, n, err, tol)
+    return fields, stats, errs
+
+
+@pytest.mark.parametrize("n", [1024, 4096, 8192, 65536])
+def test_single_signal_adaptive(n):
+    E0 = W.nls_signal(n, seed=W.BASE_SEED + n)
+    check_nls([n], [E0], 25, 1e-5, thr=1e-3)
+
+
+@pytest.mark.parametrize("n,precision,tol", [(4096, 1, 1e-12), (16384, 1, 1e-12), (2048, 0, 2e-6), (262144, 0, 2e-6)])
+def test_cw_exact_solution_dense(n, precision, tol):
+    """A CW on a bin evolves as A exp(i (beta2 w0^2 / 2 + gamma |A|^2) z), also on the GPU."""
+    m, A, steps = 37, 0.1, 20
+    E0 = W.nls_cw(n, m, A)
+    fields, _, _, _ = gpu_nls([n], [E0], steps, precision=precision, mode=0)
+    w0 = 2 * math.pi * m / n
+    expect = E0 * np.exp(1j * (-21.7 * w0 * w0 / 2 + 1.3 * A * A) * steps * 0.1)
+    assert np.max(np.abs(fields[0] - expect)) <= tol * A * (1 + steps)
+
+
+def test_mixed_length_batch_one_plan():
+    lengths = [4096, 8192, 2048, 4096, 32768, 8192]
+    signals = [W.nls_signal(n, seed=W.BASE_SEED + 100 + i) for i, n in enumerate(lengths)]
+    _, stats, _ = check_nls(lengths, signals, 21, 1e-5, thr=1e-2, R=7)
+    assert all(s["step"] == 21 and s["assessments"] == 3 for s in stats)
+
+
+@pytest.mark.parametrize("n", [4096, 65536])
+def test_threshold_zero_equals_regular_on_gpu(n):
+    E0 = W.nls_signal(n, seed=W.BASE_SEED + 5)
+    a, masks, _, _ = gpu_nls([n], [E0], 12, thr=0.0, R=4)
+    b, _, _, _ = gpu_nls([n], [E0], 12, mode=0)
+    assert np.array_equal(a[0], b[0])
+    assert all(np.all(m == 2) for m in masks[0].values())
+
+
+@pytest.mark.parametrize("n", [4096, 131072])
+def test_energy_conserved_and_reported(n):
+    """alpha = 0: the split-step operators are unitary; the FP64 power sum is reported."""
+    E0 = W.nls_signal(n, seed=W.BASE_SEED + 9)
+    fields, _, _, stats = gpu_nls([n], [E0], 30, thr=1e-3, transitions=0, lockstep=False)
+    e0 = float(np.sum(np.abs(E0.astype(np.complex64).astype(np.complex128)) ** 2))
+    assert abs(np.sum(np.abs(fields[0].astype(np.complex128)) ** 2) - e0) <= 2e-5 * e0
+    assert abs(stats[0]["mass"] - e0) <= 2e-5 * e0
+
+
+def test_transmission_80km_full_run_fp32():
+    """The configuration's propagation: h = 0.1 km over 80 km (800 steps), 1/64-length
+    blocks, tau = 1e-6 max|E~|, R = 10, complex64 vs the FP64 oracle."""
+    n = 8192
+    E0 = W.nls_signal(n, seed=W.BASE_SEED + 11)
+    check_nls([n], [E0], 800, 1e-4)
+
+
+def test_backpropagation_recovers_transmitted_field():
+    """Dense forward propagation on the GPU, then sp-DBA back-propagation with the
+    negated (beta2, gamma): NMSE <= -20 dB (S5.3)."""
+    n, steps = 4096, 200
+    E_tx = W.nls_signal(n, seed=W.BASE_SEED + 8)
+    rx, _, _, _ = gpu_nls([n], [E_tx], steps, mode=0)
+    rec, masks, _, _ = gpu_nls([n], [rx[0].astype(np.complex128)], steps, thr=1e-2, beta2=21.7, gamma=-1.3,
+                               lockstep=False)
+    assert O.nmse_db(rec[0], E_tx) <= -20.0
+    assert O.field_corr(rec[0], E_tx) >= 0.998
