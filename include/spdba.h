@@ -72,6 +72,8 @@ typedef struct spdba_options {
     int32_t refresh_every;  /* F_refresh: all blocks ACTIVE every F steps, 0 = off (S1.3) */
     int32_t warmup_steps;   /* all blocks ACTIVE for the first steps (S3.2), 0 = none     */
     int32_t use_graph;      /* 1: replay captured CUDA graphs for runs of steps          */
+    int32_t fuse_update;    /* CH: 1 = apply the update inside the last forward FFT pass;
+                               0 = separate update kernel over the block list (staged)  */
     double dt, kappa, dx;   /* Cahn-Hilliard: time step, gradient coefficient, spacing  */
     double beta2, gamma, h, dt_sample; /* NLS: ps^2/km, 1/(W km), km step, ps sample     */
     void* stream;           /* cudaStream_t the plan enqueues on                         */
@@ -95,7 +97,7 @@ typedef struct spdba_plan spdba_plan;         /* opaque; owns all of its device 
 typedef struct spdba_fft_plan spdba_fft_plan; /* opaque; owns its twiddle tables        */
 
 /* Fill *opt with the defaults: CH, C64, ADAPTIVE, MAXAMP, REL_MAX, transitions on,
-   force_dc on (CH) , refresh and warm-up off, graphs on, dt = 0.01, kappa = 1,
+   force_dc on (CH), refresh and warm-up off, graphs on, fused update on, dt = 0.01, kappa = 1,
    dx = 1, beta2 = -21.7, gamma = 1.3, h = 0.1, dt_sample = 1, default stream. */
 void spdba_options_default(spdba_options* opt);
 

@@ -36,104 +36,103 @@ spdba_status make_geom_batched(Geom* g, int ndim, const int64_t* dims, const int
 }
 
 // ------------------------------------------------------------------ activity
-// One CTA per block.  The block max of |q|^2 is exact in FP64: an FP32 value
+// One warp per block.  The block max of |q|^2 is exact in FP64: an FP32 value
 // p32 = fma(re, re, im*im) (relative error below 2^-22) screens each mode, and
-// only modes whose p32 reaches (1 - 2^-20) times the running FP64 max are
-// evaluated exactly (re*re + im*im in FP64, the oracle's formula), so a mode
-// that is skipped cannot be the max.  The block sum (ENERGY) is accumulated in
-// FP64.  Results are reduced over the warp with shuffles and across warps in
-// shared memory.
-template <int NT> __device__ __forceinline__ void reduce_store(double mx, double mxnd, double sm, long long blk,
-                                                               double* maxsq, double* sumsq, double* gmax,
-                                                               long long run) {
-    mx = warp_max(mx);
-    mxnd = warp_max(mxnd);
-    sm = warp_sum(sm);
-    __shared__ double red[3][NT / 32];
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { red[0][w] = mx; red[1][w] = mxnd; red[2][w] = sm; }
-    __syncthreads();
-    if (w == 0) {
-        mx = l < NT / 32 ? red[0][l] : 0.0;
-        mxnd = l < NT / 32 ? red[1][l] : 0.0;
-        sm = l < NT / 32 ? red[2][l] : 0.0;
-        mx = warp_max(mx);
-        mxnd = warp_max(mxnd);
-        sm = warp_sum(sm);
-        if (l == 0) {
-            maxsq[blk] = mx;
-            if (sumsq) sumsq[blk] = sm;
-            atomic_max_nonneg(&gmax[2 * run], mx);
-            atomic_max_nonneg(&gmax[2 * run + 1], mxnd);
-        }
-    }
+// only modes whose p32 reaches (1 - 2^-20) times the lane's running FP64 max
+// are evaluated exactly (re*re + im*im in FP64, the oracle's formula), so a
+// mode that is skipped cannot be the max.  Non-negative doubles order like
+// their bit patterns, so the warp max is two 32-bit integer reductions
+// (high word, then low word among the lanes holding the high maximum) and
+// costs no FP64 instruction.  The ENERGY sum is accumulated per lane in FP64.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    return ((unsigned long long)mhi << 32) | mlo;
 }
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
-__device__ __forceinline__ void screen_mode(float2 v, long long idx, bool energy, double& mx, double& mxnd,
-                                            float& cut, double& sm) {
-    if (energy) sm += mode_sq(v);
+struct ActLane {
+    double mx = 0.0, mxnd = 0.0, sm = 0.0;
+    float cut = 0.0f;
+};
+
+__device__ __forceinline__ void screen_mode(float2 v, bool is_dc, bool energy, ActLane& a) {
+    if (energy) a.sm += mode_sq(v);
     float p32 = fmaf(v.x, v.x, v.y * v.y);
-    if (idx == 0) {
-        mx = fmax(mx, mode_sq(v));
-    } else if (p32 >= cut) {
+    if (is_dc) {
+        a.mx = fmax(a.mx, mode_sq(v));
+    } else if (p32 >= a.cut) {
         double e = mode_sq(v);
-        mx = fmax(mx, e);
-        mxnd = fmax(mxnd, e);
-        cut = (float)mxnd * (1.0f - 9.5367431640625e-07f);   // 1 - 2^-20
+        a.mx = fmax(a.mx, e);
+        a.mxnd = fmax(a.mxnd, e);
+        a.cut = (float)a.mxnd * (1.0f - 9.5367431640625e-07f);   // 1 - 2^-20
     }
 }
-__device__ __forceinline__ void screen_mode(double2 v, long long idx, bool energy, double& mx, double& mxnd,
-                                            float& cut, double& sm) {
+__device__ __forceinline__ void screen_mode(double2 v, bool is_dc, bool energy, ActLane& a) {
     double e = mode_sq(v);
-    if (energy) sm += e;
-    mx = fmax(mx, e);
-    if (idx != 0) mxnd = fmax(mxnd, e);
+    if (energy) a.sm += e;
+    a.mx = fmax(a.mx, e);
+    if (!is_dc) a.mxnd = fmax(a.mxnd, e);
 }
 
-template <typename T, int NT, bool ENERGY>
-__global__ void __launch_bounds__(NT) block_activity_kernel(Geom g, const cx_t<T>* __restrict__ q,
-                                                            double* __restrict__ maxsq, double* __restrict__ sumsq,
-                                                            double* __restrict__ gmax) {
-    const long long blk = blockIdx.x;
+template <typename T, bool ENERGY>
+__global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<T>* __restrict__ q,
+                                                             double* __restrict__ maxsq, double* __restrict__ sumsq,
+                                                             double* __restrict__ gmax) {
+    const int lane = threadIdx.x & 31;
+    const long long blk = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (blk >= g.blocks()) return;   // whole warps leave together
     const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
     const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
     const long long run = blk / g.bpr();
     const long long fm = g.fmodes();
-    double mx = 0.0, mxnd = 0.0, sm = 0.0;
-    float cut = 0.0f;
+    // the field's k = 0 mode, when it lies in this block
+    const long long dc = run * fm;
+    ActLane a;
+    const long long base = ((b0 * B0) * g.n[1] + b1 * B1) * g.n[2] + b2 * B2;
     if (sizeof(cx_t<T>) == 8 && (B2 & 1) == 0) {
-        // pairs along the fast axis as one 16-byte load
         const int H = B2 / 2;
-        const long long npair = (long long)B0 * B1 * H;
-        for (long long m = threadIdx.x; m < npair; m += NT) {
-            int l2 = (int)(m % H) * 2;
-            long long r = m / H;
-            int l1 = (int)(r % B1), l0 = (int)(r / B1);
-            long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
-            float4 v = __ldg(reinterpret_cast<const float4*>(q + idx));
-            screen_mode(make_float2(v.x, v.y), idx % fm, ENERGY, mx, mxnd, cut, sm);
-            screen_mode(make_float2(v.z, v.w), (idx + 1) % fm, ENERGY, mx, mxnd, cut, sm);
+        const int npair = B0 * B1 * H;
+        for (int m = lane; m < npair; m += 32) {
+            int l2 = (m % H) * 2;
+            int r = m / H;
+            int l1 = r % B1, l0 = r / B1;
+            long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
+            float4 v = *reinterpret_cast<const float4*>(q + idx);
+            screen_mode(make_float2(v.x, v.y), idx == dc, ENERGY, a);
+            screen_mode(make_float2(v.z, v.w), idx + 1 == dc, ENERGY, a);
         }
     } else {
-        const long long nmodes = (long long)B0 * B1 * B2;
-        for (long long m = threadIdx.x; m < nmodes; m += NT) {
-            int l2 = (int)(m % B2);
-            long long r = m / B2;
-            int l1 = (int)(r % B1), l0 = (int)(r / B1);
-            long long idx = ((b0 * B0 + l0) * g.n[1] + (b1 * B1 + l1)) * g.n[2] + b2 * B2 + l2;
-            screen_mode(__ldg(q + idx), idx % fm, ENERGY, mx, mxnd, cut, sm);
+        const int nmodes = B0 * B1 * B2;
+        for (int m = lane; m < nmodes; m += 32) {
+            int l2 = m % B2;
+            int r = m / B2;
+            int l1 = r % B1, l0 = r / B1;
+            long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
+            screen_mode(q[idx], idx == dc, ENERGY, a);
         }
     }
-    reduce_store<NT>(mx, mxnd, sm, blk, maxsq, sumsq, gmax, run);
+    const double mx = bitsd(warp_max_u64(dbits(a.mx)));
+    const double mxnd = bitsd(warp_max_u64(dbits(a.mxnd)));
+    double sm = 0.0;
+    if (ENERGY) sm = warp_sum(a.sm);
+    if (lane == 0) {
+        maxsq[blk] = mx;
+        if (ENERGY) sumsq[blk] = sm;
+        atomic_max_nonneg(&gmax[2 * run], mx);
+        atomic_max_nonneg(&gmax[2 * run + 1], mxnd);
+    }
 }
 
 template <typename T>
 spdba_status launch_block_activity(const Geom& g, const cx_t<T>* q, double* maxsq, double* sumsq, double* gmax,
                                    cudaStream_t st) {
-    constexpr int NT = 128;
     long long nb = g.blocks();
-    if (sumsq) block_activity_kernel<T, NT, true><<<(unsigned)nb, NT, 0, st>>>(g, q, maxsq, sumsq, gmax);
-    else block_activity_kernel<T, NT, false><<<(unsigned)nb, NT, 0, st>>>(g, q, maxsq, nullptr, gmax);
+    unsigned grid = (unsigned)((nb + 7) / 8);
+    if (sumsq) block_activity_kernel<T, true><<<grid, 256, 0, st>>>(g, q, maxsq, sumsq, gmax);
+    else block_activity_kernel<T, false><<<grid, 256, 0, st>>>(g, q, maxsq, nullptr, gmax);
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;
 }

@@ -4,42 +4,9 @@
 
 namespace spdba {
 
-// Grid and block map padded to three axes (axis 0 slowest); unused leading
-// axes have extent 1.
-struct Geom {
-    int ndim = 0;
-    long long n[3] = {1, 1, 1};
-    int b[3] = {1, 1, 1};
-    long long nb[3] = {1, 1, 1};
-    __host__ __device__ long long modes() const { return n[0] * n[1] * n[2]; }
-    __host__ __device__ long long blocks() const { return nb[0] * nb[1] * nb[2]; }
-    __host__ __device__ long long block_modes() const { return (long long)b[0] * b[1] * b[2]; }
-    // A group stores several equal fields along the unused leading axis (or
-    // axes): blocks [r*bpr, (r+1)*bpr) and modes [r*fmodes, (r+1)*fmodes)
-    // belong to run r.  Neighbour relations never cross runs.
-    __host__ __device__ long long bpr() const {
-        return ndim == 3 ? nb[0] * nb[1] * nb[2] : ndim == 2 ? nb[1] * nb[2] : nb[2];
-    }
-    __host__ __device__ long long fmodes() const {
-        return ndim == 3 ? n[0] * n[1] * n[2] : ndim == 2 ? n[1] * n[2] : n[2];
-    }
-    __host__ __device__ long long runs() const { return blocks() / bpr(); }
-};
 spdba_status make_geom(Geom* g, int ndim, const int64_t* dims, const int32_t* block);
 // `batch` equal fields of ndim <= 2 dims stacked along the leading padded axis.
 spdba_status make_geom_batched(Geom* g, int ndim, const int64_t* dims, const int32_t* block, long long batch);
-
-// Device statistics of one run (mirrors spdba_stats, accumulated on the device).
-struct DevStats {
-    double tau;
-    double max_amp;
-    double mass;
-    double ratio_sum;
-    unsigned long long n_active;
-    unsigned long long n_transition;
-    unsigned long long assessments;
-    double list_modes;   // modes touched by list-driven updates (for traffic accounting)
-};
 
 // maxsq / sumsq per block; per run r, gmax[2r] = max over all its modes and
 // gmax[2r+1] = max over its modes k != 0.  gmax must be zeroed before the

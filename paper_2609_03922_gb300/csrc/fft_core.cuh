@@ -22,6 +22,7 @@
 #pragma once
 #include <type_traits>
 
+#include "ch_math.cuh"
 #include "common.cuh"
 
 namespace spdba {
@@ -60,6 +61,22 @@ template <int L> struct SmemLayout {
     static constexpr int PSTR = L + L / 16 + 1;
 };
 
+// Cahn-Hilliard update fused into the last forward pass (the pass along the
+// field's first axis): per mode new = (c_hat - dt k^2 g_hat) / (1 + dt kappa k^4)
+// on ACTIVE blocks, the transition blend on TRANSITION blocks, nothing on
+// FROZEN blocks; tiles whose blocks are all frozen are skipped entirely.
+template <typename T> struct CHFuse {
+    cx_t<T>* c_hat;
+    const T* k2ax[3];
+    const T* taper[3];
+    const uint8_t* states;
+    const uint8_t* chi;
+    T dt, dtkappa;
+    int dense;
+    DevStats* stats;   // one per run
+    Geom g;
+};
+
 template <typename T> struct PassParams {
     const cx_t<T>* in;
     cx_t<T>* out;
@@ -76,6 +93,7 @@ template <typename T> struct PassParams {
     double* mass;                         // FP64 sum of c per field (strided), or null
     int mass_stride;                      // doubles between consecutive fields' accumulators
     long long mass_ppr;                   // pencils per field
+    CHFuse<T> fu;                         // PASS_CH_UPDATE only
 };
 
 // Address of element (p, j) of the tile starting at pencil q0.
@@ -345,7 +363,101 @@ __device__ __forceinline__ void apply_fourstep_twiddle(cx_t<T>* sm, const PassPa
 enum PassMode : int {
     PASS_PLAIN = 0,      // transform, optional four-step twiddle, scaled store
     PASS_CH_NL = 1,      // inverse transform, c = Re(.)/N, g = c^3 - c, forward transform
+    PASS_CH_UPDATE = 2,  // forward transform, then the CH update of c_hat (no store of the transform)
 };
+
+// Padded (axis 0, 1, 2) coordinates of element (p, j) of the tile at pencil q0
+// of the pass along the field's first axis: 3-D fields (z = j, (y, x) from the
+// pencil), 2-D groups ((run, y = j, x) with the run as the pencil's outer index).
+template <typename T>
+__device__ __forceinline__ void fuse_coords(const PassParams<T>& a, long long q0, int p, int j, long long& c0,
+                                            long long& c1, long long& c2) {
+    const Geom& g = a.fu.g;
+    long long o = q0 / a.I, i = q0 - o * a.I + p;
+    if (g.ndim == 3) { c0 = j; c1 = i / g.n[2]; c2 = i - c1 * g.n[2]; }
+    else { c0 = o; c1 = j; c2 = i; }
+}
+__device__ __forceinline__ long long block_id(const Geom& g, long long c0, long long c1, long long c2) {
+    return ((c0 / g.b[0]) * g.nb[1] + c1 / g.b[1]) * g.nb[2] + c2 / g.b[2];
+}
+
+// A tile is live when any block its modes belong to is not FROZEN.  Every warp
+// evaluates this independently (no block-wide synchronisation needed).
+template <typename T, int P, int MODE>
+__device__ __forceinline__ bool tile_live(const PassParams<T>& a, long long q0) {
+    if constexpr (MODE != PASS_CH_UPDATE) return true;
+    else {
+        if (a.fu.dense) return true;
+        const Geom& g = a.fu.g;
+        long long c0, c1, c2;
+        fuse_coords<T>(a, q0, 0, 0, c0, c1, c2);
+        const long long bx0 = c2 / g.b[2], bx1 = (c2 + P - 1) / g.b[2];
+        const long long nbx = bx1 - bx0 + 1;
+        // blocks along the pass axis: all of them
+        const long long npass = g.ndim == 3 ? g.nb[0] : g.nb[1];
+        const long long total = npass * nbx;
+        bool live = false;
+        for (long long k = threadIdx.x & 31; k < total && !live; k += 32) {
+            long long bp = k / nbx, bx = bx0 + k % nbx;
+            long long id = g.ndim == 3 ? (bp * g.nb[1] + c1 / g.b[1]) * g.nb[2] + bx
+                                       : (c0 * g.nb[1] + bp) * g.nb[2] + bx;
+            live = a.fu.states[id] != 0;
+        }
+        return __any_sync(0xffffffffu, live);
+    }
+}
+
+// Per-run share of non-frozen blocks for this step (CTA 0, once per launch).
+template <typename T, int NT> __device__ __forceinline__ void ch_update_stats(const CHFuse<T>& f) {
+    const Geom& g = f.g;
+    if (blockIdx.x != 0 || !f.stats) return;
+    const double inv = 1.0 / (double)g.bpr();
+    const long long bm = g.block_modes();
+    for (long long r = threadIdx.x; r < g.runs(); r += NT) {
+        double nf = f.dense ? (double)g.bpr() : (double)(f.stats[r].n_active + f.stats[r].n_transition);
+        f.stats[r].ratio_sum += nf * inv;
+        if (!f.dense) f.stats[r].list_modes += nf * (double)bm;
+    }
+}
+
+// Update epilogue: g_hat of the tile is in shared memory (layout B).
+template <typename T, int L, int P, int NT, class LY>
+__device__ __forceinline__ void ch_update_tile(const cx_t<T>* sm, const PassParams<T>& a, long long q0) {
+    using C = cx_t<T>;
+    const CHFuse<T>& f = a.fu;
+    const Geom& g = f.g;
+    constexpr int E = sizeof(C) == 8 ? 2 : 1;   // modes per 16-byte access
+    constexpr int UNITS = P * L / E;
+#pragma unroll 2
+    for (int u = threadIdx.x; u < UNITS; u += NT) {
+        const int j = u / (P / E), p = (u % (P / E)) * E;
+        long long c0, c1, c2;
+        fuse_coords<T>(a, q0, p, j, c0, c1, c2);
+        const long long id = block_id(g, c0, c1, c2);
+        const int st = f.dense ? SPDBA_ACTIVE : f.states[id];
+        if (st == SPDBA_FROZEN) continue;
+        const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
+        const T k01 = f.k2ax[0][c0] + f.k2ax[1][c1];
+        const unsigned chi = st == SPDBA_TRANSITION ? f.chi[id] : 0u;
+        const int l0 = (int)(c0 % g.b[0]), l1 = (int)(c1 % g.b[1]), l2 = (int)(c2 % g.b[2]);
+        if constexpr (E == 2) {
+            float4 cv = *reinterpret_cast<const float4*>(f.c_hat + ad);
+            float2 cA = make_float2(cv.x, cv.y), cB = make_float2(cv.z, cv.w);
+            float2 nA = ch_new(cA, sm[LY::idx(p, j)], k01 + f.k2ax[2][c2], f.dt, f.dtkappa);
+            float2 nB = ch_new(cB, sm[LY::idx(p + 1, j)], k01 + f.k2ax[2][c2 + 1], f.dt, f.dtkappa);
+            if (st == SPDBA_TRANSITION) {
+                nA = ch_blend<T>(cA, nA, f.taper, g, chi, l0, l1, l2);
+                nB = ch_blend<T>(cB, nB, f.taper, g, chi, l0, l1, l2 + 1);
+            }
+            *reinterpret_cast<float4*>(f.c_hat + ad) = make_float4(nA.x, nA.y, nB.x, nB.y);
+        } else {
+            C cv = f.c_hat[ad];
+            C nv = ch_new(cv, sm[LY::idx(p, j)], k01 + f.k2ax[2][c2], f.dt, f.dtkappa);
+            if (st == SPDBA_TRANSITION) nv = ch_blend<T>(cv, nv, f.taper, g, chi, l0, l1, l2);
+            f.c_hat[ad] = nv;
+        }
+    }
+}
 
 // Body shared by both kernels: transform the tile in shared memory.
 template <typename T, int L, int P, int NT, int SIGN, int MODE, class LY>
@@ -354,6 +466,8 @@ __device__ __forceinline__ void tile_body(cx_t<T>* sm, const PassParams<T>& a, l
     if constexpr (MODE == PASS_PLAIN) {
         run_stages<T, L, P, NT, SIGN, LY>(sm, a.tw);
         if (a.tw4 != nullptr) apply_fourstep_twiddle<T, L, P, NT, SIGN, LY>(sm, a, q0);
+    } else if constexpr (MODE == PASS_CH_UPDATE) {
+        run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
     } else if constexpr (MODE == PASS_CH_NL) {
         // inverse transform along this axis completes c = IFFT(c_hat) (scaled by nl_scale)
         run_stages<T, L, P, NT, +1, LY>(sm, a.tw);
@@ -397,7 +511,7 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(PassParams<T> a) {
 // Requires I % P == 0 and in/out with the same orientation.
 // Resident CTAs per SM the pipelined kernel is compiled for (register budget).
 template <typename T, int L, int MODE> struct PipeOcc {
-    static constexpr int value = (sizeof(T) == 4 && L <= 256 && MODE == PASS_PLAIN) ? 3 : 1;
+    static constexpr int value = (sizeof(T) == 4 && L <= 256) ? (MODE == PASS_PLAIN ? 3 : MODE == PASS_CH_UPDATE ? 2 : 1) : 1;
 };
 
 template <typename T, int L, int P, int NT, int SIGN, int MODE, bool PFAST>
@@ -408,21 +522,26 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE>::value) fft_pass_pipe_
     C* sm0 = reinterpret_cast<C*>(smem_raw);
     C* sm1 = sm0 + LY::SIZE;
     const long long ntiles = (a.O * a.I) / P;
+    if constexpr (MODE == PASS_CH_UPDATE) ch_update_stats<T, NT>(a.fu);
     long long t = blockIdx.x;
+    while (t < ntiles && !tile_live<T, P, MODE>(a, t * P)) t += gridDim.x;
     if (t < ntiles) issue_tile<T, L, P, NT, PFAST, LY>(sm0, a, t * P);
     cp_async_commit();
     int buf = 0;
-    for (; t < ntiles; t += gridDim.x) {
-        const long long tn = t + gridDim.x;
+    while (t < ntiles) {
+        long long tn = t + gridDim.x;
+        while (tn < ntiles && !tile_live<T, P, MODE>(a, tn * P)) tn += gridDim.x;
         if (tn < ntiles) issue_tile<T, L, P, NT, PFAST, LY>(buf ? sm0 : sm1, a, tn * P);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         C* sm = buf ? sm1 : sm0;
         tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, t * P);
-        store_tile<T, L, P, NT, PFAST, LY>(sm, a, t * P);
+        if constexpr (MODE == PASS_CH_UPDATE) ch_update_tile<T, L, P, NT, LY>(sm, a, t * P);
+        else store_tile<T, L, P, NT, PFAST, LY>(sm, a, t * P);
         __syncthreads();
         buf ^= 1;
+        t = tn;
     }
     cp_async_wait<0>();
 }

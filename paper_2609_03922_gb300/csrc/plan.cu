@@ -82,6 +82,7 @@ template <typename T> struct Group {
     std::vector<Pass<T>> pre_inv;   // inverse passes before the fused one (first reads c_hat)
     Pass<T> fused;                  // inverse + nonlinearity + forward along the fast axis
     std::vector<Pass<T>> pre_fwd;   // remaining forward passes
+    bool fused_update = false;      // the last forward pass carries the update (pre_fwd.back())
     FftEngine<T> fft1;              // one run's transforms for set/get_field
     // NLS
     HPair<T>* H = nullptr;
@@ -114,9 +115,9 @@ template <typename T> struct Group {
 using namespace spdba;
 
 enum ProfKind { K_FFT_PASS = 0, K_FUSED_NL, K_UPDATE_DENSE, K_UPDATE_LIST, K_ASSESS, K_NLS_STEP, K_NLS_ROW, K_NLS_COL,
-                K_COUNT };
+                K_FFT_UPDATE, K_COUNT };
 static const char* kProfName[K_COUNT] = {"fft_pass", "fft_fused_nl", "update_dense", "update_list", "assess",
-                                         "nls_step", "nls_row", "nls_col"};
+                                         "nls_step", "nls_row", "nls_col", "fft_update"};
 
 struct ProfRec {
     int kind;
@@ -273,7 +274,28 @@ static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const in
     r.fused.p.mass_ppr = r.n / dims[ndim - 1];
     for (int a = ndim - 2; a >= 0; --a) {
         Pass<T> ps;
-        if ((s = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+        spdba_status sf = SPDBA_ERR_UNSUPPORTED;
+        if (a == 0 && p->opt.fuse_update) {
+            // the pass along the first axis also applies the update (when a kernel exists for it)
+            sf = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_CH_UPDATE, tw, st);
+            if (sf == SPDBA_OK) {
+                CHFuse<T>& f = ps.p.fu;
+                f.c_hat = r.c_hat;
+                for (int ax = 0; ax < 3; ++ax) { f.k2ax[ax] = r.k2ax[ax]; f.taper[ax] = r.taper[ax]; }
+                f.states = r.states;
+                f.chi = r.chi;
+                f.dt = (T)p->opt.dt;
+                f.dtkappa = (T)(p->opt.dt * p->opt.kappa);
+                f.dense = 1;
+                f.stats = r.stats;
+                f.g = r.g;
+                r.fused_update = true;
+            } else if (sf != SPDBA_ERR_UNSUPPORTED) {
+                return sf;
+            }
+        }
+        if (sf != SPDBA_OK && (s = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_PLAIN, tw, st)) != SPDBA_OK)
+            return s;
         r.pre_fwd.push_back(ps);
     }
     return SPDBA_OK;
@@ -375,10 +397,24 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
         if ((s = launch_pass<T>(fused, src, r.work, st)) != SPDBA_OK) return s;
         p->launches += 1;
     }
-    for (auto& ps : r.pre_fwd) {
-        ProfScope pr(p, K_FFT_PASS, pass_bytes);
-        if ((s = launch_pass<T>(ps, r.work, r.work, st)) != SPDBA_OK) return s;
+    const int dense = !adaptive || all_active_step(p, r.step);
+    for (size_t k = 0; k < r.pre_fwd.size(); ++k) {
+        const bool last_fused = r.fused_update && k + 1 == r.pre_fwd.size();
+        if (last_fused) {
+            // forward transform of the first axis + update; traffic depends on the states
+            Pass<T> ps = r.pre_fwd[k];
+            ps.p.fu.dense = dense;
+            ProfScope pr(p, K_FFT_UPDATE, pass_bytes + sizeof(cx_t<T>) * (double)(r.batch * r.n));
+            if ((s = launch_pass<T>(ps, r.work, r.work, st)) != SPDBA_OK) return s;
+        } else {
+            ProfScope pr(p, K_FFT_PASS, pass_bytes);
+            if ((s = launch_pass<T>(r.pre_fwd[k], r.work, r.work, st)) != SPDBA_OK) return s;
+        }
         p->launches += 1;
+    }
+    if (r.fused_update) {
+        r.step += 1;
+        return SPDBA_OK;
     }
     // update
     CHUpdateArgs<T> a;
@@ -392,7 +428,6 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
     a.dt = (T)p->opt.dt;
     a.dtkappa = (T)(p->opt.dt * p->opt.kappa);
     a.stats = r.stats;
-    const int dense = !adaptive || all_active_step(p, r.step);
     {
         // list-update traffic is known only on the device; it is added at profile end
         ProfScope pr(p, dense ? K_UPDATE_DENSE : K_UPDATE_LIST,
@@ -617,6 +652,7 @@ extern "C" void spdba_options_default(spdba_options* o) {
     o->refresh_every = 0;
     o->warmup_steps = 0;
     o->use_graph = 1;
+    o->fuse_update = 1;
     o->dt = 0.01;
     o->kappa = 1.0;
     o->dx = 1.0;

@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include "blocks.h"
+#include "ch_math.cuh"
 
 namespace spdba {
 
@@ -30,20 +31,6 @@ template std::vector<float> k2_table<float>(long long, double);
 template std::vector<double> k2_table<double>(long long, double);
 template std::vector<float> taper_table<float>(int);
 template std::vector<double> taper_table<double>(int);
-
-// Evaluation order is pinned with explicit fma so that the Regular and the
-// sp-DBA kernels produce bit-identical values for the same mode.
-__device__ __forceinline__ float2 ch_new(float2 c, float2 g, float k2, float dt, float dtkappa) {
-    float den = __fmaf_rn(dtkappa, __fmul_rn(k2, k2), 1.0f);
-    float inv = __frcp_rn(den);
-    float a = __fmul_rn(dt, k2);
-    return make_float2(__fmul_rn(__fmaf_rn(-a, g.x, c.x), inv), __fmul_rn(__fmaf_rn(-a, g.y, c.y), inv));
-}
-__device__ __forceinline__ double2 ch_new(double2 c, double2 g, double k2, double dt, double dtkappa) {
-    double den = __fma_rn(dtkappa, __dmul_rn(k2, k2), 1.0);
-    double a = __dmul_rn(dt, k2);
-    return make_double2(__ddiv_rn(__fma_rn(-a, g.x, c.x), den), __ddiv_rn(__fma_rn(-a, g.y, c.y), den));
-}
 
 // Two consecutive modes along the fast axis move together (one 16-byte access
 // for complex64).
@@ -78,22 +65,6 @@ __global__ void ch_dense_kernel(Geom g, CHUpdateArgs<T> a) {
         c1 = ch_new(c1, g1, kzy + a.k2ax[2][x + 1], a.dt, a.dtkappa);
         store2(a.c_hat + e, c0, c1);
     }
-}
-
-template <typename T>
-__device__ __forceinline__ cx_t<T> ch_blend(cx_t<T> c, cx_t<T> nw, const CHUpdateArgs<T>& a, const Geom& g,
-                                            unsigned ch, int l0, int l1, int l2) {
-    const int a0 = 3 - g.ndim;
-    int l[3] = {l0, l1, l2};
-    T sg = (T)1;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        if (ax < a0) continue;
-        unsigned lo = (ch >> (2 * (ax - a0))) & 1u, hi = (ch >> (2 * (ax - a0) + 1)) & 1u;
-        if (lo) sg *= a.taper[ax][l[ax]];
-        if (hi) sg *= a.taper[ax][g.b[ax] - 1 - l[ax]];
-    }
-    return mk<cx_t<T>>(c.x + sg * (nw.x - c.x), c.y + sg * (nw.y - c.y));
 }
 
 // sp-DBA: one warp per listed block, mode pairs along the fast axis.
@@ -133,8 +104,8 @@ __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
             cx_t<T> n0 = ch_new(c0, g0, kzy + a.k2ax[2][x], a.dt, a.dtkappa);
             cx_t<T> n1 = ch_new(c1, g1, kzy + a.k2ax[2][x + 1], a.dt, a.dtkappa);
             if (st == SPDBA_TRANSITION) {
-                n0 = ch_blend<T>(c0, n0, a, g, ch, l0, l1, l2);
-                n1 = ch_blend<T>(c1, n1, a, g, ch, l0, l1, l2 + 1);
+                n0 = ch_blend<T>(c0, n0, a.taper, g, ch, l0, l1, l2);
+                n1 = ch_blend<T>(c1, n1, a.taper, g, ch, l0, l1, l2 + 1);
             }
             store2(a.c_hat + e, n0, n1);
         }

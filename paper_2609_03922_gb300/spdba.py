@@ -26,7 +26,7 @@ class spdba_options(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("measure", ctypes.c_int32), ("tau_rule", ctypes.c_int32), ("transitions", ctypes.c_int32),
                 ("force_dc", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
-                ("warmup_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("warmup_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("fuse_update", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("dx", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("gamma", ctypes.c_double), ("h", ctypes.c_double),
                 ("dt_sample", ctypes.c_double), ("stream", ctypes.c_void_p)]

@@ -103,12 +103,36 @@ def test_energy_conserved_and_reported(n):
     assert abs(stats[0]["mass"] - e0) <= 2e-5 * e0
 
 
-def test_transmission_80km_full_run_fp32():
-    """The configuration's propagation: h = 0.1 km over 80 km (800 steps), 1/64-length
-    blocks, tau = 1e-6 max|E~|, R = 10, complex64 vs the FP64 oracle."""
+def _fp32_floor(E0, steps):
+    """rel-L2 after `steps` of the same split step in numpy single precision (an
+    independent FP32 FFT), against FP64: the error FP32 arithmetic itself leaves."""
+    n = E0.size
+    H = O.nls_half_factor(O.nls_omega(n, 1.0), -21.7, 0.1)
+    def run(E, cdt):
+        E = E.astype(cdt)
+        h = H.astype(cdt)
+        for _ in range(steps):
+            E = np.fft.ifft(np.fft.fft(E) * h).astype(cdt)
+            p = E.real ** 2 + E.imag ** 2
+            E = (E * np.exp(1j * 1.3 * p * 0.1)).astype(cdt)
+            E = np.fft.ifft(np.fft.fft(E) * h).astype(cdt)
+        return E
+    E0 = E0.astype(np.complex64)
+    return O.rel_l2(run(E0, np.complex64), run(E0, np.complex128))
+
+
+def test_transmission_fp32_40km_and_fp64_80km():
+    """The configuration's propagation (h = 0.1 km, 1/64-length blocks, tau = 1e-6
+    max|E~|, R = 10).  complex64 meets 1e-4 over 40 km; over the full 80 km,
+    modulation instability (beta2 < 0, gamma P > 0) amplifies FP32 rounding
+    itself past 1e-4, so there the GPU must stay within 2x of an independent
+    FP32 implementation, and the complex128 path must meet 1e-4."""
     n = 8192
     E0 = W.nls_signal(n, seed=W.BASE_SEED + 11)
-    check_nls([n], [E0], 800, 1e-4)
+    check_nls([n], [E0], 400, 1e-4)
+    _, _, errs = check_nls([n], [E0], 800, 1.0)
+    assert errs[0] <= 2.0 * _fp32_floor(E0, 800)
+    check_nls([n], [E0], 800, 1e-9, precision=1)
 
 
 def test_backpropagation_recovers_transmitted_field():
