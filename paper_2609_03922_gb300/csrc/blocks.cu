@@ -53,28 +53,22 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
-struct ActLane {
-    double mx = 0.0, mxnd = 0.0, sm = 0.0;
-    float cut = 0.0f;
-};
-
-__device__ __forceinline__ void screen_mode(float2 v, bool is_dc, bool energy, ActLane& a) {
-    if (energy) a.sm += mode_sq(v);
-    float p32 = fmaf(v.x, v.x, v.y * v.y);
-    if (is_dc) {
-        a.mx = fmax(a.mx, mode_sq(v));
-    } else if (p32 >= a.cut) {
-        double e = mode_sq(v);
-        a.mx = fmax(a.mx, e);
-        a.mxnd = fmax(a.mxnd, e);
-        a.cut = (float)a.mxnd * (1.0f - 9.5367431640625e-07f);   // 1 - 2^-20
+// exact FP64 |q|^2 for the modes of `mask` (a data-dependent loop, so the FP64
+// work is not speculated for every mode)
+template <int K>
+__device__ __forceinline__ void exact_candidates(const float2 (&v)[K], unsigned mask, unsigned dcmask, double& mx,
+                                                 double& mxnd) {
+    while (mask) {
+        int i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        double e = mode_sq(v[i]);
+        mx = fmax(mx, e);
+        if (!((dcmask >> i) & 1u)) mxnd = fmax(mxnd, e);
     }
 }
-__device__ __forceinline__ void screen_mode(double2 v, bool is_dc, bool energy, ActLane& a) {
-    double e = mode_sq(v);
-    if (energy) a.sm += e;
-    a.mx = fmax(a.mx, e);
-    if (!is_dc) a.mxnd = fmax(a.mxnd, e);
+
+__device__ __forceinline__ float warp_max_nonneg_f(float x) {
+    return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(x)));
 }
 
 template <typename T, bool ENERGY>
@@ -87,37 +81,61 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
     const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
     const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
     const long long run = blk / g.bpr();
-    const long long fm = g.fmodes();
-    // the field's k = 0 mode, when it lies in this block
-    const long long dc = run * fm;
-    ActLane a;
+    const long long dc = run * g.fmodes();   // the field's k = 0 mode
     const long long base = ((b0 * B0) * g.n[1] + b1 * B1) * g.n[2] + b2 * B2;
-    if (sizeof(cx_t<T>) == 8 && (B2 & 1) == 0) {
-        const int H = B2 / 2;
-        const int npair = B0 * B1 * H;
-        for (int m = lane; m < npair; m += 32) {
-            int l2 = (m % H) * 2;
-            int r = m / H;
-            int l1 = r % B1, l0 = r / B1;
-            long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
-            float4 v = *reinterpret_cast<const float4*>(q + idx);
-            screen_mode(make_float2(v.x, v.y), idx == dc, ENERGY, a);
-            screen_mode(make_float2(v.z, v.w), idx + 1 == dc, ENERGY, a);
+    double mx = 0.0, mxnd = 0.0, sm = 0.0;
+    if constexpr (sizeof(cx_t<T>) == 8) {
+        // chunks of up to 16 modes per lane: FP32 screen, warp max, exact FP64 for candidates
+        const int nmodes = B0 * B1 * B2;
+        constexpr int K = 16;
+        for (int m0 = 0; m0 < nmodes; m0 += 32 * K) {
+            float2 v[K];
+            float p32[K];
+            unsigned dcmask = 0;
+            float lmax = 0.f, lmaxnd = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                int m = m0 + k * 32 + lane;
+                v[k] = make_float2(0.f, 0.f);
+                if (m < nmodes) {
+                    int l2 = m % B2, r = m / B2;
+                    int l1 = r % B1, l0 = r / B1;
+                    long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
+                    v[k] = q[idx];
+                    if (idx == dc) dcmask |= 1u << k;
+                }
+                p32[k] = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+                lmax = fmaxf(lmax, p32[k]);
+                if (!((dcmask >> k) & 1u)) lmaxnd = fmaxf(lmaxnd, p32[k]);
+                if (ENERGY) sm += mode_sq(v[k]);
+            }
+            // p32 is within 2^-22 of the exact value: anything below 1 - 2^-20 of the
+            // warp's largest p32 cannot be the block max
+            const float cut = warp_max_nonneg_f(lmax) * (1.0f - 9.5367431640625e-07f);
+            const float cutnd = warp_max_nonneg_f(lmaxnd) * (1.0f - 9.5367431640625e-07f);
+            unsigned mask = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                bool isdc = (dcmask >> k) & 1u;
+                if (p32[k] >= cut || (!isdc && p32[k] >= cutnd)) mask |= 1u << k;
+            }
+            exact_candidates<K>(v, mask, dcmask, mx, mxnd);
         }
     } else {
         const int nmodes = B0 * B1 * B2;
         for (int m = lane; m < nmodes; m += 32) {
-            int l2 = m % B2;
-            int r = m / B2;
+            int l2 = m % B2, r = m / B2;
             int l1 = r % B1, l0 = r / B1;
             long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
-            screen_mode(q[idx], idx == dc, ENERGY, a);
+            double e = mode_sq(q[idx]);
+            if (ENERGY) sm += e;
+            mx = fmax(mx, e);
+            if (idx != dc) mxnd = fmax(mxnd, e);
         }
     }
-    const double mx = bitsd(warp_max_u64(dbits(a.mx)));
-    const double mxnd = bitsd(warp_max_u64(dbits(a.mxnd)));
-    double sm = 0.0;
-    if (ENERGY) sm = warp_sum(a.sm);
+    mx = bitsd(warp_max_u64(dbits(mx)));
+    mxnd = bitsd(warp_max_u64(dbits(mxnd)));
+    if (ENERGY) sm = warp_sum(sm);
     if (lane == 0) {
         maxsq[blk] = mx;
         if (ENERGY) sumsq[blk] = sm;

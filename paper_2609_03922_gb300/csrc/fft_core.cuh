@@ -243,7 +243,12 @@ __device__ __forceinline__ void store_tile(const cx_t<T>* sm, const PassParams<T
             if (UNITS % NT == 0 || u < UNITS) {
                 int p, j;
                 C v0, v1;
-                if constexpr (PFAST) {
+                if constexpr (PFAST && LY::PMAP) {
+                    // layout B keeps (p, p+1) adjacent and 16-byte aligned
+                    j = u / (P / 2); p = (u % (P / 2)) * 2;
+                    float4 t = *reinterpret_cast<const float4*>(sm + LY::idx(p, j));
+                    v0 = make_float2(t.x, t.y); v1 = make_float2(t.z, t.w);
+                } else if constexpr (PFAST) {
                     j = u / (P / 2); p = (u % (P / 2)) * 2;
                     v0 = sm[LY::idx(p, j)]; v1 = sm[LY::idx(p + 1, j)];
                 } else {
@@ -420,41 +425,87 @@ template <typename T, int NT> __device__ __forceinline__ void ch_update_stats(co
     }
 }
 
-// Update epilogue: g_hat of the tile is in shared memory (layout B).
+// Update epilogue: g_hat of the tile is in shared memory (layout B).  The
+// tile's block states and chi bits are staged in shared memory once; every
+// thread issues its c_hat loads (non-frozen rows only) before using any.
 template <typename T, int L, int P, int NT, class LY>
 __device__ __forceinline__ void ch_update_tile(const cx_t<T>* sm, const PassParams<T>& a, long long q0) {
     using C = cx_t<T>;
     const CHFuse<T>& f = a.fu;
     const Geom& g = f.g;
+    constexpr int MAXB = 256;
+    __shared__ uint8_t s_st[MAXB], s_chi[MAXB];
+    // tile-constant coordinates: 3-D (z = j, y, x0 + p); 2-D group (run, y = j, x0 + p)
+    const long long o = q0 / a.I, i0 = q0 - o * a.I;
+    const bool d3 = g.ndim == 3;
+    const long long cy = d3 ? i0 / g.n[2] : o;        // coordinate on the non-pass outer axis
+    const long long x0 = d3 ? i0 - cy * g.n[2] : i0;
+    const int Bp = d3 ? g.b[0] : g.b[1];               // block edge along the pass axis
+    const long long npass = d3 ? g.nb[0] : g.nb[1];
+    const long long bx0 = x0 / g.b[2];
+    const int nbx = (int)((x0 + P - 1) / g.b[2] - bx0 + 1);
+    const int nst = (int)(npass * nbx);
+    for (int k = threadIdx.x; k < nst; k += NT) {
+        long long bp = k / nbx, bx = bx0 + k % nbx;
+        long long id = d3 ? (bp * g.nb[1] + cy / g.b[1]) * g.nb[2] + bx : (cy * g.nb[1] + bp) * g.nb[2] + bx;
+        s_st[k] = f.dense ? (uint8_t)SPDBA_ACTIVE : f.states[id];
+        s_chi[k] = f.dense ? (uint8_t)0 : f.chi[id];
+    }
+    __syncthreads();
+    const T* __restrict__ kp = d3 ? f.k2ax[0] : f.k2ax[1];   // |k|^2 table of the pass axis
+    const T kc = d3 ? f.k2ax[1][cy] : f.k2ax[0][cy];         // fixed outer axis (0 for a group's run axis)
+    const int l_out = (int)(d3 ? cy % g.b[1] : 0);
     constexpr int E = sizeof(C) == 8 ? 2 : 1;   // modes per 16-byte access
     constexpr int UNITS = P * L / E;
-#pragma unroll 2
-    for (int u = threadIdx.x; u < UNITS; u += NT) {
+    constexpr int PER = (UNITS + NT - 1) / NT;
+    C cv[PER][E];
+    int stv[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int u = threadIdx.x + k * NT;
+        stv[k] = SPDBA_FROZEN;
+        if (UNITS % NT != 0 && u >= UNITS) continue;
         const int j = u / (P / E), p = (u % (P / E)) * E;
-        long long c0, c1, c2;
-        fuse_coords<T>(a, q0, p, j, c0, c1, c2);
-        const long long id = block_id(g, c0, c1, c2);
-        const int st = f.dense ? SPDBA_ACTIVE : f.states[id];
-        if (st == SPDBA_FROZEN) continue;
+        const int sidx = (j / Bp) * nbx + (int)((x0 + p) / g.b[2] - bx0);
+        stv[k] = s_st[sidx];
+        if (stv[k] == SPDBA_FROZEN) continue;
         const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
-        const T k01 = f.k2ax[0][c0] + f.k2ax[1][c1];
-        const unsigned chi = st == SPDBA_TRANSITION ? f.chi[id] : 0u;
-        const int l0 = (int)(c0 % g.b[0]), l1 = (int)(c1 % g.b[1]), l2 = (int)(c2 % g.b[2]);
         if constexpr (E == 2) {
-            float4 cv = *reinterpret_cast<const float4*>(f.c_hat + ad);
-            float2 cA = make_float2(cv.x, cv.y), cB = make_float2(cv.z, cv.w);
-            float2 nA = ch_new(cA, sm[LY::idx(p, j)], k01 + f.k2ax[2][c2], f.dt, f.dtkappa);
-            float2 nB = ch_new(cB, sm[LY::idx(p + 1, j)], k01 + f.k2ax[2][c2 + 1], f.dt, f.dtkappa);
-            if (st == SPDBA_TRANSITION) {
-                nA = ch_blend<T>(cA, nA, f.taper, g, chi, l0, l1, l2);
-                nB = ch_blend<T>(cB, nB, f.taper, g, chi, l0, l1, l2 + 1);
-            }
-            *reinterpret_cast<float4*>(f.c_hat + ad) = make_float4(nA.x, nA.y, nB.x, nB.y);
+            float4 t = *reinterpret_cast<const float4*>(f.c_hat + ad);
+            cv[k][0] = make_float2(t.x, t.y);
+            cv[k][1] = make_float2(t.z, t.w);
         } else {
-            C cv = f.c_hat[ad];
-            C nv = ch_new(cv, sm[LY::idx(p, j)], k01 + f.k2ax[2][c2], f.dt, f.dtkappa);
-            if (st == SPDBA_TRANSITION) nv = ch_blend<T>(cv, nv, f.taper, g, chi, l0, l1, l2);
-            f.c_hat[ad] = nv;
+            cv[k][0] = f.c_hat[ad];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (stv[k] == SPDBA_FROZEN) continue;
+        const int u = threadIdx.x + k * NT;
+        const int j = u / (P / E), p = (u % (P / E)) * E;
+        const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
+        const long long x = x0 + p;
+        // same association as the staged kernels: (k_outer + k_pass) then + k_x
+        const T k01 = d3 ? kp[j] + kc : kc + kp[j];
+        C nv[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            nv[e] = ch_new(cv[k][e], sm[LY::idx(p + e, j)], k01 + f.k2ax[2][x + e], f.dt, f.dtkappa);
+        if (stv[k] == SPDBA_TRANSITION) {
+            const int sidx = (j / Bp) * nbx + (int)(x / g.b[2] - bx0);
+            const unsigned chi = s_chi[sidx];
+            const int lj = j % Bp;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int lx = (int)((x + e) % g.b[2]);
+                nv[e] = d3 ? ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, lj, l_out, lx)
+                           : ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, 0, lj, lx);
+            }
+        }
+        if constexpr (E == 2) {
+            *reinterpret_cast<float4*>(f.c_hat + ad) = make_float4(nv[0].x, nv[0].y, nv[1].x, nv[1].y);
+        } else {
+            f.c_hat[ad] = nv[0];
         }
     }
 }
