@@ -85,25 +85,41 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
     const long long base = ((b0 * B0) * g.n[1] + b1 * B1) * g.n[2] + b2 * B2;
     double mx = 0.0, mxnd = 0.0, sm = 0.0;
     if constexpr (sizeof(cx_t<T>) == 8) {
-        // chunks of up to 16 modes per lane: FP32 screen, warp max, exact FP64 for candidates
-        const int nmodes = B0 * B1 * B2;
-        constexpr int K = 16;
-        for (int m0 = 0; m0 < nmodes; m0 += 32 * K) {
-            float2 v[K];
-            float p32[K];
+        // chunks of up to 16 modes per lane, as 8 16-byte loads of mode pairs along
+        // the fast axis (B2 is even for every supported block), all issued before
+        // use; FP32 screen; warp max; exact FP64 for the candidates only
+        const int H = B2 >> 1;
+        const int npair = B0 * B1 * H;
+        constexpr int K2 = 8;
+        for (int m0 = 0; m0 < npair; m0 += 32 * K2) {
+            float4 w[K2];
+            long long first[K2];
+#pragma unroll
+            for (int k = 0; k < K2; ++k) {
+                const int m = m0 + k * 32 + lane;
+                w[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                first[k] = -1;
+                if (m < npair) {
+                    const int row = m / H, l2 = (m - row * H) * 2;
+                    const int l1 = row % B1, l0 = row / B1;
+                    const long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
+                    first[k] = idx;
+                    w[k] = *reinterpret_cast<const float4*>(q + idx);
+                }
+            }
+            float2 v[2 * K2];
             unsigned dcmask = 0;
             float lmax = 0.f, lmaxnd = 0.f;
+            float p32[2 * K2];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                int m = m0 + k * 32 + lane;
-                v[k] = make_float2(0.f, 0.f);
-                if (m < nmodes) {
-                    int l2 = m % B2, r = m / B2;
-                    int l1 = r % B1, l0 = r / B1;
-                    long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
-                    v[k] = q[idx];
-                    if (idx == dc) dcmask |= 1u << k;
-                }
+            for (int k = 0; k < K2; ++k) {
+                v[2 * k] = make_float2(w[k].x, w[k].y);
+                v[2 * k + 1] = make_float2(w[k].z, w[k].w);
+                if (first[k] == dc) dcmask |= 1u << (2 * k);
+                if (first[k] >= 0 && first[k] + 1 == dc) dcmask |= 1u << (2 * k + 1);
+            }
+#pragma unroll
+            for (int k = 0; k < 2 * K2; ++k) {
                 p32[k] = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
                 lmax = fmaxf(lmax, p32[k]);
                 if (!((dcmask >> k) & 1u)) lmaxnd = fmaxf(lmaxnd, p32[k]);
@@ -115,11 +131,11 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
             const float cutnd = warp_max_nonneg_f(lmaxnd) * (1.0f - 9.5367431640625e-07f);
             unsigned mask = 0;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                bool isdc = (dcmask >> k) & 1u;
+            for (int k = 0; k < 2 * K2; ++k) {
+                const bool isdc = (dcmask >> k) & 1u;
                 if (p32[k] >= cut || (!isdc && p32[k] >= cutnd)) mask |= 1u << k;
             }
-            exact_candidates<K>(v, mask, dcmask, mx, mxnd);
+            exact_candidates<2 * K2>(v, mask, dcmask, mx, mxnd);
         }
     } else {
         const int nmodes = B0 * B1 * B2;

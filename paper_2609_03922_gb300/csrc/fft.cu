@@ -81,7 +81,8 @@ static std::set<const void*> g_attr_done;
 static spdba_status ensure_smem_attr(const void* f, int smem, bool max_carveout) {
     std::lock_guard<std::mutex> lk(g_attr_mu);
     if (g_attr_done.count(f)) return SPDBA_OK;
-    if (smem > 48 * 1024) SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // always raise the dynamic limit: some kernels also carry static shared memory
+    SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // row-major (pencil-fastest) pipelined tiles stream through shared memory
     // only; give them the whole carveout so three CTAs fit per SM
     if (max_carveout) SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));

@@ -438,6 +438,26 @@ __device__ __forceinline__ void ch_update_tile(const cx_t<T>* sm, const PassPara
     // tile-constant coordinates: 3-D (z = j, y, x0 + p); 2-D group (run, y = j, x0 + p)
     const long long o = q0 / a.I, i0 = q0 - o * a.I;
     const bool d3 = g.ndim == 3;
+    if (d3 && (i0 % g.n[2]) + P > g.n[2]) {
+        // the tile spans several rows of a small grid: per-mode coordinates and states
+        constexpr int UN = P * L;
+        for (int u = threadIdx.x; u < UN; u += NT) {
+            const int j = u / P, p = u % P;
+            long long c0, c1, c2;
+            fuse_coords<T>(a, q0, p, j, c0, c1, c2);
+            const long long id = block_id(g, c0, c1, c2);
+            const int st = f.dense ? SPDBA_ACTIVE : f.states[id];
+            if (st == SPDBA_FROZEN) continue;
+            const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
+            C cv = f.c_hat[ad];
+            C nv = ch_new(cv, sm[LY::idx(p, j)], (f.k2ax[0][c0] + f.k2ax[1][c1]) + f.k2ax[2][c2], f.dt, f.dtkappa);
+            if (st == SPDBA_TRANSITION)
+                nv = ch_blend<T>(cv, nv, f.taper, g, f.chi[id], (int)(c0 % g.b[0]), (int)(c1 % g.b[1]),
+                                 (int)(c2 % g.b[2]));
+            f.c_hat[ad] = nv;
+        }
+        return;
+    }
     const long long cy = d3 ? i0 / g.n[2] : o;        // coordinate on the non-pass outer axis
     const long long x0 = d3 ? i0 - cy * g.n[2] : i0;
     const int Bp = d3 ? g.b[0] : g.b[1];               // block edge along the pass axis

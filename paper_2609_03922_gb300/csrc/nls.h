@@ -29,9 +29,16 @@ template <typename T> struct NLSArgs {
     int do_fwd, do_close, do_open, do_inv, do_kerr;
 };
 
-template <typename T> spdba_status nls_small_step(const NLSArgs<T>& a, cudaStream_t st);
-template <typename T> spdba_status nls_row_pass(const NLSArgs<T>& a, cudaStream_t st);
-template <typename T> spdba_status nls_col_pass(const NLSArgs<T>& a, cudaStream_t st);
+// Launch shapes of the three NLS kernels for one group, fixed at plan creation
+// (function attributes and occupancy are queried there, never during a step).
+struct NLSLaunch {
+    long long small_grid = 0, row_grid = 0, col_grid = 0;
+    int small_smem = 0, row_smem = 0, col_smem = 0;
+};
+template <typename T> spdba_status nls_prepare(long long n, long long n1, long long batch, NLSLaunch* out);
+template <typename T> spdba_status nls_small_step(const NLSArgs<T>& a, const NLSLaunch& l, cudaStream_t st);
+template <typename T> spdba_status nls_row_pass(const NLSArgs<T>& a, const NLSLaunch& l, cudaStream_t st);
+template <typename T> spdba_status nls_col_pass(const NLSArgs<T>& a, const NLSLaunch& l, cudaStream_t st);
 template <typename T>
 spdba_status nls_permute(const cx_t<T>* in, cx_t<T>* out, long long n, long long n1, long long batch, int to_natural,
                          cudaStream_t st);

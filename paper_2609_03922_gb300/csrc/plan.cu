@@ -91,6 +91,7 @@ template <typename T> struct Group {
     const C* tw_col = nullptr;      // stage twiddles of n1 (long columns)
     const C* tw4 = nullptr;         // exp(-2 pi i m / n)
     int B = 1, nblk = 1;
+    NLSLaunch nl;                   // NLS launch shapes (fixed at creation)
     int64_t step = 0;
     bool assessed = false;
     std::vector<void*> allocs;
@@ -148,6 +149,8 @@ struct spdba_plan {
     std::vector<RunRef> runs;
     TwiddleCache<float> tw32;
     TwiddleCache<double> tw64;
+    cudaGraphExec_t seg_exec = nullptr;   // one reassessment segment (R steps of every group)
+    long long seg_launches = 0;
     int nruns() const { return (int)runs.size(); }
 };
 
@@ -338,6 +341,7 @@ static spdba_status group_init_nls(spdba_plan* p, Group<T>& r, long long n, int 
         if ((s = r.fft1.init(1, d, 1, tw, st)) != SPDBA_OK) return s;
     }
     if ((s = group_buffers<T>(p, r)) != SPDBA_OK) return s;
+    if ((s = nls_prepare<T>(n, r.n1, batch, &r.nl)) != SPDBA_OK) return s;
     if ((s = upload(r, &r.H, half_step_table<T>(n, p->opt.beta2, p->opt.h, p->opt.dt_sample), st)) != SPDBA_OK)
         return s;
     if ((s = upload(r, &r.ntaper, taper_table<T>(r.B), st)) != SPDBA_OK) return s;
@@ -461,17 +465,18 @@ template <typename T> static NLSArgs<T> nls_args(spdba_plan* p, Group<T>& r, cx_
     return a;
 }
 
-template <typename T> static spdba_status row_pass(spdba_plan* p, NLSArgs<T> a, int fwd, int close, int open, int inv) {
+template <typename T>
+static spdba_status row_pass(spdba_plan* p, Group<T>& r, NLSArgs<T> a, int fwd, int close, int open, int inv) {
     a.do_fwd = fwd; a.do_close = close; a.do_open = open; a.do_inv = inv;
     ProfScope pr(p, K_NLS_ROW, 2.0 * sizeof(cx_t<T>) * (double)(a.batch * a.n));
     p->launches += 1;
-    return nls_row_pass<T>(a, p->st);
+    return nls_row_pass<T>(a, r.nl, p->st);
 }
-template <typename T> static spdba_status col_pass(spdba_plan* p, NLSArgs<T> a, int inv, int kerr, int fwd) {
+template <typename T> static spdba_status col_pass(spdba_plan* p, Group<T>& r, NLSArgs<T> a, int inv, int kerr, int fwd) {
     a.do_inv = inv; a.do_kerr = kerr; a.do_fwd = fwd;
     ProfScope pr(p, K_NLS_COL, 2.0 * sizeof(cx_t<T>) * (double)(a.batch * a.n));
     p->launches += 1;
-    return nls_col_pass<T>(a, p->st);
+    return nls_col_pass<T>(a, r.nl, p->st);
 }
 
 // n steps of an NLS group.  Between calls S is the spectrum at a step boundary.
@@ -489,17 +494,17 @@ template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T
             const bool merge = i > 0 && !reassess && prev_dense == dense;
             if (i > 0 && !merge) {
                 NLSArgs<T> c = nls_args<T>(p, r, r.c_hat, r.batch, prev_dense);
-                if ((s = row_pass<T>(p, c, 1, 1, 0, 0)) != SPDBA_OK) return s;
+                if ((s = row_pass<T>(p, r, c, 1, 1, 0, 0)) != SPDBA_OK) return s;
             }
             if (reassess && (s = group_assess<T>(p, r)) != SPDBA_OK) return s;
-            if ((s = row_pass<T>(p, a, merge ? 1 : 0, merge ? 1 : 0, 1, 1)) != SPDBA_OK) return s;
+            if ((s = row_pass<T>(p, r, a, merge ? 1 : 0, merge ? 1 : 0, 1, 1)) != SPDBA_OK) return s;
             NLSArgs<T> c = a;
             c.tw = r.tw_col;
             if (reassess) {
                 zero_strided_kernel<<<1, 256, 0, st>>>(&r.stats[0].mass, r.batch, a.power_stride);
                 c.power = &r.stats[0].mass;
             }
-            if ((s = col_pass<T>(p, c, 1, 1, 1)) != SPDBA_OK) return s;
+            if ((s = col_pass<T>(p, r, c, 1, 1, 1)) != SPDBA_OK) return s;
         } else {
             if (reassess && (s = group_assess<T>(p, r)) != SPDBA_OK) return s;
             if (reassess) {
@@ -507,7 +512,7 @@ template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T
                 a.power = &r.stats[0].mass;
             }
             ProfScope pr(p, K_NLS_STEP, 2.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n));
-            if ((s = nls_small_step<T>(a, st)) != SPDBA_OK) return s;
+            if ((s = nls_small_step<T>(a, r.nl, st)) != SPDBA_OK) return s;
             p->launches += 1;
         }
         ratio_kernel<<<1, 256, 0, st>>>(r.stats, r.batch, r.g.bpr(), r.g.block_modes(), dense);
@@ -518,12 +523,12 @@ template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T
     }
     if (r.long_nls && nsteps > 0) {
         NLSArgs<T> c = nls_args<T>(p, r, r.c_hat, r.batch, prev_dense);
-        if ((s = row_pass<T>(p, c, 1, 1, 0, 0)) != SPDBA_OK) return s;
+        if ((s = row_pass<T>(p, r, c, 1, 1, 0, 0)) != SPDBA_OK) return s;
     }
     return SPDBA_OK;
 }
 
-template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
+template <typename T> static spdba_status direct_steps(spdba_plan* p, int64_t n) {
     auto& gs = groups<T>(p);
     if (p->opt.model == SPDBA_MODEL_NLS) {
         for (auto& g : gs) {
@@ -536,6 +541,63 @@ template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
         for (auto& g : gs) {
             spdba_status s = group_ch_step<T>(p, *g);
             if (s != SPDBA_OK) return s;
+        }
+    }
+    return SPDBA_OK;
+}
+
+// A segment is R steps starting at a reassessment step with no all-active step
+// inside: its launch sequence is the same every time, so it is captured once
+// into a CUDA graph and replayed.
+template <typename T> static bool segment_ready(spdba_plan* p) {
+    for (auto& g : groups<T>(p)) {
+        if (g->step % p->reassess != 0) return false;
+        for (int64_t s = g->step; s < g->step + p->reassess; ++s)
+            if (all_active_step(p, s)) return false;
+    }
+    return true;
+}
+
+template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
+    // graphs need a capturable (non-legacy) stream; profiling records events per kernel
+    if (!p->opt.use_graph || p->prof || p->st == 0) return direct_steps<T>(p, n);
+    const int R = p->reassess;
+    int64_t i = 0;
+    while (i < n) {
+        if (n - i >= R && segment_ready<T>(p)) {
+            if (!p->seg_exec) {
+                const long long l0 = p->launches;
+                SPDBA_CUDA(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+                spdba_status s = direct_steps<T>(p, R);
+                cudaGraph_t graph = nullptr;
+                cudaError_t e = cudaStreamEndCapture(p->st, &graph);
+                if (s != SPDBA_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return s;
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&p->seg_exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    p->seg_exec = nullptr;
+                    return cuda_fail(e, "cudaGraphInstantiate");
+                }
+                p->seg_launches = p->launches - l0;
+                // the capture advanced the host-side step counters; run what it recorded
+                SPDBA_CUDA(cudaGraphLaunch(p->seg_exec, p->st));
+            } else {
+                SPDBA_CUDA(cudaGraphLaunch(p->seg_exec, p->st));
+                for (auto& g : groups<T>(p)) {
+                    g->step += R;
+                    if (p->opt.mode == SPDBA_MODE_ADAPTIVE) g->assessed = true;
+                }
+                p->launches += p->seg_launches;
+            }
+            i += R;
+        } else {
+            spdba_status s = direct_steps<T>(p, 1);
+            if (s != SPDBA_OK) return s;
+            ++i;
         }
     }
     return SPDBA_OK;
@@ -561,10 +623,10 @@ static spdba_status run_set_field(spdba_plan* p, Group<T>& r, long long sub, con
         NLSArgs<T> a = nls_args<T>(p, r, slot, 1, 1);
         a.tw = r.tw_col;
         a.do_inv = 0; a.do_kerr = 0; a.do_fwd = 1;
-        if ((s = nls_col_pass<T>(a, st)) != SPDBA_OK) return s;
+        if ((s = nls_col_pass<T>(a, r.nl, st)) != SPDBA_OK) return s;
         a.tw = r.tw_row;
         a.do_fwd = 1; a.do_close = 0; a.do_open = 0; a.do_inv = 0;
-        if ((s = nls_row_pass<T>(a, st)) != SPDBA_OK) return s;
+        if ((s = nls_row_pass<T>(a, r.nl, st)) != SPDBA_OK) return s;
     }
     r.step = 0;
     r.assessed = false;
@@ -592,10 +654,10 @@ static spdba_status run_get_field(spdba_plan* p, Group<T>& r, long long sub, voi
         NLSArgs<T> a = nls_args<T>(p, r, wslot, 1, 1);
         a.tw = r.tw_row;
         a.do_fwd = 0; a.do_close = 0; a.do_open = 0; a.do_inv = 1;
-        if ((s = nls_row_pass<T>(a, st)) != SPDBA_OK) return s;
+        if ((s = nls_row_pass<T>(a, r.nl, st)) != SPDBA_OK) return s;
         a.tw = r.tw_col;
         a.do_inv = 1; a.do_kerr = 0; a.do_fwd = 0;
-        if ((s = nls_col_pass<T>(a, st)) != SPDBA_OK) return s;
+        if ((s = nls_col_pass<T>(a, r.nl, st)) != SPDBA_OK) return s;
         SPDBA_CUDA(cudaMemcpyAsync(dst, wslot, sizeof(cx_t<T>) * r.n, kind, st));
     }
     SPDBA_CUDA(cudaStreamSynchronize(st));
@@ -766,6 +828,7 @@ extern "C" void spdba_plan_destroy(spdba_plan* p) {
     p->tw32.release();
     p->tw64.release();
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (p->seg_exec) cudaGraphExecDestroy(p->seg_exec);
     delete p;
 }
 

@@ -183,3 +183,39 @@ def test_fused_update_equals_staged_update(shape, block, batch):
         assert np.array_equal(ma, mb)
         assert abs(ta["active_ratio_sum"] - tb["active_ratio_sum"]) < 1e-9
     assert any(np.any(m == 0) for _, m, _ in outs[0])   # some blocks were frozen
+
+
+@pytest.mark.parametrize("model", ["ch", "nls"])
+def test_graph_replay_equals_direct_launches(model):
+    """Reassessment segments captured once in a CUDA graph and replayed give the
+    same fields, masks and statistics as launching every kernel directly."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    outs = []
+    for use_graph in (1, 0):
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            if model == "ch":
+                dims = [(128, 128), (128, 128), (192, 192)]
+                plan = spdba.Plan(None, (16, 16), threshold=1e-3, reassess=5, batch_dims=dims, precision=0,
+                                  use_graph=use_graph)
+                inputs = [W.ch_initial_condition(d, mean=0.05 * i, seed=W.BASE_SEED + 60 + i).astype(np.float32)
+                          for i, d in enumerate(dims)]
+            else:
+                dims = [(4096,), (8192,), (4096,)]
+                plan = spdba.Plan(None, (-64,), threshold=1e-3, reassess=5, batch_dims=dims,
+                                  model=spdba.SPDBA_MODEL_NLS, precision=0, use_graph=use_graph)
+                inputs = [W.nls_signal(d[0], seed=W.BASE_SEED + 70 + i).astype(np.complex64) for i, d in enumerate(dims)]
+            for r, x in enumerate(inputs):
+                plan.set_field(x, run=r)
+            plan.step(3)       # off the segment grid: direct launches
+            plan.step(2)
+            plan.step(17)      # three whole segments (graph) and two single steps
+            res = [(plan.get_spectrum(run=r), plan.get_mask(run=r), plan.get_stats(run=r)) for r in range(len(dims))]
+            plan.close()
+        side.synchronize()
+        outs.append(res)
+    for (sa, ma, ta), (sb, mb, tb) in zip(*outs):
+        assert np.array_equal(sa, sb)
+        assert np.array_equal(ma, mb)
+        assert ta["step"] == tb["step"] == 22 and ta["assessments"] == tb["assessments"]
