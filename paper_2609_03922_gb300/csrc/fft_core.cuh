@@ -234,7 +234,23 @@ __device__ __forceinline__ void store_tile(const cx_t<T>* sm, const PassParams<T
     using C = cx_t<T>;
     const long long npencil = a.O * a.I;
     const T s = a.scale;
-    if constexpr (sizeof(C) == 8) {
+    if constexpr (sizeof(C) == 8 && !PFAST) {
+        // pencil-major tile: one element per thread, consecutive j across a warp
+        // (conflict-free shared reads, coalesced 8-byte stores)
+        constexpr int UNITS = P * L;
+        constexpr int PER = (UNITS + NT - 1) / NT;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            int e = threadIdx.x + k * NT;
+            if (UNITS % NT == 0 || e < UNITS) {
+                int p = e / L, j = e % L;
+                if (q0 + p < npencil) {
+                    long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, a.generic);
+                    a.out[ad] = cscale(sm[LY::idx(p, j)], s);
+                }
+            }
+        }
+    } else if constexpr (sizeof(C) == 8) {
         constexpr int UNITS = P * L / 2;
         constexpr int PER = (UNITS + NT - 1) / NT;
 #pragma unroll
@@ -248,12 +264,9 @@ __device__ __forceinline__ void store_tile(const cx_t<T>* sm, const PassParams<T
                     j = u / (P / 2); p = (u % (P / 2)) * 2;
                     float4 t = *reinterpret_cast<const float4*>(sm + LY::idx(p, j));
                     v0 = make_float2(t.x, t.y); v1 = make_float2(t.z, t.w);
-                } else if constexpr (PFAST) {
+                } else {
                     j = u / (P / 2); p = (u % (P / 2)) * 2;
                     v0 = sm[LY::idx(p, j)]; v1 = sm[LY::idx(p + 1, j)];
-                } else {
-                    p = u / (L / 2); j = (u % (L / 2)) * 2;
-                    v0 = sm[LY::idx(p, j)]; v1 = sm[LY::idx(p, j + 1)];
                 }
                 if (q0 + p < npencil) {
                     long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, a.generic);
@@ -476,20 +489,28 @@ __device__ __forceinline__ void ch_update_tile(const cx_t<T>* sm, const PassPara
     const T kc = d3 ? f.k2ax[1][cy] : f.k2ax[0][cy];         // fixed outer axis (0 for a group's run axis)
     const int l_out = (int)(d3 ? cy % g.b[1] : 0);
     constexpr int E = sizeof(C) == 8 ? 2 : 1;   // modes per 16-byte access
-    constexpr int UNITS = P * L / E;
-    constexpr int PER = (UNITS + NT - 1) / NT;
+    constexpr int UPR = P / E;                   // units per row of the tile
+    static_assert(NT % UPR == 0, "threads must cover whole rows");
+    constexpr int JSTEP = NT / UPR;              // rows advanced per unit step
+    constexpr int PER = L / JSTEP;               // units per thread
+    // this thread's pencil offset and first row never change within the tile
+    const int p = (threadIdx.x % UPR) * E;
+    const int j0 = threadIdx.x / UPR;
+    const long long x = x0 + p;
+    const int bxs = (int)(x / g.b[2] - bx0);
+    const int lx = (int)(x % g.b[2]);
+    T kx[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) kx[e] = f.k2ax[2][x + e];
+    const long long o2 = (q0 / a.I) * a.osO + (i0 + p) * a.osI;   // address of (p, j = 0)
     C cv[PER][E];
     int stv[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int u = threadIdx.x + k * NT;
-        stv[k] = SPDBA_FROZEN;
-        if (UNITS % NT != 0 && u >= UNITS) continue;
-        const int j = u / (P / E), p = (u % (P / E)) * E;
-        const int sidx = (j / Bp) * nbx + (int)((x0 + p) / g.b[2] - bx0);
-        stv[k] = s_st[sidx];
+        const int j = j0 + k * JSTEP;
+        stv[k] = s_st[(j / Bp) * nbx + bxs];
         if (stv[k] == SPDBA_FROZEN) continue;
-        const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
+        const long long ad = o2 + (long long)j * a.osJ;
         if constexpr (E == 2) {
             float4 t = *reinterpret_cast<const float4*>(f.c_hat + ad);
             cv[k][0] = make_float2(t.x, t.y);
@@ -501,26 +522,20 @@ __device__ __forceinline__ void ch_update_tile(const cx_t<T>* sm, const PassPara
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         if (stv[k] == SPDBA_FROZEN) continue;
-        const int u = threadIdx.x + k * NT;
-        const int j = u / (P / E), p = (u % (P / E)) * E;
-        const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
-        const long long x = x0 + p;
+        const int j = j0 + k * JSTEP;
+        const long long ad = o2 + (long long)j * a.osJ;
         // same association as the staged kernels: (k_outer + k_pass) then + k_x
         const T k01 = d3 ? kp[j] + kc : kc + kp[j];
         C nv[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-            nv[e] = ch_new(cv[k][e], sm[LY::idx(p + e, j)], k01 + f.k2ax[2][x + e], f.dt, f.dtkappa);
+        for (int e = 0; e < E; ++e) nv[e] = ch_new(cv[k][e], sm[LY::idx(p + e, j)], k01 + kx[e], f.dt, f.dtkappa);
         if (stv[k] == SPDBA_TRANSITION) {
-            const int sidx = (j / Bp) * nbx + (int)(x / g.b[2] - bx0);
-            const unsigned chi = s_chi[sidx];
+            const unsigned chi = s_chi[(j / Bp) * nbx + bxs];
             const int lj = j % Bp;
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int lx = (int)((x + e) % g.b[2]);
-                nv[e] = d3 ? ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, lj, l_out, lx)
-                           : ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, 0, lj, lx);
-            }
+            for (int e = 0; e < E; ++e)
+                nv[e] = d3 ? ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, lj, l_out, lx + e)
+                           : ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, 0, lj, lx + e);
         }
         if constexpr (E == 2) {
             *reinterpret_cast<float4*>(f.c_hat + ad) = make_float4(nv[0].x, nv[0].y, nv[1].x, nv[1].y);
