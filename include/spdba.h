@@ -223,6 +223,48 @@ spdba_status spdba_classify(int32_t ndim, const int64_t* nblocks, const double* 
                             uint8_t* states, uint8_t* chi, int32_t* list, int32_t* count,
                             void* scratch, void* stream);
 
+/* ------------------------------------------------------------------------------ */
+/* Learned block-activity predictor (no counterpart in the paper).                  */
+/* ------------------------------------------------------------------------------ */
+/*
+ * A 3-D convolutional network over a block map of nd x nh x nw blocks that
+ * predicts, per block, the probability that the block is non-frozen at any
+ * reassessment within the next K steps:
+ *   a1 = conv(x, W1) + b1, h1 = relu(a1)    2 -> 8 channels
+ *   a2 = conv(h1, W2) + b2, h2 = relu(a2)   8 -> 16
+ *   a3 = conv(h2, W3) + b3, h3 = relu(a3)   16 -> 8
+ *   p  = sigmoid(h3 . wh + bh);  loss = mean binary cross-entropy
+ * conv is a 3x3x3 convolution with periodic wrap (tap = 9(dz+1) + 3(dy+1) +
+ * (dx+1)).  Input features x[v] = (clamp(log10(A_B / tau) / 8, -1, 1),
+ * 1 if the block is not FROZEN).  Arrays are channels-last, maps contiguous.
+ * Parameters: one FP32 vector of spdba_predictor_num_params() values in the
+ * order W1 (8x27x2), b1, W2 (16x27x8), b2, W3 (8x27x16), b3, wh (8), bh (1),
+ * each W indexed [out][tap][in].  Convolutions run on BF16 tensor cores with
+ * FP32 accumulation; activations between layers and the backpropagated
+ * pre-activation gradients are BF16; Adam keeps FP32 master weights.
+ */
+typedef struct spdba_predictor spdba_predictor;
+int64_t spdba_predictor_num_params(void);
+/* max_batch: most maps per call; init_params: host FP32 vector (copied). */
+spdba_status spdba_predictor_create(spdba_predictor** out, int32_t nd, int32_t nh, int32_t nw,
+                                    int32_t max_batch, const float* init_params);
+void spdba_predictor_destroy(spdba_predictor* pr);
+spdba_status spdba_predictor_get_params(spdba_predictor* pr, float* host_out);
+spdba_status spdba_predictor_set_params(spdba_predictor* pr, const float* host_in);
+/* x_bf16 (device, nmaps*V*2 bf16) from per-block max|q|^2 (device FP64, nmaps*V),
+   per-map tau (device FP64, nmaps) and block states (device u8, nmaps*V). */
+spdba_status spdba_predictor_features(spdba_predictor* pr, const double* maxsq, const double* tau,
+                                      const uint8_t* states, int32_t nmaps, void* x_bf16, void* stream);
+/* prob (device FP32, nmaps*V). */
+spdba_status spdba_predictor_forward(spdba_predictor* pr, const void* x_bf16, int32_t nmaps, float* prob,
+                                     void* stream);
+/* Loss and gradients without an update; labels device FP32 in {0,1}; host outputs. Synchronizes. */
+spdba_status spdba_predictor_gradients(spdba_predictor* pr, const void* x_bf16, const float* labels,
+                                       int32_t nmaps, double* loss_out, float* grads_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; loss_out may be NULL. */
+spdba_status spdba_predictor_train_step(spdba_predictor* pr, const void* x_bf16, const float* labels,
+                                        int32_t nmaps, float lr, double* loss_out, void* stream);
+
 /*
  * spdba_classify without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- for

@@ -234,23 +234,7 @@ __device__ __forceinline__ void store_tile(const cx_t<T>* sm, const PassParams<T
     using C = cx_t<T>;
     const long long npencil = a.O * a.I;
     const T s = a.scale;
-    if constexpr (sizeof(C) == 8 && !PFAST) {
-        // pencil-major tile: one element per thread, consecutive j across a warp
-        // (conflict-free shared reads, coalesced 8-byte stores)
-        constexpr int UNITS = P * L;
-        constexpr int PER = (UNITS + NT - 1) / NT;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            int e = threadIdx.x + k * NT;
-            if (UNITS % NT == 0 || e < UNITS) {
-                int p = e / L, j = e % L;
-                if (q0 + p < npencil) {
-                    long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, a.generic);
-                    a.out[ad] = cscale(sm[LY::idx(p, j)], s);
-                }
-            }
-        }
-    } else if constexpr (sizeof(C) == 8) {
+    if constexpr (sizeof(C) == 8) {
         constexpr int UNITS = P * L / 2;
         constexpr int PER = (UNITS + NT - 1) / NT;
 #pragma unroll

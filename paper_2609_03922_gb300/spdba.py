@@ -78,6 +78,16 @@ SIGNATURES = {
                             _P, _P]),
     "spdba_classify_static": (_S, [ctypes.c_int32, _I64P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
                                    _P, _P]),
+    "spdba_predictor_num_params": (ctypes.c_int64, []),
+    "spdba_predictor_create": (_S, [_PP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
+    "spdba_predictor_destroy": (None, [_P]),
+    "spdba_predictor_get_params": (_S, [_P, _P]),
+    "spdba_predictor_set_params": (_S, [_P, _P]),
+    "spdba_predictor_features": (_S, [_P, _P, _P, _P, ctypes.c_int32, _P, _P]),
+    "spdba_predictor_forward": (_S, [_P, _P, ctypes.c_int32, _P, _P]),
+    "spdba_predictor_gradients": (_S, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
+    "spdba_predictor_train_step": (_S, [_P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_double),
+                                        _P]),
 }
 
 _lib = None
@@ -299,3 +309,68 @@ def classify_static(nblocks, measure, tau, force_dc, transitions, states, chi, l
                                       int(force_dc), int(transitions), states.data_ptr(), chi.data_ptr(),
                                       lst.data_ptr(), count.data_ptr(),
                                       current_stream() if stream is None else stream))
+
+
+def predictor_init_params(seed=0):
+    """He-style random initial parameters (FP32), in the library's flat order."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in ((2, 8), (8, 16), (16, 8)):
+        parts.append(rng.standard_normal(co * 27 * ci) * np.sqrt(2.0 / (27 * ci)))
+        parts.append(np.zeros(co))
+    parts.append(rng.standard_normal(8) * np.sqrt(1.0 / 8))
+    parts.append(np.zeros(1))
+    return np.concatenate(parts).astype(np.float32)
+
+
+class Predictor:
+    """The learned block-activity predictor (spdba_predictor_*)."""
+
+    def __init__(self, map_dims, max_batch=1, params=None, seed=0):
+        self.map_dims = tuple(int(d) for d in map_dims)
+        self.nparams = int(lib().spdba_predictor_num_params())
+        p = predictor_init_params(seed) if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        self._p = ctypes.c_void_p()
+        check(lib().spdba_predictor_create(ctypes.byref(self._p), *self.map_dims, int(max_batch), p.ctypes.data))
+
+    def close(self):
+        if self._p:
+            lib().spdba_predictor_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        check(lib().spdba_predictor_get_params(self._p, out.ctypes.data))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(lib().spdba_predictor_set_params(self._p, p.ctypes.data))
+
+    def features(self, maxsq, tau, states, x_out, nmaps=1, stream=None):
+        check(lib().spdba_predictor_features(self._p, maxsq.data_ptr(), tau.data_ptr(), states.data_ptr(), nmaps,
+                                             x_out.data_ptr(), current_stream() if stream is None else stream))
+
+    def forward(self, x, prob, nmaps=1, stream=None):
+        check(lib().spdba_predictor_forward(self._p, x.data_ptr(), nmaps, prob.data_ptr(),
+                                            current_stream() if stream is None else stream))
+
+    def gradients(self, x, labels, nmaps=1):
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams, dtype=np.float32)
+        check(lib().spdba_predictor_gradients(self._p, x.data_ptr(), labels.data_ptr(), nmaps, ctypes.byref(loss),
+                                              g.ctypes.data))
+        return loss.value, g
+
+    def train_step(self, x, labels, lr, nmaps=1, want_loss=True, stream=None):
+        loss = ctypes.c_double()
+        check(lib().spdba_predictor_train_step(self._p, x.data_ptr(), labels.data_ptr(), nmaps, float(lr),
+                                               ctypes.byref(loss) if want_loss else None,
+                                               current_stream() if stream is None else stream))
+        return loss.value if want_loss else None
