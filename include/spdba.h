@@ -91,6 +91,9 @@ typedef struct spdba_stats {
     double mass;             /* CH: FP64 sum of the real field at the last reassessment;
                                 NLS: FP64 sum |E(t)|^2                                    */
     double active_ratio_sum; /* sum over steps of (ACTIVE + TRANSITION) / nblocks        */
+    int64_t predictions;     /* reassessments answered by an attached predictor            */
+    int64_t missed_blocks;   /* blocks an exact judge found non-frozen that the prediction
+                                in force had frozen (summed over judges)                  */
 } spdba_stats;
 
 typedef struct spdba_plan spdba_plan;         /* opaque; owns all of its device buffers */
@@ -150,6 +153,10 @@ spdba_status spdba_get_mask(spdba_plan* plan, int32_t run, uint8_t* dst, int64_t
 
 /* Statistics of run `run`.  Synchronizes. */
 spdba_status spdba_get_stats(spdba_plan* plan, int32_t run, spdba_stats* out);
+
+/* Copy run `run`'s per-block max |q(k)|^2 (FP64, nblocks values) and tau of the
+   last exact reassessment, to device or host memory.  Synchronizes. */
+spdba_status spdba_get_activity(spdba_plan* plan, int32_t run, double* maxsq, double* tau, int32_t dst_on_device);
 
 /* Wait for all work enqueued by the plan. */
 spdba_status spdba_sync(spdba_plan* plan);
@@ -264,6 +271,20 @@ spdba_status spdba_predictor_gradients(spdba_predictor* pr, const void* x_bf16, 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; loss_out may be NULL. */
 spdba_status spdba_predictor_train_step(spdba_predictor* pr, const void* x_bf16, const float* labels,
                                         int32_t nmaps, float lr, double* loss_out, void* stream);
+/*
+ * Let `pr` answer most reassessments of a 3-D Cahn-Hilliard plan with one run
+ * whose block map matches the predictor's.  States are then set every
+ * `horizon` steps (instead of every reassess interval): at multiples of
+ * `judge_every` (and at the first step) by the exact activity scan, in between
+ * by the predictor (ACTIVE where p >= prob_threshold, then the usual
+ * transition dilation and k = 0 forcing), fed with the last exact scan's
+ * activity and the states in force.  Each exact judge counts the blocks it
+ * finds non-frozen that the prediction in force had frozen (spdba_stats
+ * missed_blocks) and replaces the prediction.  The plan does not own `pr`;
+ * pass NULL to detach.
+ */
+spdba_status spdba_plan_attach_predictor(spdba_plan* plan, spdba_predictor* pr, int32_t horizon,
+                                         int32_t judge_every, float prob_threshold);
 
 /*
  * spdba_classify without any allocation.  The paper has no counterpart: this

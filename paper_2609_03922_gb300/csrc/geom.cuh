@@ -37,6 +37,8 @@ struct DevStats {
     unsigned long long n_transition;
     unsigned long long assessments;
     double list_modes;   // modes touched by list-driven updates (for traffic accounting)
+    unsigned long long predictions;
+    unsigned long long missed;
 };
 
 }  // namespace spdba

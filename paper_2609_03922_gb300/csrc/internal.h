@@ -69,3 +69,10 @@ spdba_status make_axis_pass(Pass<T>* out, int ndim, const int64_t* dims, int64_t
                             int mode, TwiddleCache<T>& tw, cudaStream_t st);
 
 }  // namespace spdba
+
+struct spdba_predictor;
+// Predicted states: features from (maxsq, tau, states) -> network -> measure_out = p (FP64).
+spdba_status spdba_predictor_states_internal(spdba_predictor* pr, const double* maxsq, const double* tau,
+                                             uint8_t* states, int32_t nmaps, void* x_scratch, double* measure_out,
+                                             cudaStream_t st);
+bool spdba_predictor_map_matches(const spdba_predictor* pr, long long nd, long long nh, long long nw);

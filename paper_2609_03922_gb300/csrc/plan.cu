@@ -92,6 +92,14 @@ template <typename T> struct Group {
     const C* tw4 = nullptr;         // exp(-2 pi i m / n)
     int B = 1, nblk = 1;
     NLSLaunch nl;                   // NLS launch shapes (fixed at creation)
+    // predictor (3-D CH runs): last exact activity, prediction in force, scratch
+    double* snap_maxsq = nullptr;
+    double* snap_tau = nullptr;
+    double* pmeasure = nullptr;
+    double* pthr = nullptr;
+    uint8_t* pstates = nullptr;
+    void* px = nullptr;
+    bool has_snap = false, has_pred = false;
     int64_t step = 0;
     bool assessed = false;
     std::vector<void*> allocs;
@@ -150,6 +158,9 @@ struct spdba_plan {
     TwiddleCache<float> tw32;
     TwiddleCache<double> tw64;
     cudaGraphExec_t seg_exec = nullptr;   // one reassessment segment (R steps of every group)
+    spdba_predictor* pred = nullptr;
+    int horizon = 0, judge_every = 0;
+    float prob_thr = 0.5f;
     long long seg_launches = 0;
     int nruns() const { return (int)runs.size(); }
 };
@@ -371,6 +382,50 @@ template <typename T> static spdba_status group_assess(spdba_plan* p, Group<T>& 
     return SPDBA_OK;
 }
 
+// blocks the exact states mark non-frozen while the prediction in force had them frozen
+__global__ void missed_kernel(const uint8_t* __restrict__ exact, const uint8_t* __restrict__ pred, long long nb,
+                              DevStats* stats) {
+    unsigned long long c = 0;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x)
+        c += (exact[b] != 0 && pred[b] == 0) ? 1ull : 0ull;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&stats->missed, c);
+}
+__global__ void count_prediction_kernel(DevStats* stats) { stats->predictions += 1; }
+
+// Reassessment with an attached predictor (3-D CH, one run): exact judge or prediction.
+template <typename T> static spdba_status group_assess_predicted(spdba_plan* p, Group<T>& r) {
+    cudaStream_t st = p->st;
+    spdba_status s;
+    const long long nb = r.g.blocks();
+    const bool judge = !r.has_snap || r.step % p->judge_every == 0;
+    if (judge) {
+        if ((s = group_assess<T>(p, r)) != SPDBA_OK) return s;
+        if (r.has_pred) {
+            missed_kernel<<<grid_for(nb, 256), 256, 0, st>>>(r.states, r.pstates, nb, r.stats);
+            p->launches += 1;
+        }
+        SPDBA_CUDA(cudaMemcpyAsync(r.snap_maxsq, r.maxsq, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+        SPDBA_CUDA(cudaMemcpyAsync(r.snap_tau, r.tau, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        r.has_snap = true;
+        r.has_pred = false;
+        return SPDBA_OK;
+    }
+    ProfScope ps(p, K_ASSESS, 0.0);
+    if ((s = spdba_predictor_states_internal(p->pred, r.snap_maxsq, r.snap_tau, r.states, 1, r.px, r.pmeasure, st)) !=
+        SPDBA_OK)
+        return s;
+    if ((s = launch_classify(r.g, r.pmeasure, 0, r.pthr, p->opt.force_dc, p->opt.transitions, 0, r.active, r.states,
+                             r.chi, r.list, r.count, r.scratch, r.stats, st)) != SPDBA_OK)
+        return s;
+    SPDBA_CUDA(cudaMemcpyAsync(r.pstates, r.states, nb, cudaMemcpyDeviceToDevice, st));
+    count_prediction_kernel<<<1, 1, 0, st>>>(r.stats);
+    p->launches += 10;
+    r.has_pred = true;
+    r.assessed = true;
+    return SPDBA_OK;
+}
+
 static bool all_active_step(const spdba_plan* p, int64_t step) {
     return step < p->opt.warmup_steps || (p->opt.refresh_every > 0 && step > 0 && step % p->opt.refresh_every == 0);
 }
@@ -379,8 +434,12 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
     cudaStream_t st = p->st;
     spdba_status s;
     const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
-    const bool reassess = adaptive && (!r.assessed || r.step % p->reassess == 0);
-    if (reassess && (s = group_assess<T>(p, r)) != SPDBA_OK) return s;
+    const int interval = p->pred ? p->horizon : p->reassess;
+    const bool reassess = adaptive && (!r.assessed || r.step % interval == 0);
+    if (reassess) {
+        s = p->pred ? group_assess_predicted<T>(p, r) : group_assess<T>(p, r);
+        if (s != SPDBA_OK) return s;
+    }
     // pre-update: c = Re(IFFT(c_hat)), g = c^3 - c, g_hat = FFT(g)
     const double pass_bytes = 2.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n);
     const cx_t<T>* src = r.c_hat;
@@ -550,6 +609,7 @@ template <typename T> static spdba_status direct_steps(spdba_plan* p, int64_t n)
 // inside: its launch sequence is the same every time, so it is captured once
 // into a CUDA graph and replayed.
 template <typename T> static bool segment_ready(spdba_plan* p) {
+    if (p->pred) return false;   // judge/prediction alternate: the launch sequence varies
     for (auto& g : groups<T>(p)) {
         if (g->step % p->reassess != 0) return false;
         for (int64_t s = g->step; s < g->step + p->reassess; ++s)
@@ -630,6 +690,8 @@ static spdba_status run_set_field(spdba_plan* p, Group<T>& r, long long sub, con
     }
     r.step = 0;
     r.assessed = false;
+    r.has_snap = false;
+    r.has_pred = false;
     SPDBA_CUDA(cudaMemsetAsync(r.stats + sub, 0, sizeof(DevStats), st));
     SPDBA_CUDA(cudaMemsetAsync(r.states + sub * r.g.bpr(), SPDBA_ACTIVE, r.g.bpr(), st));
     return SPDBA_OK;
@@ -900,6 +962,8 @@ template <typename T> static spdba_status get_stats_t(spdba_plan* p, Group<T>& r
     out->max_amp = d.max_amp;
     out->mass = d.mass;
     out->active_ratio_sum = d.ratio_sum;
+    out->predictions = (int64_t)d.predictions;
+    out->missed_blocks = (int64_t)d.missed;
     return SPDBA_OK;
 }
 
@@ -958,6 +1022,68 @@ extern "C" spdba_status spdba_profile_end(spdba_plan* p, spdba_kernel_time* out,
         if (agg[k].launches > 0 && out) out[n++] = agg[k];
     if (n_out) *n_out = n;
     if (launches_out) *launches_out = p->launches;
+    return SPDBA_OK;
+}
+
+template <typename T>
+static spdba_status get_activity_t(spdba_plan* p, Group<T>& r, long long sub, double* maxsq, double* tau, int on_dev) {
+    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const long long bpr = r.g.bpr();
+    // with a predictor attached, the last exact scan is kept in the snapshot
+    const double* src = r.has_snap ? r.snap_maxsq : r.maxsq;
+    const double* tsrc = r.has_snap ? r.snap_tau : r.tau;
+    if (maxsq) SPDBA_CUDA(cudaMemcpyAsync(maxsq, src + sub * bpr, sizeof(double) * bpr, kind, p->st));
+    if (tau) SPDBA_CUDA(cudaMemcpyAsync(tau, tsrc + sub, sizeof(double), kind, p->st));
+    SPDBA_CUDA(cudaStreamSynchronize(p->st));
+    return SPDBA_OK;
+}
+
+extern "C" spdba_status spdba_get_activity(spdba_plan* p, int32_t run, double* maxsq, double* tau, int32_t on_dev) {
+    PLAN_CHECK(p);
+    if (!run_ok(p, run)) return fail(SPDBA_ERR_ARG, "spdba_get_activity: bad run");
+    return latch(p, with_run(p, run, [&](auto& G, long long sub) { return get_activity_t(p, G, sub, maxsq, tau, on_dev); }));
+}
+
+template <typename T> static spdba_status attach_t(spdba_plan* p, spdba_predictor* pr) {
+    auto& gs = groups<T>(p);
+    if (gs.size() != 1 || gs[0]->ndim != 3 || gs[0]->batch != 1 || p->opt.model != SPDBA_MODEL_CH)
+        return fail(SPDBA_ERR_UNSUPPORTED, "a predictor attaches to a 3-D Cahn-Hilliard plan with one run");
+    Group<T>& r = *gs[0];
+    if (!spdba_predictor_map_matches(pr, r.g.nb[0], r.g.nb[1], r.g.nb[2]))
+        return fail(SPDBA_ERR_ARG, "predictor block map does not match the plan's");
+    const long long nb = r.g.blocks();
+    spdba_status s;
+    if (!r.snap_maxsq) {
+        if ((s = r.alloc(&r.snap_maxsq, sizeof(double) * nb)) != SPDBA_OK) return s;
+        if ((s = r.alloc(&r.snap_tau, sizeof(double))) != SPDBA_OK) return s;
+        if ((s = r.alloc(&r.pmeasure, sizeof(double) * nb)) != SPDBA_OK) return s;
+        if ((s = r.alloc(&r.pthr, sizeof(double))) != SPDBA_OK) return s;
+        if ((s = r.alloc(&r.pstates, nb)) != SPDBA_OK) return s;
+        if ((s = r.alloc(&r.px, 2 * 2 * nb)) != SPDBA_OK) return s;   // bf16 x 2 channels
+    }
+    double thr = (double)p->prob_thr;
+    SPDBA_CUDA(cudaMemcpy(r.pthr, &thr, sizeof(double), cudaMemcpyHostToDevice));
+    r.has_snap = false;
+    r.has_pred = false;
+    r.assessed = false;
+    return SPDBA_OK;
+}
+
+extern "C" spdba_status spdba_plan_attach_predictor(spdba_plan* p, spdba_predictor* pr, int32_t horizon,
+                                                   int32_t judge_every, float prob_threshold) {
+    PLAN_CHECK(p);
+    if (!pr) {
+        p->pred = nullptr;
+        return SPDBA_OK;
+    }
+    if (horizon < 1 || judge_every < horizon || judge_every % horizon != 0 || !(prob_threshold > 0.f))
+        return fail(SPDBA_ERR_ARG, "attach: need horizon >= 1, judge_every a multiple of horizon, threshold > 0");
+    p->horizon = horizon;
+    p->judge_every = judge_every;
+    p->prob_thr = prob_threshold;
+    spdba_status s = p->precision == SPDBA_C64 ? attach_t<float>(p, pr) : attach_t<double>(p, pr);
+    if (s != SPDBA_OK) return latch(p, s);
+    p->pred = pr;
     return SPDBA_OK;
 }
 

@@ -544,3 +544,7 @@ spdba_status spdba_predictor_states_internal(spdba_predictor* pr, const double* 
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;
 }
+
+bool spdba_predictor_map_matches(const spdba_predictor* pr, long long nd, long long nh, long long nw) {
+    return pr && pr->m.D == nd && pr->m.H == nh && pr->m.W == nw;
+}

@@ -35,7 +35,8 @@ class spdba_options(ctypes.Structure):
 class spdba_stats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("assessments", ctypes.c_int64), ("nblocks", ctypes.c_int64),
                 ("n_active", ctypes.c_int64), ("n_transition", ctypes.c_int64), ("tau", ctypes.c_double),
-                ("max_amp", ctypes.c_double), ("mass", ctypes.c_double), ("active_ratio_sum", ctypes.c_double)]
+                ("max_amp", ctypes.c_double), ("mass", ctypes.c_double), ("active_ratio_sum", ctypes.c_double),
+                ("predictions", ctypes.c_int64), ("missed_blocks", ctypes.c_int64)]
 
 
 class spdba_kernel_time(ctypes.Structure):
@@ -63,6 +64,8 @@ SIGNATURES = {
     "spdba_get_mask": (_S, [_P, ctypes.c_int32, _P, ctypes.c_int64]),
     "spdba_get_stats": (_S, [_P, ctypes.c_int32, ctypes.POINTER(spdba_stats)]),
     "spdba_sync": (_S, [_P]),
+    "spdba_get_activity": (_S, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
+    "spdba_plan_attach_predictor": (_S, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
     "spdba_profile_begin": (_S, [_P]),
     "spdba_profile_end": (_S, [_P, ctypes.POINTER(spdba_kernel_time), ctypes.c_int32, _I32P,
                               ctypes.POINTER(ctypes.c_int64)]),
@@ -252,6 +255,22 @@ class Plan:
             k = buf[i]
             out[k.name.decode()] = {"launches": int(k.launches), "total_ms": float(k.total_ms), "bytes": float(k.bytes)}
         return out, int(launches.value)
+
+    def get_activity(self, maxsq=None, tau=None, run=0):
+        """Per-block max |q|^2 and tau of the last exact reassessment (numpy, or into
+        the given device tensors)."""
+        if maxsq is None:
+            maxsq = np.empty(self.nblocks_shape(run), dtype=np.float64)
+            tau_h = np.empty(1, dtype=np.float64)
+            check(lib().spdba_get_activity(self._p, run, maxsq.ctypes.data, tau_h.ctypes.data, 0))
+            return maxsq, float(tau_h[0])
+        check(lib().spdba_get_activity(self._p, run, maxsq.data_ptr(), tau.data_ptr(), 1))
+        return maxsq, tau
+
+    def attach_predictor(self, predictor, horizon=20, judge_every=100, prob_threshold=0.5):
+        self._pred = predictor
+        check(lib().spdba_plan_attach_predictor(self._p, predictor._p if predictor is not None else None,
+                                                int(horizon), int(judge_every), float(prob_threshold)))
 
     def get_stats(self, run=0):
         s = spdba_stats()
