@@ -51,6 +51,13 @@ template <int L, int P, bool ODD> struct LayoutA {
     static constexpr bool PMAP = false;
     static __device__ __forceinline__ int idx(int p, int j) { return p * PSTR + j + (j >> 4); }
 };
+// Every second pencil of a layout-A tile (pencil m at slot 2m): the packed
+// pencils of the two-real-signals transforms.
+template <int L, int P> struct LayoutA2 {
+    static constexpr int PSTR = 2 * (L + L / 16 + 1);
+    static constexpr bool PMAP = false;
+    static __device__ __forceinline__ int idx(int m, int j) { return m * PSTR + j + (j >> 4); }
+};
 template <int L, int P> struct LayoutB {
     static constexpr int SIZE = P * L;
     static constexpr bool PMAP = true;
@@ -248,9 +255,14 @@ __device__ __forceinline__ void store_tile(const cx_t<T>* sm, const PassParams<T
                     j = u / (P / 2); p = (u % (P / 2)) * 2;
                     float4 t = *reinterpret_cast<const float4*>(sm + LY::idx(p, j));
                     v0 = make_float2(t.x, t.y); v1 = make_float2(t.z, t.w);
-                } else {
+                } else if constexpr (PFAST) {
+                    // pencils are the unit stride: (p, j) and (p + 1, j) are adjacent in memory
                     j = u / (P / 2); p = (u % (P / 2)) * 2;
                     v0 = sm[LY::idx(p, j)]; v1 = sm[LY::idx(p + 1, j)];
+                } else {
+                    // elements are the unit stride: (p, j) and (p, j + 1), j even
+                    p = u / (L / 2); j = (u % (L / 2)) * 2;
+                    v0 = sm[LY::idx(p, j)]; v1 = sm[LY::idx(p, j + 1)];
                 }
                 if (q0 + p < npencil) {
                     long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, a.generic);
@@ -539,7 +551,57 @@ __device__ __forceinline__ void tile_body(cx_t<T>* sm, const PassParams<T>& a, l
     } else if constexpr (MODE == PASS_CH_UPDATE) {
         run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
     } else if constexpr (MODE == PASS_CH_NL) {
-        // inverse transform along this axis completes c = IFFT(c_hat) (scaled by nl_scale)
+        // c = Re(IFFT_x(w)) equals IFFT_x of w's Hermitian part H(w)(k) = (w(k) + conj(w(-k)))/2,
+        // which lies in the same pencil.  Two Hermitian pencils a, b go through one
+        // complex transform as H(a) + i H(b): the real and imaginary parts of the result
+        // are the two real fields; g = c^3 - c of both is packed as g_a + i g_b, transformed
+        // forward once, and separated by symmetry (G_a(k) = (Z(k) + conj Z(-k))/2,
+        // G_b(k) = (Z(k) - conj Z(-k))/(2i)).
+      if constexpr (P % 2 == 0 && !LY::PMAP) {
+        using L2 = LayoutA2<L, P>;
+        constexpr int H = L / 2 + 1;   // k = 0 .. L/2 (each with its mirror L - k)
+        for (int e = threadIdx.x; e < (P / 2) * H; e += NT) {
+            const int m = e / H, k = e % H, kr = (L - k) % L;
+            const C a0 = sm[LY::idx(2 * m, k)], a1 = sm[LY::idx(2 * m, kr)];
+            const C b0 = sm[LY::idx(2 * m + 1, k)], b1 = sm[LY::idx(2 * m + 1, kr)];
+            const T h = (T)0.5;
+            // H(a)(k) and H(b)(k); H(x)(-k) = conj(H(x)(k))
+            const C ha = mk<C>(h * (a0.x + a1.x), h * (a0.y - a1.y));
+            const C hb = mk<C>(h * (b0.x + b1.x), h * (b0.y - b1.y));
+            sm[LY::idx(2 * m, k)] = mk<C>(ha.x - hb.y, ha.y + hb.x);      // H(a) + i H(b) at k
+            sm[LY::idx(2 * m, kr)] = mk<C>(ha.x + hb.y, -ha.y + hb.x);    // at -k
+        }
+        __syncthreads();
+        run_stages<T, L, P / 2, NT, +1, L2>(sm, a.tw);
+        T msum = 0;
+        for (int e = threadIdx.x; e < (P / 2) * L; e += NT) {
+            const int m = e / L, j = e % L;
+            const C v = sm[L2::idx(m, j)];
+            const T ca = v.x * a.nl_scale, cb = v.y * a.nl_scale;
+            msum += ca + cb;
+            sm[L2::idx(m, j)] = mk<C>(ca * ca * ca - ca, cb * cb * cb - cb);
+        }
+        if (a.mass != nullptr) {
+            double ms = (double)msum;
+            ms = warp_sum(ms);
+            if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);
+        }
+        __syncthreads();
+        run_stages<T, L, P / 2, NT, -1, L2>(sm, a.tw);
+        for (int e = threadIdx.x; e < (P / 2) * H; e += NT) {
+            const int m = e / H, k = e % H, kr = (L - k) % L;
+            const C z0 = sm[LY::idx(2 * m, k)], z1 = sm[LY::idx(2 * m, kr)];
+            const T h = (T)0.5;
+            const C ga = mk<C>(h * (z0.x + z1.x), h * (z0.y - z1.y));     // (Z(k) + conj Z(-k))/2
+            const C gb = mk<C>(h * (z0.y + z1.y), h * (z1.x - z0.x));     // (Z(k) - conj Z(-k))/(2i)
+            sm[LY::idx(2 * m, k)] = ga;
+            sm[LY::idx(2 * m, kr)] = mk<C>(ga.x, -ga.y);
+            sm[LY::idx(2 * m + 1, k)] = gb;
+            sm[LY::idx(2 * m + 1, kr)] = mk<C>(gb.x, -gb.y);
+        }
+        __syncthreads();
+      } else {
+        // one pencil at a time: inverse transform, c = Re(.)/N, g = c^3 - c, forward
         run_stages<T, L, P, NT, +1, LY>(sm, a.tw);
         T msum = 0;
         for (int e = threadIdx.x; e < P * L; e += NT) {
@@ -558,6 +620,7 @@ __device__ __forceinline__ void tile_body(cx_t<T>* sm, const PassParams<T>& a, l
         }
         __syncthreads();
         run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
+      }
     }
 }
 

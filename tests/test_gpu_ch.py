@@ -71,9 +71,9 @@ def test_config1_2d_128_fp64_full_run():
     check_run(dims, block, 200, 1, c0, 1e-10)
 
 
-@pytest.mark.parametrize("precision,tol1", [(0, 1e-5), (1, 1e-12)])
-def test_one_step_3d(precision, tol1):
-    dims, block = (64, 64, 64), (8, 8, 8)
+@pytest.mark.parametrize("precision,tol1,side", [(0, 1e-5, 64), (1, 1e-12, 64), (0, 1e-5, 128), (0, 1e-5, 32)])
+def test_one_step_3d(precision, tol1, side):
+    dims, block = (side, side, side), (8, 8, 8)
     c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 1)
     check_run(dims, block, 1, precision, c0, tol1)
 

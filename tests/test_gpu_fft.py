@@ -15,7 +15,7 @@ def _rand(shape, seed, dtype):
 
 
 CASES_ND = [(16, 16), (32, 64), (128, 128), (192, 256), (384, 128), (512, 512), (16, 32, 64), (64, 64, 64),
-            (32, 192, 16), (384, 16, 16)]
+            (32, 192, 16), (384, 16, 16), (128, 128, 128), (256, 64, 32)]
 CASES_1D = [16, 256, 1024, 4096, 8192, 65536, 262144]
 
 
