@@ -11,6 +11,11 @@ every 10 steps, blockwise update).  The default K = 2000 timed steps are the
 configuration's full run, started from c0.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                      [--workload ch3d256|ch2d128|nls512|ensemble64|ch3d384pred]
+The default workload is the headline line; the others print one line each for
+the remaining configurations (2-D 128^2 FP64; 512 NLS signals; the uneven
+64-run ensemble, grouped vs one plan per run; 3-D 384^3 with the learned
+predictor).
 Under torchrun (N > 1) every rank runs an independent replica (the 256^3 run
 does not shard); value = N*K / max-over-ranks time.
 """
@@ -33,6 +38,11 @@ THRESHOLD = 1e-6
 REASSESS = 10
 DT, KAPPA = 0.01, 1.0
 MEAN, AMP = 0.1, 0.05
+PROF_EVERY = 7
+# DRAM bytes (read + write) of one launch of the plain L=256 Stockham pass on
+# the 256^3 field, from an ncu capture of the current kernel: 134.28 MB read,
+# 80.18 MB written.
+FFT_PASS_DRAM_BYTES = 134.28e6 + 80.18e6
 METRIC = "spectral steps/s adaptive vs dense on 1 GB300 at rel-L2<=1e-4; % of HBM roofline"
 WORKLOAD = "ch3d-256^3-c64-B8-tau1e-6rel-R10"
 
@@ -131,7 +141,8 @@ def run_ours(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         if profile:
-            plan.profile_begin()
+            # kernel events on one step in PROF_EVERY (coprime with the reassessment interval)
+            plan.profile_begin(PROF_EVERY)
         t0 = time.time()
         e0.record(st)
         plan.step(K)
@@ -174,8 +185,10 @@ def run_ours(args, rank, world, local_rank):
     for name, mode in (("adaptive", spdba.SPDBA_MODE_ADAPTIVE), ("dense", spdba.SPDBA_MODE_REGULAR)):
         pl = make(mode, 0)
         ms, pr, _ = timed(pl, True)
+        # the NL pass runs once per step: it counts the sampled steps
+        nsamp = max(1, pr[0]["fft_fused_nl"]["launches"])
         upd = sum(pr[0].get(k, {"total_ms": 0.0})["total_ms"] for k in ("update_list", "update_dense", "assess"))
-        staged[name] = {"steps_per_s": world * K / (ms / 1e3), "update_stage_ms": upd}
+        staged[name] = {"steps_per_s": world * K / (ms / 1e3), "update_stage_ms": upd * K / nsamp}
         pl.close()
 
     # end to end through the C ABI with host buffers: upload c0, K steps, download c
@@ -249,7 +262,9 @@ def run_ours(args, rank, world, local_rank):
         "kernels_dense": kind_summary(prof_dense),
         "roofline": {"bound": "hbm", "kernel": "fft_pass (Stockham, L=256, c64)", "achieved": achieved,
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None,
+                     "traffic": FFT_PASS_DRAM_BYTES,
+                     "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one plain L=256 launch "
+                                     "(cold L2; the launch ends with part of its output still dirty in L2)",
                      "algorithmic_bytes_per_launch": fp["bytes"] / fp["launches"]},
         "e2e": {"value": steps_total / (e2e_ms / 1e3), "unit": "steps/s",
                 "h2d_bytes_per_step": 4.0 * n / K, "d2h_bytes_per_step": 4.0 * n / K,
@@ -296,6 +311,202 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ other configurations
+def _timed_steps(plan, steps, set_input, stream=None):
+    """Restart from the input and time `steps` steps with CUDA events on the plan's stream."""
+    import torch
+    set_input()
+    torch.cuda.synchronize()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    plan.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _kind_summary(p):
+    """Per-kernel-kind launches, average event time, GB/s and share of a profile."""
+    out = {}
+    tot = sum(v["total_ms"] for v in p[0].values())
+    for k, v in p[0].items():
+        out[k] = {"launches": v["launches"], "avg_us": 1e3 * v["total_ms"] / max(1, v["launches"]),
+                  "gbs": (v["bytes"] / 1e9) / (v["total_ms"] / 1e3) if v["total_ms"] > 0 else None,
+                  "share": v["total_ms"] / tot if tot > 0 else None}
+    return out
+
+
+def _line(metric, value, unit, steps, warmup, ms, config, extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
+         "ms_per_step": ms / max(1, steps), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+         "data": "synthetic", "config": config}
+    d.update(extra)
+    return d
+
+
+def run_ch2d128(args):
+    """2-D CH 128^2, FP64, 16^2 blocks, tau = 1e-6 max, R = 10, 200 steps (graphs on a side stream)."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    import workloads as W
+    dims, steps = (128, 128), 200
+    c0 = W.ch_initial_condition(dims, mean=0.0, seed=W.BASE_SEED)
+    side = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(side):
+        for mode in (1, 0):
+            pl = spdba.Plan(dims, (16, 16), threshold=1e-6, reassess=10, precision=spdba.SPDBA_C128, mode=mode)
+            _timed_steps(pl, steps, lambda: pl.set_field(c0), side)          # warm-up (captures the graph)
+            ms = _timed_steps(pl, steps, lambda: pl.set_field(c0), side)
+            res[mode] = (ms, pl.get_field(), pl.get_stats())
+            pl.close()
+    rel = float(np.linalg.norm(res[1][1] - res[0][1]) / np.linalg.norm(res[0][1]))
+    return _line("spectral steps/s adaptive vs dense, 2-D CH 128^2 FP64", steps / (res[1][0] / 1e3), "steps/s", steps,
+                 steps, res[1][0], {"workload": "ch2d-128^2-c128-B16-R10", "steps": steps},
+                 {"dtype": "f64", "dense_steps_per_s": steps / (res[0][0] / 1e3),
+                  "rel_l2_adaptive_vs_dense": rel,
+                  "mean_nonfrozen_ratio": res[1][2]["active_ratio_sum"] / steps})
+
+
+def run_nls512(args):
+    """512 NLS signals, lengths 2^e (e uniform 12..18), 8 QPSK channels each, 64 blocks/signal,
+    h = 0.1 km over 80 km (800 steps), one plan (groups by length), graphs on a side stream."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    import workloads as W
+    lengths = W.nls_lengths(512)
+    steps = 800
+    sigs = [W.nls_signal(n, seed=W.BASE_SEED + 1 + i).astype(np.complex64) for i, n in enumerate(lengths)]
+    side = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(side):
+        for mode in (1, 0):
+            pl = spdba.Plan(None, (-64,), threshold=1e-6, reassess=10, batch_dims=[(n,) for n in lengths],
+                            model=spdba.SPDBA_MODEL_NLS, precision=spdba.SPDBA_C64, mode=mode)
+
+            def setin():
+                for r, x in enumerate(sigs):
+                    pl.set_field(x, run=r)
+            _timed_steps(pl, 20, setin, side)
+            ms = _timed_steps(pl, steps, setin, side)
+            ratio = float(np.mean([pl.get_stats(run=r)["active_ratio_sum"] / steps for r in range(0, 512, 37)]))
+            f0 = pl.get_field(run=0)
+            kinds = None
+            if mode == 1:
+                # per-kernel event timing of a short stretch (graph replay off while profiling)
+                pl.profile_begin()
+                pl.step(40)
+                kinds = _kind_summary(pl.profile_end())
+            res[mode] = (ms, ratio, f0, kinds)
+            pl.close()
+    total = int(sum(lengths))
+    rel = float(np.linalg.norm(res[1][2] - res[0][2]) / np.linalg.norm(res[0][2]))
+    return _line("NLS batch steps/s (512 signals, all advance one split step)", steps / (res[1][0] / 1e3), "steps/s",
+                 steps, 20, res[1][0], {"workload": "nls-512-signals-2^12..2^18-c64-64blocks", "samples": total},
+                 {"dtype": "c64", "dense_steps_per_s": steps / (res[0][0] / 1e3),
+                  "samples_per_s": total * steps / (res[1][0] / 1e3),
+                  "hbm_gbs_at_two_passes_per_step": 2 * 16 * total * steps / (res[1][0] / 1e3) / 1e9,
+                  "mean_nonfrozen_ratio_sampled": res[1][1], "rel_l2_adaptive_vs_dense_signal0": rel,
+                  "kernels": res[1][3]})
+
+
+def run_ensemble64(args):
+    """64 CH runs, sides uniform in {128,192,256,384,512}, means U[-0.2,0.2], c64, 16^2 blocks,
+    1000 steps: one grouped plan with graph replay vs one plan per run."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    import workloads as W
+    members = W.ensemble_members(64)
+    steps = 1000
+    c0s = [W.ch_initial_condition((sd, sd), mean=m, seed=seed).astype(np.float32) for sd, m, seed in members]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        pl = spdba.Plan(None, (16, 16), threshold=1e-6, reassess=10, batch_dims=[(sd, sd) for sd, _, _ in members],
+                        precision=spdba.SPDBA_C64)
+
+        def setin():
+            for r, x in enumerate(c0s):
+                pl.set_field(x, run=r)
+        _timed_steps(pl, 20, setin, side)
+        ms_g = _timed_steps(pl, steps, setin, side)
+        ratio = float(np.mean([pl.get_stats(run=r)["active_ratio_sum"] / steps for r in range(64)]))
+        pl.close()
+        plans = [spdba.Plan((sd, sd), (16, 16), threshold=1e-6, reassess=10, precision=spdba.SPDBA_C64, use_graph=0)
+                 for sd, _, _ in members]
+        for p_, x in zip(plans, c0s):
+            p_.set_field(x)
+        for p_ in plans:
+            p_.step(10)
+        for p_, x in zip(plans, c0s):
+            p_.set_field(x)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(steps // 10):
+            for p_ in plans:
+                p_.step(10)
+        e1.record(side)
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        for p_ in plans:
+            p_.close()
+    pts = sum(sd * sd for sd, _, _ in members)
+    return _line("ensemble steps/s (64 uneven CH runs, all advance one step)", steps / (ms_g / 1e3), "steps/s", steps,
+                 20, ms_g, {"workload": "ch2d-ensemble-64-runs-128..512-c64-B16", "points": pts},
+                 {"dtype": "c64", "per_run_plans_steps_per_s": steps / (ms_p / 1e3),
+                  "grouped_over_per_run": ms_p / ms_g, "mean_nonfrozen_ratio": ratio})
+
+
+def run_ch3d384pred(args):
+    """3-D CH 384^3 c64, 8^3 blocks (48^3 map), 5000 steps, with the learned predictor (K = 20,
+    exact judge every 100), trained on traces of two seeded 256^3 runs; compared with the
+    exact adaptive run (R = 10) and the dense run."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    from paper_2609_03922_gb300 import predictor_train as PT
+    import workloads as W
+    tr_steps, steps = 1000, 5000
+    t0 = time.time()
+    traces = [PT.collect_trace((256,) * 3, (8, 8, 8),
+                               W.ch_initial_condition((256,) * 3, mean=0.1, seed=W.BASE_SEED + 500 + i).astype(np.float32),
+                               tr_steps) for i in range(2)]
+    pr32 = PT.TrainedPredictor((32,) * 3, max_batch=8, seed=0)
+    xs, ys = [], []
+    for tr in traces:
+        x, y = PT.make_inputs(pr32, tr, PT.build_samples(tr, 20, 100))
+        xs.append(x)
+        ys.append(y)
+    hist = PT.train(pr32, torch.cat(xs), torch.cat(ys), epochs=30, lr=3e-3)
+    t_train = time.time() - t0
+    pr48 = spdba.Predictor((48,) * 3, max_batch=1, params=pr32.params())
+    dims = (384,) * 3
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED).astype(np.float32)
+    out = {}
+    for name, mode, pred in (("predictor", 1, pr48), ("exact", 1, None), ("dense", 0, None)):
+        pl = spdba.Plan(dims, (8, 8, 8), threshold=1e-6, reassess=10, precision=spdba.SPDBA_C64, mode=mode)
+        if pred is not None:
+            pl.attach_predictor(pred, 20, 100, 0.5)
+        ms = _timed_steps(pl, steps, lambda: pl.set_field(c0))
+        st = pl.get_stats()
+        out[name] = {"ms": ms, "field": pl.get_field(), "stats": st}
+        pl.close()
+    d = out["dense"]["field"].astype(np.float64)
+    rel = {k: float(np.linalg.norm(out[k]["field"] - d) / np.linalg.norm(d)) for k in ("predictor", "exact")}
+    sp, se = out["predictor"]["stats"], out["exact"]["stats"]
+    return _line("spectral steps/s with the learned predictor, 3-D CH 384^3", steps / (out["predictor"]["ms"] / 1e3),
+                 "steps/s", steps, 0, out["predictor"]["ms"], {"workload": "ch3d-384^3-c64-B8-K20-J100"},
+                 {"dtype": "c64 + bf16 predictor", "exact_adaptive_steps_per_s": steps / (out["exact"]["ms"] / 1e3),
+                  "dense_steps_per_s": steps / (out["dense"]["ms"] / 1e3),
+                  "rel_l2_vs_dense": rel, "exact_scans": {"predictor": sp["assessments"], "exact": se["assessments"]},
+                  "predictions": sp["predictions"], "missed_blocks": sp["missed_blocks"],
+                  "mean_nonfrozen_ratio": {"predictor": sp["active_ratio_sum"] / steps,
+                                           "exact": se["active_ratio_sum"] / steps},
+                  "training": {"loss_first_last": [hist[0], hist[-1]], "seconds": t_train}})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,7 +514,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="ch3d256",
+                    choices=["ch3d256", "ch2d128", "nls512", "ensemble64", "ch3d384pred"])
     args = ap.parse_args()
+    if args.workload != "ch3d256":
+        import torch
+        from paper_2609_03922_gb300 import build as B
+        B.build()
+        torch.cuda.set_device(0)
+        fn = {"ch2d128": run_ch2d128, "nls512": run_nls512, "ensemble64": run_ensemble64,
+              "ch3d384pred": run_ch3d384pred}[args.workload]
+        print(json.dumps(fn(args)), flush=True)
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))

@@ -177,6 +177,10 @@ typedef struct spdba_kernel_time {
     double bytes;
 } spdba_kernel_time;
 spdba_status spdba_profile_begin(spdba_plan* plan);
+/* As spdba_profile_begin, but records the kernels of one step in `every`
+   (steps whose index is a multiple of `every`), so that the events disturb a
+   long timed run little.  every >= 1, else SPDBA_ERR_ARG. */
+spdba_status spdba_profile_begin_sampled(spdba_plan* plan, int32_t every);
 spdba_status spdba_profile_end(spdba_plan* plan, spdba_kernel_time* out, int32_t capacity, int32_t* n_out,
                                int64_t* launches_out);
 

@@ -128,6 +128,25 @@ template <int SIGN, typename C> struct Dft<16, SIGN, C> {
     static __device__ __forceinline__ void run(C* v) { DftAB<4, 4, SIGN, C>::run(v); }
 };
 
+// Division of 0 <= x < 2^31 by a divisor 1 <= d < 2^31 fixed at plan time:
+// q = floor(x * m / 2^p) with p = 31 + ceil(log2 d), m = ceil(2^p / d) (the
+// round-up method of Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994); exact because x < 2^31 <= 2^p / d.
+struct FastDiv {
+    uint32_t d = 1, m = 0;   // m = 0: d == 1
+    int s = 0;               // p - 32
+    __host__ __device__ void init(uint32_t dd) {
+        d = dd;
+        if (d <= 1) { d = 1; m = 0; s = 0; return; }
+        int l = 0;
+        while ((1ull << l) < (unsigned long long)d) ++l;
+        const int p = 31 + l;
+        m = (uint32_t)(((1ull << p) + d - 1) / d);
+        s = p - 32;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t x) const { return m ? (__umulhi(x, m) >> s) : x; }
+};
+
 // FP64 max over warp lanes
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll

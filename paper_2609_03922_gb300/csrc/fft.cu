@@ -83,8 +83,8 @@ static spdba_status ensure_smem_attr(const void* f, int smem, bool max_carveout)
     if (g_attr_done.count(f)) return SPDBA_OK;
     // always raise the dynamic limit: some kernels also carry static shared memory
     SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    // row-major (pencil-fastest) pipelined tiles stream through shared memory
-    // only; give them the whole carveout so three CTAs fit per SM
+    // pipelined tiles stream through shared memory only; give them the whole
+    // carveout so that the compiled CTAs per SM fit
     if (max_carveout) SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     g_attr_done.insert(f);
     return SPDBA_OK;
@@ -97,6 +97,10 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     bool loadp = (isJ != 1), storep = (osJ != 1);
     if (loadp && isI != 1) return fail(SPDBA_ERR_UNSUPPORTED, "pass without a unit-stride input direction");
     if (storep && osI != 1) return fail(SPDBA_ERR_UNSUPPORTED, "pass without a unit-stride output direction");
+    // pencil indices and offsets within one tile are 32-bit in the kernels
+    if (O * I >= 0x7fffffffLL) return fail(SPDBA_ERR_UNSUPPORTED, "FFT pass over 2^31 pencils or more");
+    if ((L - 1) * (isJ > osJ ? isJ : osJ) + 4096 * (isI > osI ? isI : osI) > 0x7fffffffLL)
+        return fail(SPDBA_ERR_UNSUPPORTED, "FFT pass with a tile span beyond 2^31 elements");
     KernelInfo ki;
     // the tile size depends only on (T, L); ask once to learn P
     if (!get_pass_kernel<T>(L, sign, mode, loadp, storep, true, &ki))
@@ -104,7 +108,7 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     const bool generic = (I % ki.P) != 0;
     if (!get_pass_kernel<T>(L, sign, mode, loadp, storep, generic, &ki))
         return fail(SPDBA_ERR_UNSUPPORTED, "no FFT pass kernel for length %lld (mode %d)", (long long)L, mode);
-    spdba_status s = ensure_smem_attr(ki.func, ki.smem, ki.pipe && loadp);
+    spdba_status s = ensure_smem_attr(ki.func, ki.smem, ki.pipe);
     if (s != SPDBA_OK) return s;
     long long ntiles = (O * I + ki.P - 1) / ki.P;
     long long grid = ntiles;
@@ -123,6 +127,7 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     Pass<T> ps;
     ps.func = ki.func;
     ps.nt = ki.NT;
+    ps.P = ki.P;
     ps.smem = ki.smem;
     ps.grid = grid;
     ps.p.O = O; ps.p.I = I;
@@ -133,6 +138,7 @@ spdba_status make_pass(Pass<T>* out, int64_t L, int sign, int mode, long long O,
     ps.p.n4 = 1;
     ps.p.scale = (T)1;
     ps.p.generic = generic;
+    ps.p.fd_I.init((uint32_t)I);
     ps.p.nl_scale = (T)1;
     ps.p.mass = nullptr;
     *out = ps;

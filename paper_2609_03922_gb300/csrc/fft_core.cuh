@@ -42,6 +42,16 @@ template <> struct Radices<1024> { using type = RList<16, 16, 4>; };
 template <> struct Radices<2048> { using type = RList<16, 16, 8>; };
 template <> struct Radices<4096> { using type = RList<16, 16, 16>; };
 
+template <class RL> struct LastOf;
+template <int R0> struct LastOf<RList<R0>> { static constexpr int value = R0; };
+template <int R0, int R1, int... Rs> struct LastOf<RList<R0, R1, Rs...>> {
+    static constexpr int value = LastOf<RList<R1, Rs...>>::value;
+};
+template <class RL> struct CountOf;
+template <int... Rs> struct CountOf<RList<Rs...>> { static constexpr int value = sizeof...(Rs); };
+template <int L> struct NSTAGES { static constexpr int value = CountOf<typename Radices<L>::type>::value; };
+template <int L> struct Radices_last { static constexpr int value = LastOf<typename Radices<L>::type>::value; };
+
 // Layout A; ODD selects an odd pencil stride (needed when pencils are read
 // transposed, pencil-fastest), otherwise the stride stays even so that a pair
 // (j, j+1) is one aligned 16-byte shared-memory word.
@@ -50,13 +60,6 @@ template <int L, int P, bool ODD> struct LayoutA {
     static constexpr int SIZE = P * PSTR;
     static constexpr bool PMAP = false;
     static __device__ __forceinline__ int idx(int p, int j) { return p * PSTR + j + (j >> 4); }
-};
-// Every second pencil of a layout-A tile (pencil m at slot 2m): the packed
-// pencils of the two-real-signals transforms.
-template <int L, int P> struct LayoutA2 {
-    static constexpr int PSTR = 2 * (L + L / 16 + 1);
-    static constexpr bool PMAP = false;
-    static __device__ __forceinline__ int idx(int m, int j) { return m * PSTR + j + (j >> 4); }
 };
 template <int L, int P> struct LayoutB {
     static constexpr int SIZE = P * L;
@@ -82,6 +85,9 @@ template <typename T> struct CHFuse {
     int dense;
     DevStats* stats;   // one per run
     Geom g;
+    // divisors of the per-tile geometry (pass-axis block edge, x block edge,
+    // outer block edge (3-D), row length (3-D))
+    FastDiv fd_bp, fd_b2, fd_b1, fd_n2;
 };
 
 template <typename T> struct PassParams {
@@ -101,6 +107,7 @@ template <typename T> struct PassParams {
     int mass_stride;                      // doubles between consecutive fields' accumulators
     long long mass_ppr;                   // pencils per field
     CHFuse<T> fu;                         // PASS_CH_UPDATE only
+    FastDiv fd_I;                         // division by I (pipelined kernel, O * I < 2^31)
 };
 
 // Address of element (p, j) of the tile starting at pencil q0.
@@ -208,7 +215,7 @@ __device__ __forceinline__ void load_tile(cx_t<T>* sm, const PassParams<T>& a, l
 template <typename T, int L, int P, int NT, bool PFAST, class LY>
 __device__ __forceinline__ void issue_tile(cx_t<T>* sm, const PassParams<T>& a, long long q0) {
     using C = cx_t<T>;
-    const long long o = q0 / a.I, i0 = q0 - o * a.I;
+    const long long o = a.fd_I.div((uint32_t)q0), i0 = q0 - o * a.I;
     const C* base = a.in + o * a.isO + i0 * a.isI;
     if constexpr (sizeof(C) == 8 && PFAST) {
         constexpr int UNITS = P * L / 2;
@@ -355,6 +362,154 @@ __device__ __forceinline__ void run_stages(cx_t<T>* sm, const cx_t<T>* tw) {
     run_stages_list<T, L, P, NT, SIGN, LY>(sm, tw, typename Radices<L>::type{});
 }
 
+// Last stage with its outputs handed to `out` instead of written back to
+// shared memory.  For the last stage NS * R == L, so butterfly j of pencil p
+// produces outputs j + r NS, r = 0..R-1.  out.begin(k, p, j) runs before the
+// stage reads its inputs (so that loads the outputs need are in flight during
+// the butterflies); out.emit(k, p, j, v) receives the R outputs.  An output
+// that writes shared memory sets OUT::SYNC (all reads finish first).
+template <typename T, int L, int P, int NT, int SIGN, int NS, int R, class LY, class OUT>
+__device__ __forceinline__ void stockham_stage_out(cx_t<T>* sm, const cx_t<T>* __restrict__ tw, OUT& out) {
+    using C = cx_t<T>;
+    static_assert(NS * R == L, "direct output is for the last stage");
+    constexpr int Q = L / R;
+    constexpr int NB = P * Q;
+    constexpr int PER = (NB + NT - 1) / NT;
+    out.pre();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            int p, j;
+            if constexpr (LY::PMAP) { p = b % P; j = b / P; }
+            else { p = b / Q; j = b % Q; }
+            out.begin(k, p, j);
+        }
+    }
+    C v[PER][R];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            int p, j;
+            if constexpr (LY::PMAP) { p = b % P; j = b / P; }
+            else { p = b / Q; j = b % Q; }
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k][r] = sm[LY::idx(p, j + r * Q)];
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = __ldg(tw + r * j);
+                    if constexpr (SIGN > 0) w.y = -w.y;
+                    v[k][r] = cmul(v[k][r], w);
+                }
+            }
+            Dft<R, SIGN, C>::run(v[k]);
+        }
+    }
+    if constexpr (OUT::SYNC) __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            int p, j;
+            if constexpr (LY::PMAP) { p = b % P; j = b / P; }
+            else { p = b / Q; j = b % Q; }
+            out.emit(k, p, j, v[k]);
+        }
+    }
+}
+
+template <typename T, int L, int P, int NT, int SIGN, class LY, class OUT, int NS, int R, int... Rest>
+__device__ __forceinline__ void run_stages_out_impl(cx_t<T>* sm, const cx_t<T>* tw, OUT& out) {
+    if constexpr (sizeof...(Rest) == 0) {
+        stockham_stage_out<T, L, P, NT, SIGN, NS, R, LY, OUT>(sm, tw, out);
+    } else {
+        stockham_stage<T, L, P, NT, SIGN, NS, R, LY>(sm, tw);
+        run_stages_out_impl<T, L, P, NT, SIGN, LY, OUT, NS * R, Rest...>(sm, tw, out);
+    }
+}
+template <typename T, int L, int P, int NT, int SIGN, class LY, class OUT, int... Rs>
+__device__ __forceinline__ void run_stages_out_list(cx_t<T>* sm, const cx_t<T>* tw, OUT& out, RList<Rs...>) {
+    run_stages_out_impl<T, L, P, NT, SIGN, LY, OUT, 1, Rs...>(sm, tw, out);
+}
+// All stages of a length-L transform, the last one emitting through `out`.
+template <typename T, int L, int P, int NT, int SIGN, class LY, class OUT>
+__device__ __forceinline__ void run_stages_out(cx_t<T>* sm, const cx_t<T>* tw, OUT& out) {
+    run_stages_out_list<T, L, P, NT, SIGN, LY, OUT>(sm, tw, out, typename Radices<L>::type{});
+}
+
+// Hand a transformed tile in shared memory to `out` as if it came from a
+// last stage of radix R2 (outputs j + r L/R2 of butterfly j): the same output
+// code at lower register pressure than the fused last stage.
+template <typename T, int L, int P, int NT, int R2, class LY, class OUT>
+__device__ __forceinline__ void drain_tile(const cx_t<T>* sm, OUT& out) {
+    using C = cx_t<T>;
+    constexpr int Q = L / R2;
+    constexpr int NB = P * Q;
+    constexpr int PER = (NB + NT - 1) / NT;
+    out.pre();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            int p, j;
+            if constexpr (LY::PMAP) { p = b % P; j = b / P; }
+            else { p = b / Q; j = b % Q; }
+            out.begin(k, p, j);
+            C v[R2];
+#pragma unroll
+            for (int r = 0; r < R2; ++r) v[r] = sm[LY::idx(p, j + r * Q)];
+            out.emit(k, p, j, v);
+        }
+    }
+}
+
+// Plain pass output: scaled store of every output straight from registers.
+// Consecutive threads hold consecutive unit-stride outputs (pencils for
+// row-major tiles, elements for pencil-major tiles), so warp stores coalesce.
+template <typename T, int L> struct PlainOut {
+    using C = cx_t<T>;
+    static constexpr bool SYNC = false;
+    C* base;      // output (p = 0, j = 0) of the tile
+    int osI, osJ;  // strides within a tile fit 32 bits (checked at plan time)
+    T scale;
+    __device__ __forceinline__ PlainOut(const PassParams<T>& a, long long q0) {
+        const long long o = a.fd_I.div((uint32_t)q0);
+        base = a.out + (o * a.osO + (q0 - o * a.I) * a.osI);
+        osI = (int)a.osI;
+        osJ = (int)a.osJ;
+        scale = a.scale;
+    }
+    __device__ __forceinline__ void pre() {}
+    __device__ __forceinline__ void begin(int, int, int) {}
+    template <int R> __device__ __forceinline__ void emit(int, int p, int j, C (&v)[R]) {
+        C* po = base + (p * osI + j * osJ);
+#pragma unroll
+        for (int r = 0; r < R; ++r) po[r * (L / R) * osJ] = cscale(v[r], scale);
+    }
+};
+
+// CH nonlinearity on the inverse transform's outputs: c = Re(.) / N (its sum
+// accumulated for the mass), g = c^3 - c written back in natural order.
+template <typename T, int L, class LY> struct NlOut {
+    using C = cx_t<T>;
+    static constexpr bool SYNC = true;
+    C* sm;
+    T scale;
+    T msum;
+    __device__ __forceinline__ void pre() {}
+    __device__ __forceinline__ void begin(int, int, int) {}
+    template <int R> __device__ __forceinline__ void emit(int, int p, int j, C (&v)[R]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T c = v[r].x * scale;
+            msum += c;
+            sm[LY::idx(p, j + r * (L / R))] = mk<C>(c * c * c - c, (T)0);
+        }
+    }
+};
+
 // Four-step twiddle: element (pencil i, output index j) *= W_N^{i j}.
 template <typename T, int L, int P, int NT, int SIGN, class LY>
 __device__ __forceinline__ void apply_fourstep_twiddle(cx_t<T>* sm, const PassParams<T>& a, long long q0) {
@@ -395,6 +550,47 @@ __device__ __forceinline__ long long block_id(const Geom& g, long long c0, long 
     return ((c0 / g.b[0]) * g.nb[1] + c1 / g.b[1]) * g.nb[2] + c2 / g.b[2];
 }
 
+// Per-tile constants of the fused update (32-bit; every thread derives the
+// same values).  The tile holds pencils x0 .. x0 + P - 1 of one row cy of the
+// outer axis (3-D: y; 2-D group: the run), unless `rows` (the tile spans
+// several rows of a small 3-D grid).
+struct UpdTile {
+    int o, i0, cy, x0, bx0, nbx, l_out;
+    long long boff;   // block id offset of (block row 0, x-block bx0)
+    int bstride;      // block id step per block row of the pass axis
+    bool rows;
+};
+template <typename T, int P>
+__device__ __forceinline__ UpdTile upd_tile(const PassParams<T>& a, int q0) {
+    const CHFuse<T>& f = a.fu;
+    const Geom& g = f.g;
+    UpdTile u;
+    u.o = (int)a.fd_I.div((uint32_t)q0);
+    u.i0 = q0 - u.o * (int)a.I;
+    const bool d3 = g.ndim == 3;
+    if (d3) {
+        u.cy = (int)f.fd_n2.div((uint32_t)u.i0);
+        u.x0 = u.i0 - u.cy * (int)g.n[2];
+    } else {
+        u.cy = u.o;
+        u.x0 = u.i0;
+    }
+    u.rows = d3 && u.x0 + P > (int)g.n[2];
+    u.bx0 = (int)f.fd_b2.div((uint32_t)u.x0);
+    u.nbx = (int)f.fd_b2.div((uint32_t)(u.x0 + P - 1)) - u.bx0 + 1;
+    if (d3) {
+        const int by = (int)f.fd_b1.div((uint32_t)u.cy);
+        u.l_out = u.cy - by * g.b[1];
+        u.boff = (long long)by * g.nb[2] + u.bx0;
+        u.bstride = (int)(g.nb[1] * g.nb[2]);
+    } else {
+        u.l_out = 0;
+        u.boff = (long long)u.cy * g.nb[1] * g.nb[2] + u.bx0;
+        u.bstride = (int)g.nb[2];
+    }
+    return u;
+}
+
 // A tile is live when any block its modes belong to is not FROZEN.  Every warp
 // evaluates this independently (no block-wide synchronisation needed).
 template <typename T, int P, int MODE>
@@ -402,21 +598,12 @@ __device__ __forceinline__ bool tile_live(const PassParams<T>& a, long long q0) 
     if constexpr (MODE != PASS_CH_UPDATE) return true;
     else {
         if (a.fu.dense) return true;
-        const Geom& g = a.fu.g;
-        long long c0, c1, c2;
-        fuse_coords<T>(a, q0, 0, 0, c0, c1, c2);
-        const long long bx0 = c2 / g.b[2], bx1 = (c2 + P - 1) / g.b[2];
-        const long long nbx = bx1 - bx0 + 1;
-        // blocks along the pass axis: all of them
-        const long long npass = g.ndim == 3 ? g.nb[0] : g.nb[1];
-        const long long total = npass * nbx;
+        const UpdTile u = upd_tile<T, P>(a, (int)q0);
+        if (u.rows) return true;
+        const int npass = (int)(a.fu.g.ndim == 3 ? a.fu.g.nb[0] : a.fu.g.nb[1]);
         bool live = false;
-        for (long long k = threadIdx.x & 31; k < total && !live; k += 32) {
-            long long bp = k / nbx, bx = bx0 + k % nbx;
-            long long id = g.ndim == 3 ? (bp * g.nb[1] + c1 / g.b[1]) * g.nb[2] + bx
-                                       : (c0 * g.nb[1] + bp) * g.nb[2] + bx;
-            live = a.fu.states[id] != 0;
-        }
+        for (int bp = threadIdx.x & 31; bp < npass && !live; bp += 32)
+            for (int bx = 0; bx < u.nbx; ++bx) live |= a.fu.states[u.boff + (long long)bp * u.bstride + bx] != 0;
         return __any_sync(0xffffffffu, live);
     }
 }
@@ -434,111 +621,167 @@ template <typename T, int NT> __device__ __forceinline__ void ch_update_stats(co
     }
 }
 
-// Update epilogue: g_hat of the tile is in shared memory (layout B).  The
-// tile's block states and chi bits are staged in shared memory once; every
-// thread issues its c_hat loads (non-frozen rows only) before using any.
+// Update of a tile that spans several rows of a small grid (P > row length):
+// g_hat of the tile is in shared memory; per-mode coordinates and states.
 template <typename T, int L, int P, int NT, class LY>
-__device__ __forceinline__ void ch_update_tile(const cx_t<T>* sm, const PassParams<T>& a, long long q0) {
+__device__ __forceinline__ void ch_update_tile_rows(const cx_t<T>* sm, const PassParams<T>& a, long long q0) {
     using C = cx_t<T>;
     const CHFuse<T>& f = a.fu;
     const Geom& g = f.g;
-    constexpr int MAXB = 256;
-    __shared__ uint8_t s_st[MAXB], s_chi[MAXB];
-    // tile-constant coordinates: 3-D (z = j, y, x0 + p); 2-D group (run, y = j, x0 + p)
-    const long long o = q0 / a.I, i0 = q0 - o * a.I;
-    const bool d3 = g.ndim == 3;
-    if (d3 && (i0 % g.n[2]) + P > g.n[2]) {
-        // the tile spans several rows of a small grid: per-mode coordinates and states
-        constexpr int UN = P * L;
-        for (int u = threadIdx.x; u < UN; u += NT) {
-            const int j = u / P, p = u % P;
-            long long c0, c1, c2;
-            fuse_coords<T>(a, q0, p, j, c0, c1, c2);
-            const long long id = block_id(g, c0, c1, c2);
-            const int st = f.dense ? SPDBA_ACTIVE : f.states[id];
+    constexpr int UN = P * L;
+    for (int u = threadIdx.x; u < UN; u += NT) {
+        const int j = u / P, p = u % P;
+        long long c0, c1, c2;
+        fuse_coords<T>(a, q0, p, j, c0, c1, c2);
+        const long long id = block_id(g, c0, c1, c2);
+        const int st = f.dense ? SPDBA_ACTIVE : f.states[id];
+        if (st == SPDBA_FROZEN) continue;
+        const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
+        C cv = f.c_hat[ad];
+        C nv = ch_new(cv, sm[LY::idx(p, j)], (f.k2ax[0][c0] + f.k2ax[1][c1]) + f.k2ax[2][c2], f.dt, f.dtkappa);
+        if (st == SPDBA_TRANSITION)
+            nv = ch_blend<T>(cv, nv, f.taper, g, f.chi[id], (int)(c0 % g.b[0]), (int)(c1 % g.b[1]),
+                             (int)(c2 % g.b[2]));
+        f.c_hat[ad] = nv;
+    }
+}
+
+// Per-tile table of the update: entry (bp, bx) = state | chi << 2 of the block
+// in block row bp of the pass axis and x-block bx0 + bx (bytes).
+constexpr int kUpdTable = 4096;
+__host__ __device__ __forceinline__ int upd_table_cols(int P, int bx) { return (P + bx - 2) / bx + 1; }
+// The update pass stages c_hat in a third tile buffer for row-major tiles of
+// L <= 256 whose last stage emits directly (not the radix-3 tail of 192).
+template <typename T, int L> __host__ __device__ constexpr bool upd_stages_chat() {
+    return L <= 256 && Radices_last<L>::value != 3;
+}
+
+// Update emitted from the forward transform's last stage (tile within one row):
+// each output is updated and stored from registers.  With CS the tile's
+// non-frozen c_hat rows were staged in shared memory (layout LY) by cp.async
+// during the transform; otherwise a butterfly's c_hat loads are issued before
+// its arithmetic.
+template <typename T, int L, int P, int NT, int R, bool CS, class LY> struct UpdOut {
+    using C = cx_t<T>;
+    static constexpr bool SYNC = false;
+    static constexpr int NS = L / R;
+    static constexpr int PER = (P * NS + NT - 1) / NT;
+    static_assert(NT % P == 0, "each thread keeps one pencil");
+    const PassParams<T>& a;
+    const uint8_t* tab;   // shared per-tile table
+    const T* kp;          // shared |k|^2 table of the pass axis
+    const C* cs;          // staged c_hat tile (CS)
+    int nbx, bxs, lx, l_out;
+    C* cb;                // c_hat of (p, j = 0)
+    int osJ;
+    T kx, kc;
+    C cv[CS ? 1 : PER][CS ? 1 : R];
+    __device__ __forceinline__ UpdOut(const PassParams<T>& a_, const UpdTile& u, const uint8_t* tab_, const T* kp_,
+                                      const C* cs_)
+        : a(a_), tab(tab_), kp(kp_), cs(cs_) {
+        const CHFuse<T>& f = a.fu;
+        const bool d3 = f.g.ndim == 3;
+        nbx = u.nbx;
+        const int x = u.x0 + (int)(threadIdx.x % P);
+        const int bx = (int)f.fd_b2.div((uint32_t)x);
+        bxs = bx - u.bx0;
+        lx = x - bx * f.g.b[2];
+        kx = f.k2ax[2][x];
+        kc = d3 ? f.k2ax[1][u.cy] : f.k2ax[0][u.cy];
+        l_out = u.l_out;
+        cb = f.c_hat + ((long long)u.o * a.osO + (long long)(u.i0 + (int)(threadIdx.x % P)) * a.osI);
+        osJ = (int)a.osJ;
+    }
+    // before the last stage: the staged c_hat must have landed and be visible
+    __device__ __forceinline__ void pre() {
+        if constexpr (CS) {
+            cp_async_wait<0>();
+            __syncthreads();
+        }
+    }
+    __device__ __forceinline__ unsigned entry(int jj) const { return tab[(int)a.fu.fd_bp.div((uint32_t)jj) * nbx + bxs]; }
+    __device__ __forceinline__ void begin(int k, int, int j) {
+        if constexpr (!CS) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int jj = j + r * NS;
+                if ((entry(jj) & 3u) != SPDBA_FROZEN) cv[k][r] = cb[jj * osJ];
+            }
+        }
+    }
+    __device__ __forceinline__ void emit(int k, int p, int j, C (&v)[R]) {
+        const CHFuse<T>& f = a.fu;
+        const bool d3 = f.g.ndim == 3;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int jj = j + r * NS;
+            const int bp = (int)f.fd_bp.div((uint32_t)jj);
+            const unsigned e = tab[bp * nbx + bxs];
+            const int st = (int)(e & 3u);
             if (st == SPDBA_FROZEN) continue;
-            const long long ad = tile_addr(q0, p, j, a.I, a.osO, a.osI, a.osJ, 0);
-            C cv = f.c_hat[ad];
-            C nv = ch_new(cv, sm[LY::idx(p, j)], (f.k2ax[0][c0] + f.k2ax[1][c1]) + f.k2ax[2][c2], f.dt, f.dtkappa);
-            if (st == SPDBA_TRANSITION)
-                nv = ch_blend<T>(cv, nv, f.taper, g, f.chi[id], (int)(c0 % g.b[0]), (int)(c1 % g.b[1]),
-                                 (int)(c2 % g.b[2]));
-            f.c_hat[ad] = nv;
-        }
-        return;
-    }
-    const long long cy = d3 ? i0 / g.n[2] : o;        // coordinate on the non-pass outer axis
-    const long long x0 = d3 ? i0 - cy * g.n[2] : i0;
-    const int Bp = d3 ? g.b[0] : g.b[1];               // block edge along the pass axis
-    const long long npass = d3 ? g.nb[0] : g.nb[1];
-    const long long bx0 = x0 / g.b[2];
-    const int nbx = (int)((x0 + P - 1) / g.b[2] - bx0 + 1);
-    const int nst = (int)(npass * nbx);
-    for (int k = threadIdx.x; k < nst; k += NT) {
-        long long bp = k / nbx, bx = bx0 + k % nbx;
-        long long id = d3 ? (bp * g.nb[1] + cy / g.b[1]) * g.nb[2] + bx : (cy * g.nb[1] + bp) * g.nb[2] + bx;
-        s_st[k] = f.dense ? (uint8_t)SPDBA_ACTIVE : f.states[id];
-        s_chi[k] = f.dense ? (uint8_t)0 : f.chi[id];
-    }
-    __syncthreads();
-    const T* __restrict__ kp = d3 ? f.k2ax[0] : f.k2ax[1];   // |k|^2 table of the pass axis
-    const T kc = d3 ? f.k2ax[1][cy] : f.k2ax[0][cy];         // fixed outer axis (0 for a group's run axis)
-    const int l_out = (int)(d3 ? cy % g.b[1] : 0);
-    constexpr int E = sizeof(C) == 8 ? 2 : 1;   // modes per 16-byte access
-    constexpr int UPR = P / E;                   // units per row of the tile
-    static_assert(NT % UPR == 0, "threads must cover whole rows");
-    constexpr int JSTEP = NT / UPR;              // rows advanced per unit step
-    constexpr int PER = L / JSTEP;               // units per thread
-    // this thread's pencil offset and first row never change within the tile
-    const int p = (threadIdx.x % UPR) * E;
-    const int j0 = threadIdx.x / UPR;
-    const long long x = x0 + p;
-    const int bxs = (int)(x / g.b[2] - bx0);
-    const int lx = (int)(x % g.b[2]);
-    T kx[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) kx[e] = f.k2ax[2][x + e];
-    const long long o2 = (q0 / a.I) * a.osO + (i0 + p) * a.osI;   // address of (p, j = 0)
-    C cv[PER][E];
-    int stv[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int j = j0 + k * JSTEP;
-        stv[k] = s_st[(j / Bp) * nbx + bxs];
-        if (stv[k] == SPDBA_FROZEN) continue;
-        const long long ad = o2 + (long long)j * a.osJ;
-        if constexpr (E == 2) {
-            float4 t = *reinterpret_cast<const float4*>(f.c_hat + ad);
-            cv[k][0] = make_float2(t.x, t.y);
-            cv[k][1] = make_float2(t.z, t.w);
-        } else {
-            cv[k][0] = f.c_hat[ad];
+            C c;
+            if constexpr (CS) c = cs[LY::idx(p, jj)];
+            else c = cv[k][r];
+            // same association as the staged kernels: (k_outer + k_pass) then + k_x
+            const T k01 = d3 ? kp[jj] + kc : kc + kp[jj];
+            C nv = ch_new(c, v[r], k01 + kx, f.dt, f.dtkappa);
+            if (st == SPDBA_TRANSITION) {
+                const int lj = jj - bp * (d3 ? f.g.b[0] : f.g.b[1]);
+                nv = d3 ? ch_blend<T>(c, nv, f.taper, f.g, e >> 2, lj, l_out, lx)
+                        : ch_blend<T>(c, nv, f.taper, f.g, e >> 2, 0, lj, lx);
+            }
+            cb[jj * osJ] = nv;
         }
     }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        if (stv[k] == SPDBA_FROZEN) continue;
-        const int j = j0 + k * JSTEP;
-        const long long ad = o2 + (long long)j * a.osJ;
-        // same association as the staged kernels: (k_outer + k_pass) then + k_x
-        const T k01 = d3 ? kp[j] + kc : kc + kp[j];
-        C nv[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) nv[e] = ch_new(cv[k][e], sm[LY::idx(p + e, j)], k01 + kx[e], f.dt, f.dtkappa);
-        if (stv[k] == SPDBA_TRANSITION) {
-            const unsigned chi = s_chi[(j / Bp) * nbx + bxs];
-            const int lj = j % Bp;
-#pragma unroll
-            for (int e = 0; e < E; ++e)
-                nv[e] = d3 ? ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, lj, l_out, lx + e)
-                           : ch_blend<T>(cv[k][e], nv[e], f.taper, g, chi, 0, lj, lx + e);
+};
+
+// Fill the per-tile table (visible after the next barrier).
+template <typename T, int L, int P, int NT>
+__device__ __forceinline__ void ch_update_table(uint8_t* tab, const PassParams<T>& a, const UpdTile& u) {
+    const CHFuse<T>& f = a.fu;
+    const int npass = (int)(f.g.ndim == 3 ? f.g.nb[0] : f.g.nb[1]);
+    for (int k = threadIdx.x; k < npass * u.nbx; k += NT) {
+        const int bp = k / u.nbx, bx = k - bp * u.nbx;
+        const long long id = u.boff + (long long)bp * u.bstride + bx;
+        tab[k] = f.dense ? (uint8_t)SPDBA_ACTIVE : (uint8_t)(f.states[id] | (f.chi[id] << 2));
+    }
+}
+
+// Stage the tile's non-frozen c_hat rows into shared memory (row-major tile,
+// one cp.async group).  The table must be visible to every thread.
+template <typename T, int L, int P, int NT, class LY>
+__device__ __forceinline__ void issue_chat(cx_t<T>* cs, const PassParams<T>& a, const UpdTile& u, const uint8_t* tab) {
+    using C = cx_t<T>;
+    const CHFuse<T>& f = a.fu;
+    const C* base = f.c_hat + ((long long)u.o * a.osO + (long long)u.i0 * a.osI);
+    const int osJ = (int)a.osJ;
+    if constexpr (sizeof(C) == 8) {
+        // pencil pairs (p, p + 1): 16 bytes; copied when either block is non-frozen
+        static_assert(NT % (P / 2) == 0, "each thread keeps one pencil pair");
+        constexpr int UNITS = P * L / 2;
+        const int p = (int)(threadIdx.x % (P / 2)) * 2;
+        const int b0 = (int)f.fd_b2.div((uint32_t)(u.x0 + p)) - u.bx0;
+        const int b1 = (int)f.fd_b2.div((uint32_t)(u.x0 + p + 1)) - u.bx0;
+#pragma unroll 4
+        for (int w = threadIdx.x; w < UNITS; w += NT) {
+            const int j = w / (P / 2);
+            const int row = (int)f.fd_bp.div((uint32_t)j) * u.nbx;
+            if ((tab[row + b0] & 3) != SPDBA_FROZEN || (tab[row + b1] & 3) != SPDBA_FROZEN)
+                cp_async16(cs + LY::idx(p, j), base + (p + j * osJ));
         }
-        if constexpr (E == 2) {
-            *reinterpret_cast<float4*>(f.c_hat + ad) = make_float4(nv[0].x, nv[0].y, nv[1].x, nv[1].y);
-        } else {
-            f.c_hat[ad] = nv[0];
+    } else {
+        static_assert(NT % P == 0, "each thread keeps one pencil");
+        constexpr int UNITS = P * L;
+        const int p = (int)(threadIdx.x % P);
+        const int b0 = (int)f.fd_b2.div((uint32_t)(u.x0 + p)) - u.bx0;
+#pragma unroll 4
+        for (int w = threadIdx.x; w < UNITS; w += NT) {
+            const int j = w / P;
+            if ((tab[(int)f.fd_bp.div((uint32_t)j) * u.nbx + b0] & 3) != SPDBA_FROZEN)
+                cp_async16(cs + LY::idx(p, j), base + (p + j * osJ));
         }
     }
+    cp_async_commit();
 }
 
 // Body shared by both kernels: transform the tile in shared memory.
@@ -551,56 +794,7 @@ __device__ __forceinline__ void tile_body(cx_t<T>* sm, const PassParams<T>& a, l
     } else if constexpr (MODE == PASS_CH_UPDATE) {
         run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
     } else if constexpr (MODE == PASS_CH_NL) {
-        // c = Re(IFFT_x(w)) equals IFFT_x of w's Hermitian part H(w)(k) = (w(k) + conj(w(-k)))/2,
-        // which lies in the same pencil.  Two Hermitian pencils a, b go through one
-        // complex transform as H(a) + i H(b): the real and imaginary parts of the result
-        // are the two real fields; g = c^3 - c of both is packed as g_a + i g_b, transformed
-        // forward once, and separated by symmetry (G_a(k) = (Z(k) + conj Z(-k))/2,
-        // G_b(k) = (Z(k) - conj Z(-k))/(2i)).
-      if constexpr (P % 2 == 0 && !LY::PMAP) {
-        using L2 = LayoutA2<L, P>;
-        constexpr int H = L / 2 + 1;   // k = 0 .. L/2 (each with its mirror L - k)
-        for (int e = threadIdx.x; e < (P / 2) * H; e += NT) {
-            const int m = e / H, k = e % H, kr = (L - k) % L;
-            const C a0 = sm[LY::idx(2 * m, k)], a1 = sm[LY::idx(2 * m, kr)];
-            const C b0 = sm[LY::idx(2 * m + 1, k)], b1 = sm[LY::idx(2 * m + 1, kr)];
-            const T h = (T)0.5;
-            // H(a)(k) and H(b)(k); H(x)(-k) = conj(H(x)(k))
-            const C ha = mk<C>(h * (a0.x + a1.x), h * (a0.y - a1.y));
-            const C hb = mk<C>(h * (b0.x + b1.x), h * (b0.y - b1.y));
-            sm[LY::idx(2 * m, k)] = mk<C>(ha.x - hb.y, ha.y + hb.x);      // H(a) + i H(b) at k
-            sm[LY::idx(2 * m, kr)] = mk<C>(ha.x + hb.y, -ha.y + hb.x);    // at -k
-        }
-        __syncthreads();
-        run_stages<T, L, P / 2, NT, +1, L2>(sm, a.tw);
-        T msum = 0;
-        for (int e = threadIdx.x; e < (P / 2) * L; e += NT) {
-            const int m = e / L, j = e % L;
-            const C v = sm[L2::idx(m, j)];
-            const T ca = v.x * a.nl_scale, cb = v.y * a.nl_scale;
-            msum += ca + cb;
-            sm[L2::idx(m, j)] = mk<C>(ca * ca * ca - ca, cb * cb * cb - cb);
-        }
-        if (a.mass != nullptr) {
-            double ms = (double)msum;
-            ms = warp_sum(ms);
-            if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);
-        }
-        __syncthreads();
-        run_stages<T, L, P / 2, NT, -1, L2>(sm, a.tw);
-        for (int e = threadIdx.x; e < (P / 2) * H; e += NT) {
-            const int m = e / H, k = e % H, kr = (L - k) % L;
-            const C z0 = sm[LY::idx(2 * m, k)], z1 = sm[LY::idx(2 * m, kr)];
-            const T h = (T)0.5;
-            const C ga = mk<C>(h * (z0.x + z1.x), h * (z0.y - z1.y));     // (Z(k) + conj Z(-k))/2
-            const C gb = mk<C>(h * (z0.y + z1.y), h * (z1.x - z0.x));     // (Z(k) - conj Z(-k))/(2i)
-            sm[LY::idx(2 * m, k)] = ga;
-            sm[LY::idx(2 * m, kr)] = mk<C>(ga.x, -ga.y);
-            sm[LY::idx(2 * m + 1, k)] = gb;
-            sm[LY::idx(2 * m + 1, kr)] = mk<C>(gb.x, -gb.y);
-        }
-        __syncthreads();
-      } else {
+      {
         // one pencil at a time: inverse transform, c = Re(.)/N, g = c^3 - c, forward
         run_stages<T, L, P, NT, +1, LY>(sm, a.tw);
         T msum = 0;
@@ -644,7 +838,10 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(PassParams<T> a) {
 // Requires I % P == 0 and in/out with the same orientation.
 // Resident CTAs per SM the pipelined kernel is compiled for (register budget).
 template <typename T, int L, int MODE> struct PipeOcc {
-    static constexpr int value = (sizeof(T) == 4 && L <= 256) ? (MODE == PASS_PLAIN ? 3 : MODE == PASS_CH_UPDATE ? 2 : 1) : 1;
+    static constexpr int value = sizeof(T) != 4 || L > 256     ? 1
+                                 : L == 192                    ? (MODE == PASS_CH_NL ? 1 : 2)
+                                 : MODE == PASS_CH_UPDATE      ? 2
+                                                               : 3;
 };
 
 template <typename T, int L, int P, int NT, int SIGN, int MODE, bool PFAST>
@@ -654,6 +851,17 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE>::value) fft_pass_pipe_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm0 = reinterpret_cast<C*>(smem_raw);
     C* sm1 = sm0 + LY::SIZE;
+    __shared__ uint8_t s_tab[MODE == PASS_CH_UPDATE ? kUpdTable : 1];
+    __shared__ T s_kp[MODE == PASS_CH_UPDATE ? L : 1];   // |k|^2 of the pass axis
+    if constexpr (MODE == PASS_CH_UPDATE) {
+        const T* kpg = a.fu.g.ndim == 3 ? a.fu.k2ax[0] : a.fu.k2ax[1];
+        for (int j = threadIdx.x; j < L; j += NT) s_kp[j] = kpg[j];   // visible after the loop's first barrier
+    }
+    // direct stores from the last stage stay coalesced when a warp's lanes
+    // cover at least 32 contiguous bytes of each output row
+    // (the radix-3 tails of 192 and 384 hold too many registers to emit directly)
+    constexpr bool DIRECT = (LY::PMAP || (L / Radices_last<L>::value) * (int)sizeof(C) >= 32) &&
+                            Radices_last<L>::value != 3;
     const long long ntiles = (a.O * a.I) / P;
     if constexpr (MODE == PASS_CH_UPDATE) ch_update_stats<T, NT>(a.fu);
     long long t = blockIdx.x;
@@ -669,9 +877,52 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE>::value) fft_pass_pipe_
         cp_async_wait<1>();
         __syncthreads();
         C* sm = buf ? sm1 : sm0;
-        tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, t * P);
-        if constexpr (MODE == PASS_CH_UPDATE) ch_update_tile<T, L, P, NT, LY>(sm, a, t * P);
-        else store_tile<T, L, P, NT, PFAST, LY>(sm, a, t * P);
+        const long long q0 = t * P;
+        if constexpr (MODE != PASS_CH_UPDATE && !DIRECT) {
+            // short pencil-major pencils: the staged store keeps 16-byte coalesced writes
+            tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
+            store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
+        } else if constexpr (MODE == PASS_PLAIN) {
+            if (a.tw4 != nullptr) {
+                // first pass of a four-step transform: twiddle in shared memory
+                tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
+                store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
+            } else {
+                PlainOut<T, L> out(a, q0);
+                run_stages_out<T, L, P, NT, SIGN, LY>(sm, a.tw, out);
+            }
+        } else if constexpr (MODE == PASS_CH_NL) {
+            // inverse transform with the nonlinearity in its last stage, then forward
+            NlOut<T, L, LY> nl{sm, a.nl_scale, (T)0};
+            run_stages_out<T, L, P, NT, +1, LY>(sm, a.tw, nl);
+            if (a.mass != nullptr) {
+                double ms = warp_sum((double)nl.msum);
+                if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);
+            }
+            __syncthreads();
+            PlainOut<T, L> out(a, q0);
+            run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
+        } else {
+            const UpdTile u = upd_tile<T, P>(a, (int)q0);
+            if (u.rows) {
+                // the tile spans several rows of a small grid
+                run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
+                ch_update_tile_rows<T, L, P, NT, LY>(sm, a, q0);
+            } else if constexpr (upd_stages_chat<T, L>()) {
+                // c_hat of the tile's non-frozen rows streams in during the transform
+                ch_update_table<T, L, P, NT>(s_tab, a, u);
+                __syncthreads();
+                C* smc = sm0 + 2 * LY::SIZE;
+                issue_chat<T, L, P, NT, LY>(smc, a, u, s_tab);
+                UpdOut<T, L, P, NT, Radices_last<L>::value, true, LY> out(a, u, s_tab, s_kp, smc);
+                run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
+            } else {
+                ch_update_table<T, L, P, NT>(s_tab, a, u);
+                run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
+                UpdOut<T, L, P, NT, 4, false, LY> out(a, u, s_tab, s_kp, nullptr);
+                drain_tile<T, L, P, NT, 4, LY>(sm, out);
+            }
+        }
         __syncthreads();
         buf ^= 1;
         t = tn;

@@ -37,6 +37,7 @@ template <typename T> struct TwiddleCache {
 template <typename T> struct Pass {
     const void* func = nullptr;
     int nt = 0, smem = 0;
+    int P = 0;           // pencils per tile
     long long grid = 0;
     PassParams<T> p{};
 };

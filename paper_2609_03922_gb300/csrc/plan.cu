@@ -142,6 +142,8 @@ struct RunRef {
 struct spdba_plan {
     spdba_options opt;
     bool prof = false;
+    int prof_every = 1;     // record the kernels of one step in `prof_every`
+    bool prof_on = false;   // recording the current step
     std::vector<ProfRec> prof_recs;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
@@ -183,10 +185,10 @@ struct ProfScope {
     double bytes;
     cudaEvent_t a = nullptr;
     ProfScope(spdba_plan* pp, int k, double by) : p(pp), kind(k), bytes(by) {
-        if (p->prof && (a = ev_get(p)) != nullptr) cudaEventRecord(a, p->st);
+        if (p->prof && p->prof_on && (a = ev_get(p)) != nullptr) cudaEventRecord(a, p->st);
     }
     ~ProfScope() {
-        if (!p->prof || !a) return;
+        if (!a) return;
         cudaEvent_t b = ev_get(p);
         if (!b) return;
         cudaEventRecord(b, p->st);
@@ -292,6 +294,12 @@ static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const in
         if (a == 0 && p->opt.fuse_update) {
             // the pass along the first axis also applies the update (when a kernel exists for it)
             sf = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_CH_UPDATE, tw, st);
+            // the tile's (row, x-block) state table must fit the kernel's shared table
+            const int64_t bpass = ndim == 3 ? r.g.b[0] : r.g.b[1];
+            if (sf == SPDBA_OK && (dims[0] / bpass) * (int64_t)upd_table_cols(ps.P, (int)r.g.b[2]) > kUpdTable)
+                sf = SPDBA_ERR_UNSUPPORTED;
+            // 32-bit mode indices inside the kernel
+            if (sf == SPDBA_OK && r.batch * r.n >= 0x7fffffffLL) sf = SPDBA_ERR_UNSUPPORTED;
             if (sf == SPDBA_OK) {
                 CHFuse<T>& f = ps.p.fu;
                 f.c_hat = r.c_hat;
@@ -303,6 +311,10 @@ static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const in
                 f.dense = 1;
                 f.stats = r.stats;
                 f.g = r.g;
+                f.fd_bp.init((uint32_t)(ndim == 3 ? r.g.b[0] : r.g.b[1]));
+                f.fd_b2.init((uint32_t)r.g.b[2]);
+                f.fd_b1.init((uint32_t)r.g.b[1]);
+                f.fd_n2.init((uint32_t)r.g.n[2]);
                 r.fused_update = true;
             } else if (sf != SPDBA_ERR_UNSUPPORTED) {
                 return sf;
@@ -430,9 +442,15 @@ static bool all_active_step(const spdba_plan* p, int64_t step) {
     return step < p->opt.warmup_steps || (p->opt.refresh_every > 0 && step > 0 && step % p->opt.refresh_every == 0);
 }
 
+// Whether the kernels of step `step` are recorded by an active profile.
+static void prof_select(spdba_plan* p, long long step) {
+    p->prof_on = p->prof && (p->prof_every <= 1 || step % p->prof_every == 0);
+}
+
 template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>& r) {
     cudaStream_t st = p->st;
     spdba_status s;
+    prof_select(p, r.step);
     const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
     const int interval = p->pred ? p->horizon : p->reassess;
     const bool reassess = adaptive && (!r.assessed || r.step % interval == 0);
@@ -545,6 +563,7 @@ template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T
     const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
     int prev_dense = 1;
     for (int64_t i = 0; i < nsteps; ++i) {
+        prof_select(p, r.step);
         const bool reassess = adaptive && (!r.assessed || r.step % p->reassess == 0);
         const int dense = !adaptive || all_active_step(p, r.step);
         NLSArgs<T> a = nls_args<T>(p, r, r.c_hat, r.batch, dense);
@@ -984,8 +1003,13 @@ template <typename T> static spdba_status list_bytes_now(spdba_plan* p, double* 
     return SPDBA_OK;
 }
 
-extern "C" spdba_status spdba_profile_begin(spdba_plan* p) {
+extern "C" spdba_status spdba_profile_begin(spdba_plan* p) { return spdba_profile_begin_sampled(p, 1); }
+
+extern "C" spdba_status spdba_profile_begin_sampled(spdba_plan* p, int32_t every) {
     PLAN_CHECK(p);
+    if (every < 1) return fail(SPDBA_ERR_ARG, "profile sampling interval must be >= 1");
+    p->prof_every = every;
+    p->prof_on = every == 1;
     p->prof_recs.clear();
     p->ev_used = 0;
     p->launches = 0;
@@ -1001,6 +1025,7 @@ extern "C" spdba_status spdba_profile_end(spdba_plan* p, spdba_kernel_time* out,
     PLAN_CHECK(p);
     if (!p->prof) return fail(SPDBA_ERR_STATE, "profiling was not started");
     p->prof = false;
+    p->prof_on = false;
     cudaError_t e = cudaStreamSynchronize(p->st);
     if (e != cudaSuccess) return latch(p, cuda_fail(e, "profile sync"));
     spdba_kernel_time agg[K_COUNT];

@@ -67,6 +67,7 @@ SIGNATURES = {
     "spdba_get_activity": (_S, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "spdba_plan_attach_predictor": (_S, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
     "spdba_profile_begin": (_S, [_P]),
+    "spdba_profile_begin_sampled": (_S, [_P, ctypes.c_int32]),
     "spdba_profile_end": (_S, [_P, ctypes.POINTER(spdba_kernel_time), ctypes.c_int32, _I32P,
                               ctypes.POINTER(ctypes.c_int64)]),
     "spdba_plan_destroy": (None, [_P]),
@@ -241,8 +242,9 @@ class Plan:
         check(lib().spdba_get_mask(self._p, run, out.ctypes.data, out.size))
         return out
 
-    def profile_begin(self):
-        check(lib().spdba_profile_begin(self._p))
+    def profile_begin(self, every=1):
+        """Record kernel events of every step, or of one step in `every`."""
+        check(lib().spdba_profile_begin_sampled(self._p, int(every)))
 
     def profile_end(self):
         """Returns ({kind: {launches, total_ms, bytes}}, kernel launches since begin)."""
