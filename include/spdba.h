@@ -82,7 +82,7 @@ typedef struct spdba_options {
 /* Per-run statistics, refreshed at each reassessment. */
 typedef struct spdba_stats {
     int64_t step;            /* steps taken so far                                       */
-    int64_t assessments;     /* reassessments done                                       */
+    int64_t assessments;     /* reassessments done (block states set, exact or predicted) */
     int64_t nblocks;         /* blocks in the block map                                  */
     int64_t n_active;        /* ACTIVE blocks at the last reassessment                  */
     int64_t n_transition;    /* TRANSITION blocks at the last reassessment              */

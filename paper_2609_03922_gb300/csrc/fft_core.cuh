@@ -50,6 +50,18 @@ template <int R0, int R1, int... Rs> struct LastOf<RList<R0, R1, Rs...>> {
 template <class RL> struct CountOf;
 template <int... Rs> struct CountOf<RList<Rs...>> { static constexpr int value = sizeof...(Rs); };
 template <int L> struct NSTAGES { static constexpr int value = CountOf<typename Radices<L>::type>::value; };
+template <class RL> struct RArr;
+template <int... Rs> struct RArr<RList<Rs...>> {
+    static constexpr int n = sizeof...(Rs);
+    static constexpr int v[sizeof...(Rs)] = {Rs...};
+};
+// i-th radix of a length and the product of the radices before it
+template <int L> __host__ __device__ constexpr int radix_at(int i) { return RArr<typename Radices<L>::type>::v[i]; }
+template <int L> __host__ __device__ constexpr int ns_at(int i) {
+    int p = 1;
+    for (int k = 0; k < i; ++k) p *= radix_at<L>(k);
+    return p;
+}
 template <int L> struct Radices_last { static constexpr int value = LastOf<typename Radices<L>::type>::value; };
 
 // Layout A; ODD selects an odd pencil stride (needed when pencils are read
@@ -437,6 +449,83 @@ __device__ __forceinline__ void run_stages_out_list(cx_t<T>* sm, const cx_t<T>* 
 template <typename T, int L, int P, int NT, int SIGN, class LY, class OUT>
 __device__ __forceinline__ void run_stages_out(cx_t<T>* sm, const cx_t<T>* tw, OUT& out) {
     run_stages_out_list<T, L, P, NT, SIGN, LY, OUT>(sm, tw, out, typename Radices<L>::type{});
+}
+
+// Stages I .. E-1 of a length-L transform (in shared memory).
+template <typename T, int L, int P, int NT, int SIGN, class LY, int I, int E>
+__device__ __forceinline__ void run_stage_range(cx_t<T>* sm, const cx_t<T>* tw) {
+    if constexpr (I < E) {
+        stockham_stage<T, L, P, NT, SIGN, ns_at<L>(I), radix_at<L>(I), LY>(sm, tw);
+        run_stage_range<T, L, P, NT, SIGN, LY, I + 1, E>(sm, tw);
+    }
+}
+
+// Outputs of a first stage (NS = 1): butterfly j writes j R + r.
+template <typename T, int L, int R, class LY> struct FirstStageOut {
+    using C = cx_t<T>;
+    static constexpr bool SYNC = true;
+    C* sm;
+    __device__ __forceinline__ void pre() {}
+    __device__ __forceinline__ void begin(int, int, int) {}
+    __device__ __forceinline__ void emit(int, int p, int j, C (&v)[R]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[LY::idx(p, j * R + r)] = v[r];
+    }
+};
+
+// The CH nonlinearity between the inverse and the forward transform of one
+// pencil when the inverse's last radix equals the forward's first (R): the
+// inverse's last butterfly j yields exactly the elements j + r L/R that the
+// forward's first butterfly j reads, so both butterflies and c = Re(.)/N,
+// g = c^3 - c run in registers.  NS = the inverse's last-stage span (L / R).
+template <typename T, int L, int P, int NT, int NS, int R, class LY, class OUT>
+__device__ __forceinline__ void nl_middle_stage(cx_t<T>* sm, const cx_t<T>* __restrict__ tw, T nl_scale, T& msum,
+                                                OUT& out) {
+    using C = cx_t<T>;
+    static_assert(NS * R == L, "the middle stage closes the inverse transform");
+    constexpr int Q = L / R;
+    constexpr int NB = P * Q;
+    constexpr int PER = (NB + NT - 1) / NT;
+    out.pre();
+    C v[PER][R];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            int p, j;
+            if constexpr (LY::PMAP) { p = b % P; j = b / P; }
+            else { p = b / Q; j = b % Q; }
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k][r] = sm[LY::idx(p, j + r * Q)];
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = __ldg(tw + r * j);
+                    w.y = -w.y;
+                    v[k][r] = cmul(v[k][r], w);
+                }
+            }
+            Dft<R, +1, C>::run(v[k]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const T c = v[k][r].x * nl_scale;
+                msum += c;
+                v[k][r] = mk<C>(c * c * c - c, (T)0);
+            }
+            Dft<R, -1, C>::run(v[k]);
+        }
+    }
+    if constexpr (OUT::SYNC) __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int b = threadIdx.x + k * NT;
+        if (NB % NT == 0 || b < NB) {
+            int p, j;
+            if constexpr (LY::PMAP) { p = b % P; j = b / P; }
+            else { p = b / Q; j = b % Q; }
+            out.emit(k, p, j, v[k]);
+        }
+    }
 }
 
 // Hand a transformed tile in shared memory to `out` as if it came from a
@@ -837,15 +926,18 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(PassParams<T> a) {
 // the second shared buffer with cp.async while the current one is transformed.
 // Requires I % P == 0 and in/out with the same orientation.
 // Resident CTAs per SM the pipelined kernel is compiled for (register budget).
-template <typename T, int L, int MODE> struct PipeOcc {
-    static constexpr int value = sizeof(T) != 4 || L > 256     ? 1
+// (chosen from the compiler's register counts: the largest count of CTAs at
+// which the kernel does not spill)
+template <typename T, int L, int MODE, bool PFAST> struct PipeOcc {
+    static constexpr int value = sizeof(T) != 4 || L > 512     ? 1
+                                 : L == 384 || L == 512        ? ((MODE == PASS_PLAIN && (PFAST || L == 512)) ? 2 : 1)
                                  : L == 192                    ? (MODE == PASS_CH_NL ? 1 : 2)
                                  : MODE == PASS_CH_UPDATE      ? 2
                                                                : 3;
 };
 
 template <typename T, int L, int P, int NT, int SIGN, int MODE, bool PFAST>
-__global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE>::value) fft_pass_pipe_kernel(PassParams<T> a) {
+__global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pass_pipe_kernel(PassParams<T> a) {
     using C = cx_t<T>;
     using LY = typename std::conditional<PFAST, LayoutB<L, P>, LayoutA<L, P, true>>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -892,16 +984,37 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE>::value) fft_pass_pipe_
                 run_stages_out<T, L, P, NT, SIGN, LY>(sm, a.tw, out);
             }
         } else if constexpr (MODE == PASS_CH_NL) {
-            // inverse transform with the nonlinearity in its last stage, then forward
-            NlOut<T, L, LY> nl{sm, a.nl_scale, (T)0};
-            run_stages_out<T, L, P, NT, +1, LY>(sm, a.tw, nl);
+            constexpr int NST = NSTAGES<L>::value;
+            T msum = 0;
+            if constexpr (radix_at<L>(0) == radix_at<L>(NST - 1)) {
+                // inverse stages but the last; last inverse + nonlinearity + first forward
+                // butterflies in registers; remaining forward stages, the last storing
+                constexpr int R = radix_at<L>(0);
+                run_stage_range<T, L, P, NT, +1, LY, 0, NST - 1>(sm, a.tw);
+                if constexpr (NST == 1) {
+                    PlainOut<T, L> out(a, q0);
+                    nl_middle_stage<T, L, P, NT, 1, R, LY>(sm, a.tw, a.nl_scale, msum, out);
+                } else {
+                    FirstStageOut<T, L, R, LY> fo{sm};
+                    nl_middle_stage<T, L, P, NT, L / R, R, LY>(sm, a.tw, a.nl_scale, msum, fo);
+                    __syncthreads();
+                    run_stage_range<T, L, P, NT, -1, LY, 1, NST - 1>(sm, a.tw);
+                    PlainOut<T, L> out(a, q0);
+                    stockham_stage_out<T, L, P, NT, -1, ns_at<L>(NST - 1), radix_at<L>(NST - 1), LY>(sm, a.tw, out);
+                }
+            } else {
+                // inverse transform with the nonlinearity in its last stage, then forward
+                NlOut<T, L, LY> nl{sm, a.nl_scale, (T)0};
+                run_stages_out<T, L, P, NT, +1, LY>(sm, a.tw, nl);
+                msum = nl.msum;
+                __syncthreads();
+                PlainOut<T, L> out(a, q0);
+                run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
+            }
             if (a.mass != nullptr) {
-                double ms = warp_sum((double)nl.msum);
+                double ms = warp_sum((double)msum);
                 if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);
             }
-            __syncthreads();
-            PlainOut<T, L> out(a, q0);
-            run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
         } else {
             const UpdTile u = upd_tile<T, P>(a, (int)q0);
             if (u.rows) {
