@@ -90,6 +90,7 @@ template <typename T> struct Group {
     const C* tw_row = nullptr;      // stage twiddles: n (short) or 512 (long rows)
     const C* tw_col = nullptr;      // stage twiddles of n1 (long columns)
     const C* tw4 = nullptr;         // exp(-2 pi i m / n)
+    C* tw2 = nullptr;               // exp(-2 pi i a b / n) at a * 512 + b (long NLS signals)
     int B = 1, nblk = 1;
     NLSLaunch nl;                   // NLS launch shapes (fixed at creation)
     // predictor (3-D CH runs): last exact activity, prediction in force, scratch
@@ -365,8 +366,18 @@ static spdba_status group_init_nls(spdba_plan* p, Group<T>& r, long long n, int 
     }
     if ((s = group_buffers<T>(p, r)) != SPDBA_OK) return s;
     if ((s = nls_prepare<T>(n, r.n1, batch, &r.nl)) != SPDBA_OK) return s;
-    if ((s = upload(r, &r.H, half_step_table<T>(n, p->opt.beta2, p->opt.h, p->opt.dt_sample), st)) != SPDBA_OK)
-        return s;
+    std::vector<HPair<T>> H = half_step_table<T>(n, p->opt.beta2, p->opt.h, p->opt.dt_sample);
+    if (r.long_nls) {
+        // the row pass reads H(k1 + n1 m) at k1 * 512 + m: store it in that order
+        std::vector<HPair<T>> HT(H.size());
+        for (long long k1 = 0; k1 < r.n1; ++k1)
+            for (long long m = 0; m < 512; ++m) HT[(size_t)(k1 * 512 + m)] = H[(size_t)(k1 + r.n1 * m)];
+        H.swap(HT);
+        // four-step twiddles W_n^{a b} (a < n1, b < 512) at a * 512 + b
+        if ((s = r.alloc(&r.tw2, sizeof(cx_t<T>) * (size_t)n)) != SPDBA_OK) return s;
+        if ((s = nls_twiddle2<T>(r.tw4, r.tw2, n, st)) != SPDBA_OK) return s;
+    }
+    if ((s = upload(r, &r.H, H, st)) != SPDBA_OK) return s;
     if ((s = upload(r, &r.ntaper, taper_table<T>(r.B), st)) != SPDBA_OK) return s;
     return SPDBA_OK;
 }
@@ -528,12 +539,16 @@ template <typename T> static NLSArgs<T> nls_args(spdba_plan* p, Group<T>& r, cx_
     a.chi = r.chi;
     a.taper = r.ntaper;
     a.tw = r.tw_row;
-    a.tw4 = r.tw4;
+    a.tw4 = r.tw2;
     a.n = r.n;
     a.n1 = r.n1;
     a.batch = batch;
     a.B = r.B;
     a.nblk = r.nblk;
+    a.fd_B.init((uint32_t)r.B);
+    a.mb_shift = 0;
+    if (r.long_nls)
+        while ((512 >> a.mb_shift) > r.nblk) ++a.mb_shift;
     a.dense = dense;
     a.gamma_h = (T)(p->opt.gamma * p->opt.h);
     a.inv_n = (T)(1.0 / (double)r.n);
