@@ -176,6 +176,29 @@ typedef struct spdba_kernel_time {
     double total_ms;
     double bytes;
 } spdba_kernel_time;
+/*
+ * Autotuner (no counterpart in the paper).  Times `steps` steps of the plan
+ * for every candidate launch configuration -- the CH update fused into the
+ * last forward FFT pass or staged as its own kernel (when the plan was created
+ * with fuse_update = 1), and reassessment segments replayed as a CUDA graph or
+ * launched directly (graphs only on a non-legacy stream) -- each from the same
+ * state after one warm-up segment, keeps the fastest for later spdba_step
+ * calls, and restores the plan's fields, block states, statistics and step
+ * count, so that the tuning leaves no trace in the results.  Both update forms
+ * and both launch modes give bit-identical fields.  Needs about one extra copy
+ * of the plan's state in device memory for the duration of the call; not with
+ * an attached predictor (SPDBA_ERR_STATE).  report may be NULL.  Synchronizes.
+ */
+#define SPDBA_TUNE_MAX 8
+typedef struct spdba_tune_report {
+    int32_t n_candidates;
+    int32_t fuse_update[SPDBA_TUNE_MAX];
+    int32_t use_graph[SPDBA_TUNE_MAX];
+    double ms_per_step[SPDBA_TUNE_MAX];
+    int32_t chosen;          /* index of the configuration in force afterwards */
+} spdba_tune_report;
+spdba_status spdba_plan_autotune(spdba_plan* plan, int32_t steps, spdba_tune_report* report);
+
 spdba_status spdba_profile_begin(spdba_plan* plan);
 /* As spdba_profile_begin, but records the kernels of one step in `every`
    (steps whose index is a multiple of `every`), so that the events disturb a

@@ -61,7 +61,12 @@ __device__ __forceinline__ void exact_candidates(const float2 (&v)[K], unsigned 
     while (mask) {
         int i = __ffs(mask) - 1;
         mask &= mask - 1;
-        double e = mode_sq(v[i]);
+        // select v[i] by compares (a dynamic index would move v to local memory)
+        float2 c = v[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k)
+            if (i == k) c = v[k];
+        double e = mode_sq(c);
         mx = fmax(mx, e);
         if (!((dcmask >> i) & 1u)) mxnd = fmax(mxnd, e);
     }
@@ -160,10 +165,135 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
     }
 }
 
+// complex64 fields whose rows are short (n2 / 2 <= 256 mode pairs): one CTA
+// per row of blocks (b0, b1), reading its B0 * B1 whole rows of n2 modes in
+// order (full-row 16-byte loads, the layout HBM streams best).  A thread keeps
+// one mode pair column 2u, so it stays in one block bx = 2u / B2 throughout,
+// shared with the G = B2 / 2 neighbouring lanes of its row.  Per chunk of 16
+// modes a lane forms the FP32 screens p32, the G lanes agree (shuffles) on the
+// running screen max of their block, and only modes whose p32 reaches
+// (1 - 2^-20) of it are evaluated in FP64 -- about one per block and chunk, so
+// the slow FP64 pipe stays idle (a mode below that cannot be the max, as p32
+// is within 2^-22 of the exact value).  The row groups combine through shared
+// memory at the end.
+constexpr int ROWACT_NT = 256;
+__global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, const float2* __restrict__ q,
+                                                                         double* __restrict__ maxsq,
+                                                                         double* __restrict__ gmax) {
+    __shared__ unsigned long long s_mx[ROWACT_NT], s_mxnd[ROWACT_NT];
+    const int n2 = (int)g.n[2], half = n2 >> 1;          // mode pairs per row
+    const int rpi = ROWACT_NT / half;                      // rows per iteration (threads beyond rpi rows idle)
+    const int u = threadIdx.x % half, rho = threadIdx.x / half;
+    const int b0 = blockIdx.x / (int)g.nb[1], b1 = blockIdx.x - b0 * (int)g.nb[1];
+    const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
+    const int G = B2 >> 1;                                 // lanes per block (a power of two <= 32)
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
+    const int rows = B0 * B1;
+    const long long bpr = g.bpr();
+    const long long blk0 = ((long long)b0 * g.nb[1] + b1) * g.nb[2];   // block id of bx = 0
+    const long long run = blk0 / bpr;
+    const long long dc = run * g.fmodes();
+    const long long rowbase = ((long long)b0 * B0 * g.n[1] + (long long)b1 * B1) * n2 + 2 * u;
+    float pm = 0.f, pmnd = 0.f;                            // the block's running screen maxima
+    double mx = 0.0, mxnd = 0.0;
+    constexpr int U = 8;
+    for (int r0 = rho; rho < rpi && r0 < rows; r0 += U * rpi) {
+        float4 w[U];
+        long long idx[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int r = r0 + k * rpi;
+            idx[k] = -1;
+            w[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < rows) {
+                const int l0 = r / B1, l1 = r - l0 * B1;
+                idx[k] = rowbase + ((long long)l0 * g.n[1] + l1) * n2;
+                w[k] = *reinterpret_cast<const float4*>(q + idx[k]);
+            }
+        }
+        float2 v[2 * U];
+        float p32[2 * U];
+        unsigned dcmask = 0;
+        float lmax = 0.f, lmaxnd = 0.f;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            v[2 * k] = make_float2(w[k].x, w[k].y);
+            v[2 * k + 1] = make_float2(w[k].z, w[k].w);
+            if (idx[k] == dc) dcmask |= 1u << (2 * k);
+            if (idx[k] >= 0 && idx[k] + 1 == dc) dcmask |= 1u << (2 * k + 1);
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * U; ++k) {
+            p32[k] = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+            lmax = fmaxf(lmax, p32[k]);
+            if (!((dcmask >> k) & 1u)) lmaxnd = fmaxf(lmaxnd, p32[k]);
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            lmax = fmaxf(lmax, __shfl_xor_sync(gmask, lmax, o));
+            lmaxnd = fmaxf(lmaxnd, __shfl_xor_sync(gmask, lmaxnd, o));
+        }
+        pm = fmaxf(pm, lmax);
+        pmnd = fmaxf(pmnd, lmaxnd);
+        const float cut = pm * (1.0f - 9.5367431640625e-07f);
+        const float cutnd = pmnd * (1.0f - 9.5367431640625e-07f);
+        unsigned mask = 0;
+#pragma unroll
+        for (int k = 0; k < 2 * U; ++k) {
+            const bool isdc = (dcmask >> k) & 1u;
+            if (p32[k] >= cut || (!isdc && p32[k] >= cutnd)) mask |= 1u << k;
+        }
+        exact_candidates<2 * U>(v, mask, dcmask, mx, mxnd);
+    }
+    // combine the G lanes of one block (aligned lane groups), then the row groups
+    unsigned long long bm = dbits(mx), bmnd = dbits(mxnd);
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const unsigned long long om = __shfl_xor_sync(0xffffffffu, bm, o);
+        const unsigned long long omnd = __shfl_xor_sync(0xffffffffu, bmnd, o);
+        bm = om > bm ? om : bm;
+        bmnd = omnd > bmnd ? omnd : bmnd;
+    }
+    s_mx[threadIdx.x] = bm;
+    s_mxnd[threadIdx.x] = bmnd;
+    __syncthreads();
+    const int nbx = n2 / B2;
+    if (threadIdx.x < nbx) {
+        const int ul = threadIdx.x * G;   // first pair column of block bx
+        unsigned long long a = 0, b = 0;
+        for (int rr = 0; rr < rpi && rr < rows; ++rr) {
+            a = s_mx[rr * half + ul] > a ? s_mx[rr * half + ul] : a;
+            b = s_mxnd[rr * half + ul] > b ? s_mxnd[rr * half + ul] : b;
+        }
+        maxsq[blk0 + threadIdx.x] = bitsd(a);
+        atomic_max_nonneg(&gmax[2 * run], bitsd(a));
+        atomic_max_nonneg(&gmax[2 * run + 1], bitsd(b));
+    }
+}
+
+static bool rows_kernel_fits(const Geom& g) {
+    const long long n2 = g.n[2];
+    if (n2 % 2 != 0 || n2 / 2 > ROWACT_NT) return false;
+    const int B2 = g.b[2];
+    if (B2 % 2 != 0) return false;
+    const int G = B2 / 2;                                   // lanes per block
+    if (G > 32 || (G & (G - 1)) != 0) return false;
+    // one CTA per row of blocks: only where that gives a few waves of CTAs
+    if (g.nb[0] * g.nb[1] < 608 || g.nb[0] * g.nb[1] >= 0x7fffffffLL) return false;
+    return true;
+}
+
 template <typename T>
 spdba_status launch_block_activity(const Geom& g, const cx_t<T>* q, double* maxsq, double* sumsq, double* gmax,
                                    cudaStream_t st) {
     long long nb = g.blocks();
+    if constexpr (sizeof(cx_t<T>) == 8) {
+        if (!sumsq && rows_kernel_fits(g)) {
+            block_activity_rows_kernel<<<(unsigned)(g.nb[0] * g.nb[1]), ROWACT_NT, 0, st>>>(
+                g, reinterpret_cast<const float2*>(q), maxsq, gmax);
+            SPDBA_CUDA(cudaGetLastError());
+            return SPDBA_OK;
+        }
+    }
     unsigned grid = (unsigned)((nb + 7) / 8);
     if (sumsq) block_activity_kernel<T, true><<<grid, 256, 0, st>>>(g, q, maxsq, sumsq, gmax);
     else block_activity_kernel<T, false><<<grid, 256, 0, st>>>(g, q, maxsq, nullptr, gmax);

@@ -451,6 +451,34 @@ __device__ __forceinline__ void run_stages_out(cx_t<T>* sm, const cx_t<T>* tw, O
     run_stages_out_list<T, L, P, NT, SIGN, LY, OUT>(sm, tw, out, typename Radices<L>::type{});
 }
 
+// Last-stage outputs passed through an elementwise step and written back to
+// shared memory in natural order.
+template <typename T, int L, class LY, class MID> struct MidOut {
+    using C = cx_t<T>;
+    static constexpr bool SYNC = true;
+    C* sm;
+    MID& mid;
+    __device__ __forceinline__ void pre() {}
+    __device__ __forceinline__ void begin(int, int, int) {}
+    template <int R> __device__ __forceinline__ void emit(int, int p, int j, C (&v)[R]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int m = j + r * (L / R);
+            sm[LY::idx(p, m)] = mid(p, m, v[r]);
+        }
+    }
+};
+
+// c = Re(x) / N, g = c^3 - c (the CH nonlinearity), with the sum of c kept.
+template <typename T> struct ChNlMid {
+    T scale, msum;
+    __device__ __forceinline__ cx_t<T> operator()(int, int, cx_t<T> x) {
+        const T c = x.x * scale;
+        msum += c;
+        return mk<cx_t<T>>(c * c * c - c, (T)0);
+    }
+};
+
 // Stages I .. E-1 of a length-L transform (in shared memory).
 template <typename T, int L, int P, int NT, int SIGN, class LY, int I, int E>
 __device__ __forceinline__ void run_stage_range(cx_t<T>* sm, const cx_t<T>* tw) {
@@ -473,16 +501,16 @@ template <typename T, int L, int R, class LY> struct FirstStageOut {
     }
 };
 
-// The CH nonlinearity between the inverse and the forward transform of one
-// pencil when the inverse's last radix equals the forward's first (R): the
-// inverse's last butterfly j yields exactly the elements j + r L/R that the
-// forward's first butterfly j reads, so both butterflies and c = Re(.)/N,
-// g = c^3 - c run in registers.  NS = the inverse's last-stage span (L / R).
-template <typename T, int L, int P, int NT, int NS, int R, class LY, class OUT>
-__device__ __forceinline__ void nl_middle_stage(cx_t<T>* sm, const cx_t<T>* __restrict__ tw, T nl_scale, T& msum,
-                                                OUT& out) {
+// The last stage of one transform (sign SA, span NS = L / R) and the first
+// stage of the next (sign SB) of the same pencil, when both have radix R: the
+// first's butterfly j yields exactly the elements j + r L/R (natural order)
+// that the second's butterfly j reads, so both butterflies and an elementwise
+// step between them (mid(p, m, x) for element m) run in registers.  The
+// second stage's outputs go to `out` (j R + r for a stage that others follow).
+template <typename T, int L, int P, int NT, int SA, int SB, int NS, int R, class LY, class MID, class OUT>
+__device__ __forceinline__ void fused_mid_stage(cx_t<T>* sm, const cx_t<T>* __restrict__ tw, MID& mid, OUT& out) {
     using C = cx_t<T>;
-    static_assert(NS * R == L, "the middle stage closes the inverse transform");
+    static_assert(NS * R == L, "the first of the two stages closes its transform");
     constexpr int Q = L / R;
     constexpr int NB = P * Q;
     constexpr int PER = (NB + NT - 1) / NT;
@@ -501,18 +529,14 @@ __device__ __forceinline__ void nl_middle_stage(cx_t<T>* sm, const cx_t<T>* __re
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
                     C w = __ldg(tw + r * j);
-                    w.y = -w.y;
+                    if constexpr (SA > 0) w.y = -w.y;
                     v[k][r] = cmul(v[k][r], w);
                 }
             }
-            Dft<R, +1, C>::run(v[k]);
+            Dft<R, SA, C>::run(v[k]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const T c = v[k][r].x * nl_scale;
-                msum += c;
-                v[k][r] = mk<C>(c * c * c - c, (T)0);
-            }
-            Dft<R, -1, C>::run(v[k]);
+            for (int r = 0; r < R; ++r) v[k][r] = mid(p, j + r * Q, v[k][r]);
+            Dft<R, SB, C>::run(v[k]);
         }
     }
     if constexpr (OUT::SYNC) __syncthreads();
@@ -525,6 +549,33 @@ __device__ __forceinline__ void nl_middle_stage(cx_t<T>* sm, const cx_t<T>* __re
             else { p = b / Q; j = b % Q; }
             out.emit(k, p, j, v[k]);
         }
+    }
+}
+
+// Two transforms of the tile with an elementwise step between them: SA then
+// SB, the second's last stage emitting through `out`.  When the first's last
+// radix equals the second's first, the two meeting stages run fused in
+// registers (fused_mid_stage); otherwise `mid` rides in the first's last stage.
+template <typename T, int L, int P, int NT, int SA, int SB, class LY, class MID, class OUT>
+__device__ __forceinline__ void transform_pair(cx_t<T>* sm, const cx_t<T>* tw, MID& mid, OUT& out) {
+    constexpr int NST = NSTAGES<L>::value;
+    constexpr int R0 = radix_at<L>(0), RL = radix_at<L>(NST - 1);
+    if constexpr (R0 == RL) {
+        run_stage_range<T, L, P, NT, SA, LY, 0, NST - 1>(sm, tw);
+        if constexpr (NST == 1) {
+            fused_mid_stage<T, L, P, NT, SA, SB, 1, R0, LY>(sm, tw, mid, out);
+        } else {
+            FirstStageOut<T, L, R0, LY> fo{sm};
+            fused_mid_stage<T, L, P, NT, SA, SB, L / R0, R0, LY>(sm, tw, mid, fo);
+            __syncthreads();
+            run_stage_range<T, L, P, NT, SB, LY, 1, NST - 1>(sm, tw);
+            stockham_stage_out<T, L, P, NT, SB, ns_at<L>(NST - 1), RL, LY>(sm, tw, out);
+        }
+    } else {
+        MidOut<T, L, LY, MID> mo{sm, mid};
+        run_stages_out<T, L, P, NT, SA, LY>(sm, tw, mo);
+        __syncthreads();
+        run_stages_out<T, L, P, NT, SB, LY>(sm, tw, out);
     }
 }
 
@@ -579,25 +630,6 @@ template <typename T, int L> struct PlainOut {
     }
 };
 
-// CH nonlinearity on the inverse transform's outputs: c = Re(.) / N (its sum
-// accumulated for the mass), g = c^3 - c written back in natural order.
-template <typename T, int L, class LY> struct NlOut {
-    using C = cx_t<T>;
-    static constexpr bool SYNC = true;
-    C* sm;
-    T scale;
-    T msum;
-    __device__ __forceinline__ void pre() {}
-    __device__ __forceinline__ void begin(int, int, int) {}
-    template <int R> __device__ __forceinline__ void emit(int, int p, int j, C (&v)[R]) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T c = v[r].x * scale;
-            msum += c;
-            sm[LY::idx(p, j + r * (L / R))] = mk<C>(c * c * c - c, (T)0);
-        }
-    }
-};
 
 // Four-step twiddle: element (pencil i, output index j) *= W_N^{i j}.
 template <typename T, int L, int P, int NT, int SIGN, class LY>
@@ -984,33 +1016,11 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
                 run_stages_out<T, L, P, NT, SIGN, LY>(sm, a.tw, out);
             }
         } else if constexpr (MODE == PASS_CH_NL) {
-            constexpr int NST = NSTAGES<L>::value;
-            T msum = 0;
-            if constexpr (radix_at<L>(0) == radix_at<L>(NST - 1)) {
-                // inverse stages but the last; last inverse + nonlinearity + first forward
-                // butterflies in registers; remaining forward stages, the last storing
-                constexpr int R = radix_at<L>(0);
-                run_stage_range<T, L, P, NT, +1, LY, 0, NST - 1>(sm, a.tw);
-                if constexpr (NST == 1) {
-                    PlainOut<T, L> out(a, q0);
-                    nl_middle_stage<T, L, P, NT, 1, R, LY>(sm, a.tw, a.nl_scale, msum, out);
-                } else {
-                    FirstStageOut<T, L, R, LY> fo{sm};
-                    nl_middle_stage<T, L, P, NT, L / R, R, LY>(sm, a.tw, a.nl_scale, msum, fo);
-                    __syncthreads();
-                    run_stage_range<T, L, P, NT, -1, LY, 1, NST - 1>(sm, a.tw);
-                    PlainOut<T, L> out(a, q0);
-                    stockham_stage_out<T, L, P, NT, -1, ns_at<L>(NST - 1), radix_at<L>(NST - 1), LY>(sm, a.tw, out);
-                }
-            } else {
-                // inverse transform with the nonlinearity in its last stage, then forward
-                NlOut<T, L, LY> nl{sm, a.nl_scale, (T)0};
-                run_stages_out<T, L, P, NT, +1, LY>(sm, a.tw, nl);
-                msum = nl.msum;
-                __syncthreads();
-                PlainOut<T, L> out(a, q0);
-                run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
-            }
+            // inverse transform, the nonlinearity, forward transform (last stage storing)
+            ChNlMid<T> mid{a.nl_scale, (T)0};
+            PlainOut<T, L> out(a, q0);
+            transform_pair<T, L, P, NT, +1, -1, LY>(sm, a.tw, mid, out);
+            const T msum = mid.msum;
             if (a.mass != nullptr) {
                 double ms = warp_sum((double)msum);
                 if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);

@@ -82,7 +82,9 @@ template <typename T> struct Group {
     std::vector<Pass<T>> pre_inv;   // inverse passes before the fused one (first reads c_hat)
     Pass<T> fused;                  // inverse + nonlinearity + forward along the fast axis
     std::vector<Pass<T>> pre_fwd;   // remaining forward passes
-    bool fused_update = false;      // the last forward pass carries the update (pre_fwd.back())
+    bool fused_update = false;      // the last forward pass carries the update (upd_pass)
+    bool has_fused = false;         // upd_pass exists (else only the staged form)
+    Pass<T> upd_pass;               // forward pass of the first axis with the update fused
     FftEngine<T> fft1;              // one run's transforms for set/get_field
     // NLS
     HPair<T>* H = nullptr;
@@ -165,6 +167,10 @@ struct spdba_plan {
     int horizon = 0, judge_every = 0;
     float prob_thr = 0.5f;
     long long seg_launches = 0;
+    // groups step concurrently on their own streams, forked from and joined to st
+    std::vector<cudaStream_t> gstreams;
+    std::vector<cudaEvent_t> gevents;
+    cudaEvent_t fork_ev = nullptr;
     int nruns() const { return (int)runs.size(); }
 };
 
@@ -316,13 +322,15 @@ static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const in
                 f.fd_b2.init((uint32_t)r.g.b[2]);
                 f.fd_b1.init((uint32_t)r.g.b[1]);
                 f.fd_n2.init((uint32_t)r.g.n[2]);
+                r.upd_pass = ps;
+                r.has_fused = true;
                 r.fused_update = true;
             } else if (sf != SPDBA_ERR_UNSUPPORTED) {
                 return sf;
             }
         }
-        if (sf != SPDBA_OK && (s = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_PLAIN, tw, st)) != SPDBA_OK)
-            return s;
+        // the plain pass is kept in every case: the staged form uses it
+        if ((s = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
         r.pre_fwd.push_back(ps);
     }
     return SPDBA_OK;
@@ -494,7 +502,7 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
         const bool last_fused = r.fused_update && k + 1 == r.pre_fwd.size();
         if (last_fused) {
             // forward transform of the first axis + update; traffic depends on the states
-            Pass<T> ps = r.pre_fwd[k];
+            Pass<T> ps = r.upd_pass;
             ps.p.fu.dense = dense;
             ProfScope pr(p, K_FFT_UPDATE, pass_bytes + sizeof(cx_t<T>) * (double)(r.batch * r.n));
             if ((s = launch_pass<T>(ps, r.work, r.work, st)) != SPDBA_OK) return s;
@@ -621,8 +629,55 @@ template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T
     return SPDBA_OK;
 }
 
+template <typename T> static spdba_status group_steps(spdba_plan* p, Group<T>& g, int64_t n) {
+    if (p->opt.model == SPDBA_MODEL_NLS) return group_nls_steps<T>(p, g, n);
+    for (int64_t i = 0; i < n; ++i) {
+        spdba_status s = group_ch_step<T>(p, g);
+        if (s != SPDBA_OK) return s;
+    }
+    return SPDBA_OK;
+}
+
+// Streams and events for running the groups concurrently (created once).
+static spdba_status ensure_group_streams(spdba_plan* p, size_t ngroups) {
+    if (p->gstreams.size() >= ngroups) return SPDBA_OK;
+    if (!p->fork_ev) SPDBA_CUDA(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
+    while (p->gstreams.size() < ngroups) {
+        cudaStream_t s = nullptr;
+        SPDBA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        p->gstreams.push_back(s);
+        cudaEvent_t e = nullptr;
+        SPDBA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->gevents.push_back(e);
+    }
+    return SPDBA_OK;
+}
+
 template <typename T> static spdba_status direct_steps(spdba_plan* p, int64_t n) {
     auto& gs = groups<T>(p);
+    if (gs.size() > 1 && !p->prof) {
+        // groups share nothing during steps: each runs its n steps on its own
+        // stream, forked from the plan's stream and joined back to it (inside a
+        // graph capture the forked streams join the capture)
+        spdba_status s = ensure_group_streams(p, gs.size());
+        if (s != SPDBA_OK) return s;
+        const cudaStream_t main = p->st;
+        SPDBA_CUDA(cudaEventRecord(p->fork_ev, main));
+        for (size_t i = 0; i < gs.size() && s == SPDBA_OK; ++i) {
+            SPDBA_CUDA(cudaStreamWaitEvent(p->gstreams[i], p->fork_ev, 0));
+            p->st = p->gstreams[i];
+            s = group_steps<T>(p, *gs[i], n);
+            p->st = main;
+            cudaError_t e = cudaEventRecord(p->gevents[i], p->gstreams[i]);
+            if (s == SPDBA_OK && e != cudaSuccess) s = cuda_fail(e, "cudaEventRecord(group)");
+            if (s == SPDBA_OK) {
+                e = cudaStreamWaitEvent(main, p->gevents[i], 0);
+                if (e != cudaSuccess) s = cuda_fail(e, "cudaStreamWaitEvent(join)");
+            }
+        }
+        p->st = main;
+        return s;
+    }
     if (p->opt.model == SPDBA_MODEL_NLS) {
         for (auto& g : gs) {
             spdba_status s = group_nls_steps<T>(p, *g, n);
@@ -925,6 +980,12 @@ extern "C" void spdba_plan_destroy(spdba_plan* p) {
     p->tw64.release();
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (p->seg_exec) cudaGraphExecDestroy(p->seg_exec);
+    for (cudaStream_t gs : p->gstreams) {
+        cudaStreamSynchronize(gs);
+        cudaStreamDestroy(gs);
+    }
+    for (cudaEvent_t e : p->gevents) cudaEventDestroy(e);
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     delete p;
 }
 
@@ -947,6 +1008,134 @@ extern "C" spdba_status spdba_step(spdba_plan* p, int64_t n) {
     PLAN_CHECK(p);
     if (n < 0) return fail(SPDBA_ERR_ARG, "negative step count");
     spdba_status s = p->precision == SPDBA_C64 ? plan_step<float>(p, n) : plan_step<double>(p, n);
+    return latch(p, s);
+}
+
+// ------------------------------------------------------------------ autotuner
+// Device state of a group copied aside, so that trial steps can be undone.
+struct GroupSnap {
+    std::vector<std::pair<void*, size_t>> bufs;   // (source, bytes)
+    std::vector<void*> copies;
+    int64_t step = 0;
+    bool assessed = false;
+    void release() {
+        for (void* q : copies) cudaFree(q);
+        copies.clear();
+    }
+};
+
+template <typename T> static spdba_status snap_take(spdba_plan* p, Group<T>& r, GroupSnap& sn) {
+    const long long nb = r.g.blocks();
+    sn.bufs = {{r.c_hat, sizeof(cx_t<T>) * (size_t)(r.batch * r.n)},
+               {r.stats, sizeof(DevStats) * (size_t)r.batch},
+               {r.maxsq, sizeof(double) * (size_t)nb},
+               {r.sumsq, sizeof(double) * (size_t)nb},
+               {r.gmax, sizeof(double) * 2 * (size_t)r.batch},
+               {r.tau, sizeof(double) * (size_t)r.batch},
+               {r.active, (size_t)nb},
+               {r.states, (size_t)nb},
+               {r.chi, (size_t)nb},
+               {r.list, sizeof(int32_t) * (size_t)nb},
+               {r.count, sizeof(int32_t) * 2}};
+    for (auto& b : sn.bufs) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, b.second);
+        if (e != cudaSuccess) { sn.release(); return cuda_fail(e, "cudaMalloc(autotune snapshot)"); }
+        sn.copies.push_back(q);
+        SPDBA_CUDA(cudaMemcpyAsync(q, b.first, b.second, cudaMemcpyDeviceToDevice, p->st));
+    }
+    sn.step = r.step;
+    sn.assessed = r.assessed;
+    return SPDBA_OK;
+}
+
+template <typename T> static spdba_status snap_restore(spdba_plan* p, Group<T>& r, const GroupSnap& sn) {
+    for (size_t i = 0; i < sn.bufs.size(); ++i)
+        SPDBA_CUDA(cudaMemcpyAsync(sn.bufs[i].first, sn.copies[i], sn.bufs[i].second, cudaMemcpyDeviceToDevice, p->st));
+    r.step = sn.step;
+    r.assessed = sn.assessed;
+    return SPDBA_OK;
+}
+
+template <typename T> static void apply_config(spdba_plan* p, int fuse, int graph) {
+    for (auto& g : groups<T>(p)) g->fused_update = fuse && g->has_fused;
+    p->opt.use_graph = graph;
+    if (p->seg_exec) {
+        cudaGraphExecDestroy(p->seg_exec);
+        p->seg_exec = nullptr;
+    }
+}
+
+// Times `steps` steps (after a warm-up segment that also captures a graph)
+// for every candidate (update form x graph replay) from the same state, then
+// keeps the fastest and restores the state.
+template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t steps, spdba_tune_report* rep) {
+    auto& gs = groups<T>(p);
+    bool any_fused = false;
+    for (auto& g : gs) any_fused |= g->has_fused;
+    std::vector<std::pair<int, int>> cand;
+    for (int f : {1, 0}) {
+        if (f && !any_fused) continue;
+        for (int gr : {1, 0}) {
+            if (gr && p->st == 0) continue;   // graphs need a non-legacy stream
+            cand.push_back({f, gr});
+        }
+    }
+    if ((int)cand.size() > SPDBA_TUNE_MAX) cand.resize(SPDBA_TUNE_MAX);
+    std::vector<GroupSnap> snaps(gs.size());
+    spdba_status s = SPDBA_OK;
+    for (size_t i = 0; i < gs.size() && s == SPDBA_OK; ++i) s = snap_take<T>(p, *gs[i], snaps[i]);
+    const long long launches0 = p->launches;
+    const int R = p->reassess;
+    std::vector<double> ms(cand.size(), 0.0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s == SPDBA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        s = fail(SPDBA_ERR_CUDA, "autotune: cudaEventCreate failed");
+    for (size_t c = 0; c < cand.size() && s == SPDBA_OK; ++c) {
+        apply_config<T>(p, cand[c].first, cand[c].second);
+        if ((s = plan_step<T>(p, R)) != SPDBA_OK) break;   // warm-up (graph capture)
+        for (size_t i = 0; i < gs.size() && s == SPDBA_OK; ++i) s = snap_restore<T>(p, *gs[i], snaps[i]);
+        if (s != SPDBA_OK) break;
+        cudaEventRecord(e0, p->st);
+        if ((s = plan_step<T>(p, steps)) != SPDBA_OK) break;
+        cudaEventRecord(e1, p->st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { s = cuda_fail(e, "autotune sync"); break; }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[c] = t / (double)steps;
+        for (size_t i = 0; i < gs.size() && s == SPDBA_OK; ++i) s = snap_restore<T>(p, *gs[i], snaps[i]);
+    }
+    size_t best = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+        if (ms[c] < ms[best]) best = c;
+    if (s == SPDBA_OK && !cand.empty()) apply_config<T>(p, cand[best].first, cand[best].second);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaError_t e = cudaStreamSynchronize(p->st);
+    for (auto& sn : snaps) sn.release();
+    p->launches = launches0;
+    if (s != SPDBA_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune sync");
+    if (rep) {
+        memset(rep, 0, sizeof *rep);
+        rep->n_candidates = (int32_t)cand.size();
+        for (size_t c = 0; c < cand.size(); ++c) {
+            rep->fuse_update[c] = cand[c].first;
+            rep->use_graph[c] = cand[c].second;
+            rep->ms_per_step[c] = ms[c];
+        }
+        rep->chosen = (int32_t)best;
+    }
+    return SPDBA_OK;
+}
+
+extern "C" spdba_status spdba_plan_autotune(spdba_plan* p, int32_t steps, spdba_tune_report* report) {
+    PLAN_CHECK(p);
+    if (steps < 1) return fail(SPDBA_ERR_ARG, "spdba_plan_autotune: steps must be >= 1");
+    if (p->pred) return fail(SPDBA_ERR_STATE, "spdba_plan_autotune: detach the predictor first");
+    if (p->prof) return fail(SPDBA_ERR_STATE, "spdba_plan_autotune: a profile is open");
+    spdba_status s = p->precision == SPDBA_C64 ? autotune_t<float>(p, steps, report) : autotune_t<double>(p, steps, report);
     return latch(p, s);
 }
 

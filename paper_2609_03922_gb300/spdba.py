@@ -39,6 +39,11 @@ class spdba_stats(ctypes.Structure):
                 ("predictions", ctypes.c_int64), ("missed_blocks", ctypes.c_int64)]
 
 
+class spdba_tune_report(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("fuse_update", ctypes.c_int32 * 8),
+                ("use_graph", ctypes.c_int32 * 8), ("ms_per_step", ctypes.c_double * 8), ("chosen", ctypes.c_int32)]
+
+
 class spdba_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -66,6 +71,7 @@ SIGNATURES = {
     "spdba_sync": (_S, [_P]),
     "spdba_get_activity": (_S, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "spdba_plan_attach_predictor": (_S, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
+    "spdba_plan_autotune": (_S, [_P, ctypes.c_int32, ctypes.POINTER(spdba_tune_report)]),
     "spdba_profile_begin": (_S, [_P]),
     "spdba_profile_begin_sampled": (_S, [_P, ctypes.c_int32]),
     "spdba_profile_end": (_S, [_P, ctypes.POINTER(spdba_kernel_time), ctypes.c_int32, _I32P,
@@ -241,6 +247,15 @@ class Plan:
         out = np.empty(shape, dtype=np.uint8)
         check(lib().spdba_get_mask(self._p, run, out.ctypes.data, out.size))
         return out
+
+    def autotune(self, steps=20):
+        """Pick the fastest launch configuration (spdba_plan_autotune); returns the
+        candidates with their ms per step and the chosen index."""
+        rep = spdba_tune_report()
+        check(lib().spdba_plan_autotune(self._p, int(steps), ctypes.byref(rep)))
+        cands = [{"fuse_update": int(rep.fuse_update[i]), "use_graph": int(rep.use_graph[i]),
+                  "ms_per_step": float(rep.ms_per_step[i])} for i in range(rep.n_candidates)]
+        return {"candidates": cands, "chosen": int(rep.chosen)}
 
     def profile_begin(self, every=1):
         """Record kernel events of every step, or of one step in `every`."""

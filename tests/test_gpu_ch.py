@@ -219,3 +219,37 @@ def test_graph_replay_equals_direct_launches(model):
         assert np.array_equal(sa, sb)
         assert np.array_equal(ma, mb)
         assert ta["step"] == tb["step"] == 22 and ta["assessments"] == tb["assessments"]
+
+
+def test_autotune_restores_state_and_keeps_results():
+    """The autotuner tries every launch configuration from the same state and
+    leaves no trace: after it, the plan's step count, fields, masks and
+    statistics evolve exactly as in an untuned plan."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    dims = [(128, 128), (192, 192)]
+    inputs = [W.ch_initial_condition(d, mean=0.05, seed=W.BASE_SEED + 80 + i).astype(np.float32)
+              for i, d in enumerate(dims)]
+    outs = []
+    for tune in (True, False):
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            plan = spdba.Plan(None, (16, 16), threshold=1e-3, reassess=5, batch_dims=dims, precision=0)
+            for r, x in enumerate(inputs):
+                plan.set_field(x, run=r)
+            if tune:
+                rep = plan.autotune(10)
+                assert rep["chosen"] in range(len(rep["candidates"]))
+                assert {(c["fuse_update"], c["use_graph"]) for c in rep["candidates"]} == {(1, 1), (1, 0), (0, 1), (0, 0)}
+                assert all(c["ms_per_step"] > 0 for c in rep["candidates"])
+                assert plan.get_stats(run=0)["step"] == 0
+            plan.step(23)
+            res = [(plan.get_spectrum(run=r), plan.get_mask(run=r), plan.get_stats(run=r)) for r in range(len(dims))]
+            plan.close()
+        side.synchronize()
+        outs.append(res)
+    for (sa, ma, ta), (sb, mb, tb) in zip(*outs):
+        assert np.array_equal(sa, sb)
+        assert np.array_equal(ma, mb)
+        assert ta["step"] == tb["step"] == 23 and ta["assessments"] == tb["assessments"]
+        assert ta["active_ratio_sum"] == tb["active_ratio_sum"]
