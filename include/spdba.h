@@ -74,6 +74,10 @@ typedef struct spdba_options {
     int32_t use_graph;      /* 1: replay captured CUDA graphs for runs of steps          */
     int32_t fuse_update;    /* CH: 1 = apply the update inside the last forward FFT pass;
                                0 = separate update kernel over the block list (staged)  */
+    int32_t half_spectrum;  /* 3-D CH, complex64: 1 = run the transforms on x frequencies
+                               0 .. N2/2 of the Hermitian part of c_hat (c = Re IFFT(c_hat)
+                               is its inverse), 0 = full complex transforms; ignored where
+                               no half-spectrum kernels exist for the shape                */
     double dt, kappa, dx;   /* Cahn-Hilliard: time step, gradient coefficient, spacing  */
     double beta2, gamma, h, dt_sample; /* NLS: ps^2/km, 1/(W km), km step, ps sample     */
     void* stream;           /* cudaStream_t the plan enqueues on                         */
@@ -180,12 +184,15 @@ typedef struct spdba_kernel_time {
  * Autotuner (no counterpart in the paper).  Times `steps` steps of the plan
  * for every candidate launch configuration -- the CH update fused into the
  * last forward FFT pass or staged as its own kernel (when the plan was created
- * with fuse_update = 1), and reassessment segments replayed as a CUDA graph or
+ * with fuse_update = 1), the 3-D transforms on the Hermitian half spectrum or
+ * on the full one (when created with half_spectrum = 1 and the shape has half-
+ * spectrum kernels), and reassessment segments replayed as a CUDA graph or
  * launched directly (graphs only on a non-legacy stream) -- each from the same
  * state after one warm-up segment, keeps the fastest for later spdba_step
  * calls, and restores the plan's fields, block states, statistics and step
  * count, so that the tuning leaves no trace in the results.  Both update forms
- * and both launch modes give bit-identical fields.  Needs about one extra copy
+ * and both launch modes give bit-identical fields; the two transform forms
+ * differ by rounding only.  Needs about one extra copy
  * of the plan's state in device memory for the duration of the call; not with
  * an attached predictor (SPDBA_ERR_STATE).  report may be NULL.  Synchronizes.
  */
@@ -194,6 +201,7 @@ typedef struct spdba_tune_report {
     int32_t n_candidates;
     int32_t fuse_update[SPDBA_TUNE_MAX];
     int32_t use_graph[SPDBA_TUNE_MAX];
+    int32_t half_spectrum[SPDBA_TUNE_MAX];
     double ms_per_step[SPDBA_TUNE_MAX];
     int32_t chosen;          /* index of the configuration in force afterwards */
 } spdba_tune_report;

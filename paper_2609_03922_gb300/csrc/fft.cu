@@ -6,6 +6,8 @@
 #include <mutex>
 #include <set>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "kernel_table.h"
 
@@ -254,6 +256,55 @@ template spdba_status make_pass<float>(Pass<float>*, int64_t, int, int, long lon
 template spdba_status make_pass<double>(Pass<double>*, int64_t, int, int, long long, long long, long long, long long,
                                         long long, long long, long long, long long, TwiddleCache<double>&,
                                         cudaStream_t);
+// Half-spectrum passes of a 3-D complex64 field (see fft_half.cuh).
+spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, TwiddleCache<float>& tw, cudaStream_t st) {
+    const bool rows = mode == PASS_NL_HALF;
+    const int64_t L = rows ? hg.N2 / 2 : hg.N0;
+    KernelInfo ki;
+    if (!get_half_kernel(L, mode, hg.NHP, &ki))
+        return fail(SPDBA_ERR_UNSUPPORTED, "no half-spectrum kernel for length %lld (mode %d)", (long long)L, mode);
+    Pass<float> ps;
+    PassParams<float>& a = ps.p;
+    if (rows) {
+        a.O = hg.N0;
+        a.I = hg.N1;
+    } else {
+        a.O = 1;
+        a.I = (long long)hg.N1 * (mode == PASS_HERM_INV ? hg.NHP : hg.N2);
+        a.osO = 0;
+        a.osI = 1;
+        a.osJ = a.I;
+    }
+    if ((a.O * a.I) % ki.P != 0) return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum tiles do not divide the pencils");
+    spdba_status s = ensure_smem_attr(ki.func, ki.smem, true);
+    if (s != SPDBA_OK) return s;
+    int per_sm = 0, nsm = 0, dev = 0;
+    SPDBA_CUDA(cudaGetDevice(&dev));
+    SPDBA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SPDBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.func, ki.NT, ki.smem));
+    if (per_sm < 1) return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum kernel does not fit an SM");
+    const long long ntiles = a.O * a.I / ki.P;
+    ps.grid = std::min<long long>(ntiles, (long long)per_sm * nsm);
+    ps.func = ki.func;
+    ps.nt = ki.NT;
+    ps.P = ki.P;
+    ps.smem = ki.smem;
+    s = SPDBA_OK;
+    if (!(a.tw = tw.get(L, st, &s))) return s;
+    a.tw4 = nullptr;
+    if (rows && !(a.tw4 = tw.get(hg.N2, st, &s))) return s;
+    a.n4 = 1;
+    a.scale = 1.f;
+    a.generic = 0;
+    a.nl_scale = (float)(1.0 / ((double)hg.N0 * hg.N1 * hg.N2));
+    a.mass = nullptr;
+    a.mass_ppr = (long long)hg.N0 * hg.N1;
+    a.fd_I.init((uint32_t)a.I);
+    a.hg = hg;
+    *out = ps;
+    return SPDBA_OK;
+}
+
 template spdba_status launch_pass<float>(const Pass<float>&, const void*, void*, cudaStream_t);
 template spdba_status launch_pass<double>(const Pass<double>&, const void*, void*, cudaStream_t);
 template spdba_status make_axis_pass<float>(Pass<float>*, int, const int64_t*, int64_t, int, int, int,

@@ -102,6 +102,13 @@ template <typename T> struct CHFuse {
     FastDiv fd_bp, fd_b2, fd_b1, fd_n2;
 };
 
+// Half-spectrum geometry of a 3-D field N0 x N1 x N2 (N2 even): the half array
+// holds x frequencies 0 .. N2/2 in rows of NHP >= N2/2 + 1 entries (the rest 0).
+struct HalfGeo {
+    int N0 = 1, N1 = 1, N2 = 2, NHP = 2;
+    FastDiv fd_N2, fd_NHP;
+};
+
 template <typename T> struct PassParams {
     const cx_t<T>* in;
     cx_t<T>* out;
@@ -120,6 +127,7 @@ template <typename T> struct PassParams {
     long long mass_ppr;                   // pencils per field
     CHFuse<T> fu;                         // PASS_CH_UPDATE only
     FastDiv fd_I;                         // division by I (pipelined kernel, O * I < 2^31)
+    HalfGeo hg;                           // half-spectrum passes only
 };
 
 // Address of element (p, j) of the tile starting at pencil q0.
@@ -252,6 +260,39 @@ __device__ __forceinline__ void issue_tile(cx_t<T>* sm, const PassParams<T>& a, 
             else { p = u / L; j = u % L; }
             cp_async16(sm + LY::idx(p, j), base + (long long)p * a.isI + (long long)j * a.isJ);
         }
+    }
+}
+
+// Asynchronous load of a z-pencil tile of a 3-D field from its half array
+// (PASS_MIRROR / PASS_UPD_HALF): pencil (ky, kx) of the full field is the half
+// array's pencil (ky, kx) for kx <= N2/2 and, for kx > N2/2, the conjugate
+// mirror ((-ky) mod N1, N2 - kx) (the transform of a real field along y and x
+// satisfies D(z, ky, kx) = conj(D(z, -ky, -kx))); the caller applies the
+// conjugation and the index reversal to the transform's outputs.
+template <typename T, int L, int P, int NT, class LY>
+__device__ __forceinline__ void issue_tile_half(cx_t<T>* sm, const PassParams<T>& a, long long q0) {
+    using C = cx_t<T>;
+    const HalfGeo& h = a.hg;
+    const int M = h.N2 >> 1;
+    static_assert(NT % P == 0, "each thread keeps one pencil");
+    const int p = (int)(threadIdx.x % P);
+    const int q = (int)q0 + p;                       // full pencil index ky * N2 + kx (one field)
+    const int ky = (int)h.fd_N2.div((uint32_t)q), kx = q - ky * h.N2;
+    const bool mir = kx > M;
+    const int sy = mir ? (ky == 0 ? 0 : h.N1 - ky) : ky;
+    const int sx = mir ? h.N2 - kx : kx;
+    const C* src = a.in + ((long long)sy * h.NHP + sx);
+    const long long zs = (long long)h.N1 * h.NHP;   // z stride of the half array
+    // direct pencil pairs (p, p + 1), p even, are one 16-byte copy by pencil p
+    // (kx and NHP even keep it aligned; P even keeps kx's parity that of p)
+    const bool pair = !mir && (p & 1) == 0 && kx + 1 <= M;
+    const bool covered = !mir && (p & 1) == 1;        // kx odd <= M: copied with pencil p - 1
+    if (pair) {
+#pragma unroll 4
+        for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) cp_async16(sm + LY::idx(p, j), src + j * zs);
+    } else if (!covered) {
+#pragma unroll 4
+        for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) cp_async8(sm + LY::idx(p, j), src + j * zs);
     }
 }
 
@@ -488,6 +529,40 @@ __device__ __forceinline__ void run_stage_range(cx_t<T>* sm, const cx_t<T>* tw) 
     }
 }
 
+// Plain store of a z-transform from the half array (PASS_MIRROR): outputs of
+// a mirrored pencil go, conjugated, to frequency -m.
+template <typename T, int L, int P> struct MirrorPlainOut {
+    using C = cx_t<T>;
+    static constexpr bool SYNC = false;
+    C* po;        // this thread's pencil, output element 0
+    int osJ;
+    bool mir;
+    __device__ __forceinline__ MirrorPlainOut(const PassParams<T>& a, long long q0) {
+        const int p = (int)(threadIdx.x % P);
+        const long long o = a.fd_I.div((uint32_t)q0);
+        po = a.out + (o * a.osO + (q0 - o * a.I + p) * a.osI);
+        osJ = (int)a.osJ;
+        const int q = (int)(q0 - o * a.I) + p;
+        const int ky = (int)a.hg.fd_N2.div((uint32_t)q);
+        mir = q - ky * a.hg.N2 > (a.hg.N2 >> 1);
+    }
+    __device__ __forceinline__ void pre() {}
+    __device__ __forceinline__ void begin(int, int, int) {}
+    template <int R> __device__ __forceinline__ void emit(int, int, int j, C (&v)[R]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int m = j + r * (L / R);
+            C x = v[r];
+            int kz = m;
+            if (mir) {
+                x.y = -x.y;
+                kz = m == 0 ? 0 : L - m;
+            }
+            po[kz * osJ] = x;
+        }
+    }
+};
+
 // Outputs of a first stage (NS = 1): butterfly j writes j R + r.
 template <typename T, int L, int R, class LY> struct FirstStageOut {
     using C = cx_t<T>;
@@ -654,7 +729,14 @@ enum PassMode : int {
     PASS_PLAIN = 0,      // transform, optional four-step twiddle, scaled store
     PASS_CH_NL = 1,      // inverse transform, c = Re(.)/N, g = c^3 - c, forward transform
     PASS_CH_UPDATE = 2,  // forward transform, then the CH update of c_hat (no store of the transform)
+    // Hermitian half-spectrum passes of a 3-D field (x frequencies 0 .. N2/2 kept)
+    PASS_HERM_INV = 3,   // inverse z-transform of (c_hat(k) + conj(c_hat(-k))) / 2 into the half array
+    PASS_NL_HALF = 4,    // x rows: half spectrum -> real -> g = c^3 - c -> half spectrum
+    PASS_MIRROR = 5,     // forward z-transform of the half array, stored for every x frequency
+    PASS_UPD_HALF = 6,   // forward z-transform of the half array, then the CH update of c_hat
 };
+constexpr bool is_update_mode(int m) { return m == PASS_CH_UPDATE || m == PASS_UPD_HALF; }
+constexpr bool reads_half(int m) { return m == PASS_MIRROR || m == PASS_UPD_HALF; }
 
 // Padded (axis 0, 1, 2) coordinates of element (p, j) of the tile at pencil q0
 // of the pass along the field's first axis: 3-D fields (z = j, (y, x) from the
@@ -716,7 +798,7 @@ __device__ __forceinline__ UpdTile upd_tile(const PassParams<T>& a, int q0) {
 // evaluates this independently (no block-wide synchronisation needed).
 template <typename T, int P, int MODE>
 __device__ __forceinline__ bool tile_live(const PassParams<T>& a, long long q0) {
-    if constexpr (MODE != PASS_CH_UPDATE) return true;
+    if constexpr (!is_update_mode(MODE)) return true;
     else {
         if (a.fu.dense) return true;
         const UpdTile u = upd_tile<T, P>(a, (int)q0);
@@ -782,7 +864,7 @@ template <typename T, int L> __host__ __device__ constexpr bool upd_stages_chat(
 // non-frozen c_hat rows were staged in shared memory (layout LY) by cp.async
 // during the transform; otherwise a butterfly's c_hat loads are issued before
 // its arithmetic.
-template <typename T, int L, int P, int NT, int R, bool CS, class LY> struct UpdOut {
+template <typename T, int L, int P, int NT, int R, bool CS, class LY, bool HALF = false> struct UpdOut {
     using C = cx_t<T>;
     static constexpr bool SYNC = false;
     static constexpr int NS = L / R;
@@ -793,6 +875,7 @@ template <typename T, int L, int P, int NT, int R, bool CS, class LY> struct Upd
     const T* kp;          // shared |k|^2 table of the pass axis
     const C* cs;          // staged c_hat tile (CS)
     int nbx, bxs, lx, l_out;
+    bool mir;             // HALF: this pencil's transform is the conjugate mirror's
     C* cb;                // c_hat of (p, j = 0)
     int osJ;
     T kx, kc;
@@ -812,6 +895,12 @@ template <typename T, int L, int P, int NT, int R, bool CS, class LY> struct Upd
         l_out = u.l_out;
         cb = f.c_hat + ((long long)u.o * a.osO + (long long)(u.i0 + (int)(threadIdx.x % P)) * a.osI);
         osJ = (int)a.osJ;
+        mir = HALF && x > (a.hg.N2 >> 1);
+    }
+    // output index of transform output m: the mirror's output m is frequency -m
+    __device__ __forceinline__ int kz_of(int m) const {
+        if constexpr (HALF) return (mir && m != 0) ? L - m : m;
+        else return m;
     }
     // before the last stage: the staged c_hat must have landed and be visible
     __device__ __forceinline__ void pre() {
@@ -825,7 +914,7 @@ template <typename T, int L, int P, int NT, int R, bool CS, class LY> struct Upd
         if constexpr (!CS) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int jj = j + r * NS;
+                const int jj = kz_of(j + r * NS);
                 if ((entry(jj) & 3u) != SPDBA_FROZEN) cv[k][r] = cb[jj * osJ];
             }
         }
@@ -835,7 +924,7 @@ template <typename T, int L, int P, int NT, int R, bool CS, class LY> struct Upd
         const bool d3 = f.g.ndim == 3;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int jj = j + r * NS;
+            const int jj = kz_of(j + r * NS);
             const int bp = (int)f.fd_bp.div((uint32_t)jj);
             const unsigned e = tab[bp * nbx + bxs];
             const int st = (int)(e & 3u);
@@ -843,9 +932,13 @@ template <typename T, int L, int P, int NT, int R, bool CS, class LY> struct Upd
             C c;
             if constexpr (CS) c = cs[LY::idx(p, jj)];
             else c = cv[k][r];
+            C gv = v[r];
+            if constexpr (HALF) {
+                if (mir) gv.y = -gv.y;
+            }
             // same association as the staged kernels: (k_outer + k_pass) then + k_x
             const T k01 = d3 ? kp[jj] + kc : kc + kp[jj];
-            C nv = ch_new(c, v[r], k01 + kx, f.dt, f.dtkappa);
+            C nv = ch_new(c, gv, k01 + kx, f.dt, f.dtkappa);
             if (st == SPDBA_TRANSITION) {
                 const int lj = jj - bp * (d3 ? f.g.b[0] : f.g.b[1]);
                 nv = d3 ? ch_blend<T>(c, nv, f.taper, f.g, e >> 2, lj, l_out, lx)
@@ -961,10 +1054,11 @@ __global__ void __launch_bounds__(NT) fft_pass_kernel(PassParams<T> a) {
 // (chosen from the compiler's register counts: the largest count of CTAs at
 // which the kernel does not spill)
 template <typename T, int L, int MODE, bool PFAST> struct PipeOcc {
+    static constexpr bool PLAINISH = MODE == PASS_PLAIN || MODE == PASS_MIRROR;
     static constexpr int value = sizeof(T) != 4 || L > 512     ? 1
-                                 : L == 384 || L == 512        ? ((MODE == PASS_PLAIN && (PFAST || L == 512)) ? 2 : 1)
+                                 : L == 384 || L == 512        ? ((PLAINISH && (PFAST || L == 512)) ? 2 : 1)
                                  : L == 192                    ? (MODE == PASS_CH_NL ? 1 : 2)
-                                 : MODE == PASS_CH_UPDATE      ? 2
+                                 : is_update_mode(MODE)        ? 2
                                                                : 3;
 };
 
@@ -975,9 +1069,9 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm0 = reinterpret_cast<C*>(smem_raw);
     C* sm1 = sm0 + LY::SIZE;
-    __shared__ uint8_t s_tab[MODE == PASS_CH_UPDATE ? kUpdTable : 1];
-    __shared__ T s_kp[MODE == PASS_CH_UPDATE ? L : 1];   // |k|^2 of the pass axis
-    if constexpr (MODE == PASS_CH_UPDATE) {
+    __shared__ uint8_t s_tab[is_update_mode(MODE) ? kUpdTable : 1];
+    __shared__ T s_kp[is_update_mode(MODE) ? L : 1];   // |k|^2 of the pass axis
+    if constexpr (is_update_mode(MODE)) {
         const T* kpg = a.fu.g.ndim == 3 ? a.fu.k2ax[0] : a.fu.k2ax[1];
         for (int j = threadIdx.x; j < L; j += NT) s_kp[j] = kpg[j];   // visible after the loop's first barrier
     }
@@ -987,22 +1081,31 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
     constexpr bool DIRECT = (LY::PMAP || (L / Radices_last<L>::value) * (int)sizeof(C) >= 32) &&
                             Radices_last<L>::value != 3;
     const long long ntiles = (a.O * a.I) / P;
-    if constexpr (MODE == PASS_CH_UPDATE) ch_update_stats<T, NT>(a.fu);
+    if constexpr (is_update_mode(MODE)) ch_update_stats<T, NT>(a.fu);
     long long t = blockIdx.x;
     while (t < ntiles && !tile_live<T, P, MODE>(a, t * P)) t += gridDim.x;
-    if (t < ntiles) issue_tile<T, L, P, NT, PFAST, LY>(sm0, a, t * P);
+    if (t < ntiles) {
+        if constexpr (reads_half(MODE)) issue_tile_half<T, L, P, NT, LY>(sm0, a, t * P);
+        else issue_tile<T, L, P, NT, PFAST, LY>(sm0, a, t * P);
+    }
     cp_async_commit();
     int buf = 0;
     while (t < ntiles) {
         long long tn = t + gridDim.x;
         while (tn < ntiles && !tile_live<T, P, MODE>(a, tn * P)) tn += gridDim.x;
-        if (tn < ntiles) issue_tile<T, L, P, NT, PFAST, LY>(buf ? sm0 : sm1, a, tn * P);
+        if (tn < ntiles) {
+            if constexpr (reads_half(MODE)) issue_tile_half<T, L, P, NT, LY>(buf ? sm0 : sm1, a, tn * P);
+            else issue_tile<T, L, P, NT, PFAST, LY>(buf ? sm0 : sm1, a, tn * P);
+        }
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         C* sm = buf ? sm1 : sm0;
         const long long q0 = t * P;
-        if constexpr (MODE != PASS_CH_UPDATE && !DIRECT) {
+        if constexpr (MODE == PASS_MIRROR) {
+            MirrorPlainOut<T, L, P> out(a, q0);
+            run_stages_out<T, L, P, NT, SIGN, LY>(sm, a.tw, out);
+        } else if constexpr (!is_update_mode(MODE) && !DIRECT) {
             // short pencil-major pencils: the staged store keeps 16-byte coalesced writes
             tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
             store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
@@ -1037,12 +1140,13 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
                 __syncthreads();
                 C* smc = sm0 + 2 * LY::SIZE;
                 issue_chat<T, L, P, NT, LY>(smc, a, u, s_tab);
-                UpdOut<T, L, P, NT, Radices_last<L>::value, true, LY> out(a, u, s_tab, s_kp, smc);
+                UpdOut<T, L, P, NT, Radices_last<L>::value, true, LY, MODE == PASS_UPD_HALF> out(a, u, s_tab, s_kp,
+                                                                                               smc);
                 run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
             } else {
                 ch_update_table<T, L, P, NT>(s_tab, a, u);
                 run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
-                UpdOut<T, L, P, NT, 4, false, LY> out(a, u, s_tab, s_kp, nullptr);
+                UpdOut<T, L, P, NT, 4, false, LY, MODE == PASS_UPD_HALF> out(a, u, s_tab, s_kp, nullptr);
                 drain_tile<T, L, P, NT, 4, LY>(sm, out);
             }
         }

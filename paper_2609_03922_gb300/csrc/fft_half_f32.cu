@@ -1,0 +1,74 @@
+// Half-spectrum pass kernels of 3-D complex64 Cahn-Hilliard steps.
+#include "fft_half.cuh"
+#include "kernel_table.h"
+
+namespace spdba {
+
+// pencils per tile of the z passes (row-major tiles), threads per CTA
+template <int L> struct HalfTile;
+template <> struct HalfTile<64> { static constexpr int P = 64; };
+template <> struct HalfTile<128> { static constexpr int P = 32; };
+template <> struct HalfTile<256> { static constexpr int P = 16; };
+template <> struct HalfTile<384> { static constexpr int P = 8; };
+template <> struct HalfTile<512> { static constexpr int P = 16; };
+constexpr int kHalfNT = 256;
+// rows per tile of the x pass: enough that every butterfly of a stage has a thread
+template <int M> struct NlHalfRows { static constexpr int value = M <= 128 ? 4096 / M : 16; };
+
+template <int L> static bool pick_z(int mode, KernelInfo* ki) {
+    constexpr int P = HalfTile<L>::P, NT = kHalfNT;
+    using C = cx_t<float>;
+    ki->P = P;
+    ki->NT = NT;
+    ki->pipe = true;
+    const int tile = LayoutB<L, P>::SIZE * (int)sizeof(C);
+    switch (mode) {
+        case PASS_HERM_INV:
+            ki->func = (const void*)fft_herm_inv_kernel<float, L, P, NT>;
+            ki->smem = 3 * tile;
+            return true;
+        case PASS_MIRROR:
+            ki->func = (const void*)fft_pass_pipe_kernel<float, L, P, NT, -1, PASS_MIRROR, true>;
+            ki->smem = 2 * tile;
+            return true;
+        case PASS_UPD_HALF:
+            ki->func = (const void*)fft_pass_pipe_kernel<float, L, P, NT, -1, PASS_UPD_HALF, true>;
+            ki->smem = (upd_stages_chat<float, L>() ? 3 : 2) * tile;
+            return true;
+        default:
+            return false;
+    }
+}
+
+template <int M> static bool pick_x(int nhp, KernelInfo* ki) {
+    constexpr int P = NlHalfRows<M>::value, NT = kHalfNT;
+    ki->P = P;
+    ki->NT = NT;
+    ki->pipe = true;
+    ki->func = (const void*)fft_nl_half_kernel<float, M, P, NT>;
+    ki->smem = (2 * P * nhp + LayoutA<M, P, true>::SIZE) * (int)sizeof(cx_t<float>);
+    return true;
+}
+
+bool get_half_kernel(int64_t L, int mode, int nhp, KernelInfo* ki) {
+    if (mode == PASS_NL_HALF) {
+        switch (L) {
+            case 32: return pick_x<32>(nhp, ki);
+            case 64: return pick_x<64>(nhp, ki);
+            case 128: return pick_x<128>(nhp, ki);
+            case 192: return pick_x<192>(nhp, ki);
+            case 256: return pick_x<256>(nhp, ki);
+            default: return false;
+        }
+    }
+    switch (L) {
+        case 64: return pick_z<64>(mode, ki);
+        case 128: return pick_z<128>(mode, ki);
+        case 256: return pick_z<256>(mode, ki);
+        case 384: return pick_z<384>(mode, ki);
+        case 512: return pick_z<512>(mode, ki);
+        default: return false;
+    }
+}
+
+}  // namespace spdba

@@ -64,6 +64,12 @@ template <typename T> struct FftEngine {
     void release();
 };
 
+// Half-spectrum pass of a 3-D complex64 field (PASS_HERM_INV, PASS_NL_HALF,
+// PASS_MIRROR, PASS_UPD_HALF); the caller fills the update / mass fields.
+spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, TwiddleCache<float>& tw, cudaStream_t st);
+// Pencils per tile of the pass kernels of length L (0 if none).
+template <typename T> int pass_tile_pencils(int64_t L);
+
 // Pass along axis `axis` of `batch` contiguous arrays of shape dims (in place).
 template <typename T>
 spdba_status make_axis_pass(Pass<T>* out, int ndim, const int64_t* dims, int64_t batch, int axis, int sign,

@@ -11,4 +11,9 @@ struct KernelInfo {
 // generic: the pencil count is not a multiple of the tile (simple kernel only)
 template <typename T>
 bool get_pass_kernel(int64_t L, int sign, int mode, bool loadp, bool storep, bool generic, KernelInfo* ki);
+// complex64 half-spectrum passes (PASS_HERM_INV, PASS_NL_HALF, PASS_MIRROR,
+// PASS_UPD_HALF); nhp = half row length (PASS_NL_HALF shared memory)
+bool get_half_kernel(int64_t L, int mode, int nhp, KernelInfo* ki);
+// pencils per tile of the pass kernels of length L (0 if none)
+template <typename T> int pass_tile_pencils(int64_t L);
 }  // namespace spdba

@@ -82,6 +82,13 @@ template <typename T> struct Group {
     std::vector<Pass<T>> pre_inv;   // inverse passes before the fused one (first reads c_hat)
     Pass<T> fused;                  // inverse + nonlinearity + forward along the fast axis
     std::vector<Pass<T>> pre_fwd;   // remaining forward passes
+    // Hermitian half-spectrum form (3-D complex64): the transforms between c_hat
+    // and the update run on x frequencies 0 .. N2/2 in `half`
+    bool use_half = false;          // in use (has_half: passes built)
+    bool has_half = false;
+    C* half = nullptr;
+    long long half_n = 0;           // elements of the half array
+    Pass<T> h_inv_z, h_inv_y, h_nl, h_fwd_y, h_mirror, h_upd;
     bool fused_update = false;      // the last forward pass carries the update (upd_pass)
     bool has_fused = false;         // upd_pass exists (else only the staged form)
     Pass<T> upd_pass;               // forward pass of the first axis with the update fused
@@ -265,6 +272,52 @@ template <typename T> static spdba_status group_buffers(spdba_plan* p, Group<T>&
     return SPDBA_OK;
 }
 
+// Half-spectrum passes of a 3-D complex64 group; SPDBA_ERR_UNSUPPORTED (and
+// no change) where the shape has no half-spectrum kernels or gains nothing.
+static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* dims) {
+    cudaStream_t st = p->st;
+    const int64_t N0 = dims[0], N1 = dims[1], N2 = dims[2];
+    if (N2 % 2 != 0 || N0 > 4096 || N1 > 4096 || N2 > 4096) return SPDBA_ERR_UNSUPPORTED;
+    const int Py = pass_tile_pencils<float>(N1);
+    if (Py == 0) return SPDBA_ERR_UNSUPPORTED;
+    const int64_t M = N2 / 2;
+    const int64_t NHP = ((M + 1 + Py - 1) / Py) * Py;
+    if (4 * NHP > 3 * N2) return SPDBA_ERR_UNSUPPORTED;   // under a quarter saved: keep the full form
+    HalfGeo hg;
+    hg.N0 = (int)N0; hg.N1 = (int)N1; hg.N2 = (int)N2; hg.NHP = (int)NHP;
+    hg.fd_N2.init((uint32_t)N2);
+    hg.fd_NHP.init((uint32_t)NHP);
+    TwiddleCache<float>& tw = p->tw32;
+    Pass<float> hz, hy_inv, hnl, hy_fwd, hmir, hupd;
+    spdba_status s;
+    if ((s = make_half_pass(&hz, PASS_HERM_INV, hg, tw, st)) != SPDBA_OK) return s;
+    if ((s = make_half_pass(&hnl, PASS_NL_HALF, hg, tw, st)) != SPDBA_OK) return s;
+    if ((s = make_half_pass(&hmir, PASS_MIRROR, hg, tw, st)) != SPDBA_OK) return s;
+    if (N2 % hmir.P != 0) return SPDBA_ERR_UNSUPPORTED;   // z tiles must stay within one x row
+    const int64_t dh[3] = {N0, N1, NHP};
+    if ((s = make_axis_pass<float>(&hy_inv, 3, dh, 1, 1, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+    if ((s = make_axis_pass<float>(&hy_fwd, 3, dh, 1, 1, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+    if (r.has_fused) {
+        if ((s = make_half_pass(&hupd, PASS_UPD_HALF, hg, tw, st)) != SPDBA_OK) return s;
+        const PassParams<float> keep = hupd.p;
+        hupd.p.fu = r.upd_pass.p.fu;   // the same update (states, tables, divisors) as the full form
+        hupd.p.hg = keep.hg;
+    }
+    r.half_n = N0 * N1 * NHP;
+    if ((s = r.alloc(&r.half, sizeof(cx_t<float>) * (size_t)r.half_n)) != SPDBA_OK) return s;
+    SPDBA_CUDA(cudaMemsetAsync(r.half, 0, sizeof(cx_t<float>) * (size_t)r.half_n, st));
+    hnl.p.mass_stride = (int)(sizeof(DevStats) / sizeof(double));
+    r.h_inv_z = hz;
+    r.h_inv_y = hy_inv;
+    r.h_nl = hnl;
+    r.h_fwd_y = hy_fwd;
+    r.h_mirror = hmir;
+    r.h_upd = hupd;
+    r.has_half = true;
+    r.use_half = true;
+    return SPDBA_OK;
+}
+
 template <typename T>
 static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const int64_t* dims, const int32_t* block,
                                   long long batch) {
@@ -332,6 +385,12 @@ static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const in
         // the plain pass is kept in every case: the staged form uses it
         if ((s = make_axis_pass<T>(&ps, ndim, dims, batch, a, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
         r.pre_fwd.push_back(ps);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (ndim == 3 && batch == 1 && p->opt.half_spectrum) {
+            s = setup_half(p, r, dims);
+            if (s != SPDBA_OK && s != SPDBA_ERR_UNSUPPORTED) return s;
+        }
     }
     return SPDBA_OK;
 }
@@ -466,6 +525,8 @@ static void prof_select(spdba_plan* p, long long step) {
     p->prof_on = p->prof && (p->prof_every <= 1 || step % p->prof_every == 0);
 }
 
+template <typename T> static spdba_status ch_staged_update(spdba_plan* p, Group<T>& r, int dense);
+
 template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>& r) {
     cudaStream_t st = p->st;
     spdba_status s;
@@ -476,6 +537,50 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
     if (reassess) {
         s = p->pred ? group_assess_predicted<T>(p, r) : group_assess<T>(p, r);
         if (s != SPDBA_OK) return s;
+    }
+    const int dense = !adaptive || all_active_step(p, r.step);
+    if (r.use_half) {
+        // Hermitian half-spectrum form: z (from c_hat), y, x (nonlinearity), y, z (update)
+        const double full_b = sizeof(cx_t<T>) * (double)(r.batch * r.n);
+        const double half_b = sizeof(cx_t<T>) * (double)r.half_n;
+        {
+            ProfScope pr(p, K_FFT_PASS, full_b + half_b);
+            if ((s = launch_pass<T>(r.h_inv_z, r.c_hat, r.half, st)) != SPDBA_OK) return s;
+        }
+        {
+            ProfScope pr(p, K_FFT_PASS, 2.0 * half_b);
+            if ((s = launch_pass<T>(r.h_inv_y, r.half, r.half, st)) != SPDBA_OK) return s;
+        }
+        Pass<T> nl = r.h_nl;
+        if (reassess) {
+            nl.p.mass = &r.stats[0].mass;
+            zero_strided_kernel<<<1, 256, 0, st>>>(&r.stats[0].mass, r.batch, nl.p.mass_stride);
+            p->launches += 1;
+        }
+        {
+            ProfScope pr(p, K_FUSED_NL, 2.0 * half_b);
+            if ((s = launch_pass<T>(nl, r.half, r.half, st)) != SPDBA_OK) return s;
+        }
+        {
+            ProfScope pr(p, K_FFT_PASS, 2.0 * half_b);
+            if ((s = launch_pass<T>(r.h_fwd_y, r.half, r.half, st)) != SPDBA_OK) return s;
+        }
+        p->launches += 4;
+        if (r.fused_update) {
+            Pass<T> ps = r.h_upd;
+            ps.p.fu.dense = dense;
+            ProfScope pr(p, K_FFT_UPDATE, half_b + 2.0 * full_b);
+            if ((s = launch_pass<T>(ps, r.half, r.work, st)) != SPDBA_OK) return s;
+            p->launches += 1;
+            r.step += 1;
+            return SPDBA_OK;
+        }
+        {
+            ProfScope pr(p, K_FFT_PASS, half_b + full_b);
+            if ((s = launch_pass<T>(r.h_mirror, r.half, r.work, st)) != SPDBA_OK) return s;
+            p->launches += 1;
+        }
+        return ch_staged_update<T>(p, r, dense);
     }
     // pre-update: c = Re(IFFT(c_hat)), g = c^3 - c, g_hat = FFT(g)
     const double pass_bytes = 2.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n);
@@ -497,7 +602,6 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
         if ((s = launch_pass<T>(fused, src, r.work, st)) != SPDBA_OK) return s;
         p->launches += 1;
     }
-    const int dense = !adaptive || all_active_step(p, r.step);
     for (size_t k = 0; k < r.pre_fwd.size(); ++k) {
         const bool last_fused = r.fused_update && k + 1 == r.pre_fwd.size();
         if (last_fused) {
@@ -516,7 +620,13 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
         r.step += 1;
         return SPDBA_OK;
     }
-    // update
+    return ch_staged_update<T>(p, r, dense);
+}
+
+// The staged update: list-driven (or dense) update kernel reading g_hat from work.
+template <typename T> static spdba_status ch_staged_update(spdba_plan* p, Group<T>& r, int dense) {
+    cudaStream_t st = p->st;
+    spdba_status s;
     CHUpdateArgs<T> a;
     a.c_hat = r.c_hat;
     a.g_hat = r.work;
@@ -866,6 +976,7 @@ extern "C" void spdba_options_default(spdba_options* o) {
     o->warmup_steps = 0;
     o->use_graph = 1;
     o->fuse_update = 1;
+    o->half_spectrum = 1;
     o->dt = 0.01;
     o->kappa = 1.0;
     o->dx = 1.0;
@@ -1057,8 +1168,11 @@ template <typename T> static spdba_status snap_restore(spdba_plan* p, Group<T>& 
     return SPDBA_OK;
 }
 
-template <typename T> static void apply_config(spdba_plan* p, int fuse, int graph) {
-    for (auto& g : groups<T>(p)) g->fused_update = fuse && g->has_fused;
+template <typename T> static void apply_config(spdba_plan* p, int fuse, int graph, int half) {
+    for (auto& g : groups<T>(p)) {
+        g->fused_update = fuse && g->has_fused;
+        g->use_half = half && g->has_half;
+    }
     p->opt.use_graph = graph;
     if (p->seg_exec) {
         cudaGraphExecDestroy(p->seg_exec);
@@ -1071,14 +1185,21 @@ template <typename T> static void apply_config(spdba_plan* p, int fuse, int grap
 // keeps the fastest and restores the state.
 template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t steps, spdba_tune_report* rep) {
     auto& gs = groups<T>(p);
-    bool any_fused = false;
-    for (auto& g : gs) any_fused |= g->has_fused;
-    std::vector<std::pair<int, int>> cand;
-    for (int f : {1, 0}) {
-        if (f && !any_fused) continue;
-        for (int gr : {1, 0}) {
-            if (gr && p->st == 0) continue;   // graphs need a non-legacy stream
-            cand.push_back({f, gr});
+    bool any_fused = false, any_half = false;
+    for (auto& g : gs) {
+        any_fused |= g->has_fused;
+        any_half |= g->has_half;
+    }
+    struct Cand { int fuse, graph, half; };
+    std::vector<Cand> cand;
+    for (int hf : {1, 0}) {
+        if (hf && !any_half) continue;
+        for (int f : {1, 0}) {
+            if (f && !any_fused) continue;
+            for (int gr : {1, 0}) {
+                if (gr && p->st == 0) continue;   // graphs need a non-legacy stream
+                cand.push_back({f, gr, hf});
+            }
         }
     }
     if ((int)cand.size() > SPDBA_TUNE_MAX) cand.resize(SPDBA_TUNE_MAX);
@@ -1092,7 +1213,7 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
     if (s == SPDBA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         s = fail(SPDBA_ERR_CUDA, "autotune: cudaEventCreate failed");
     for (size_t c = 0; c < cand.size() && s == SPDBA_OK; ++c) {
-        apply_config<T>(p, cand[c].first, cand[c].second);
+        apply_config<T>(p, cand[c].fuse, cand[c].graph, cand[c].half);
         if ((s = plan_step<T>(p, R)) != SPDBA_OK) break;   // warm-up (graph capture)
         for (size_t i = 0; i < gs.size() && s == SPDBA_OK; ++i) s = snap_restore<T>(p, *gs[i], snaps[i]);
         if (s != SPDBA_OK) break;
@@ -1109,7 +1230,7 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
     size_t best = 0;
     for (size_t c = 1; c < cand.size(); ++c)
         if (ms[c] < ms[best]) best = c;
-    if (s == SPDBA_OK && !cand.empty()) apply_config<T>(p, cand[best].first, cand[best].second);
+    if (s == SPDBA_OK && !cand.empty()) apply_config<T>(p, cand[best].fuse, cand[best].graph, cand[best].half);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaError_t e = cudaStreamSynchronize(p->st);
@@ -1121,8 +1242,9 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
         memset(rep, 0, sizeof *rep);
         rep->n_candidates = (int32_t)cand.size();
         for (size_t c = 0; c < cand.size(); ++c) {
-            rep->fuse_update[c] = cand[c].first;
-            rep->use_graph[c] = cand[c].second;
+            rep->fuse_update[c] = cand[c].fuse;
+            rep->use_graph[c] = cand[c].graph;
+            rep->half_spectrum[c] = cand[c].half;
             rep->ms_per_step[c] = ms[c];
         }
         rep->chosen = (int32_t)best;

@@ -27,6 +27,7 @@ class spdba_options(ctypes.Structure):
                 ("measure", ctypes.c_int32), ("tau_rule", ctypes.c_int32), ("transitions", ctypes.c_int32),
                 ("force_dc", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
                 ("warmup_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("fuse_update", ctypes.c_int32),
+                ("half_spectrum", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("dx", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("gamma", ctypes.c_double), ("h", ctypes.c_double),
                 ("dt_sample", ctypes.c_double), ("stream", ctypes.c_void_p)]
@@ -41,7 +42,8 @@ class spdba_stats(ctypes.Structure):
 
 class spdba_tune_report(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int32), ("fuse_update", ctypes.c_int32 * 8),
-                ("use_graph", ctypes.c_int32 * 8), ("ms_per_step", ctypes.c_double * 8), ("chosen", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32 * 8), ("half_spectrum", ctypes.c_int32 * 8),
+                ("ms_per_step", ctypes.c_double * 8), ("chosen", ctypes.c_int32)]
 
 
 class spdba_kernel_time(ctypes.Structure):
@@ -254,7 +256,8 @@ class Plan:
         rep = spdba_tune_report()
         check(lib().spdba_plan_autotune(self._p, int(steps), ctypes.byref(rep)))
         cands = [{"fuse_update": int(rep.fuse_update[i]), "use_graph": int(rep.use_graph[i]),
-                  "ms_per_step": float(rep.ms_per_step[i])} for i in range(rep.n_candidates)]
+                  "half_spectrum": int(rep.half_spectrum[i]), "ms_per_step": float(rep.ms_per_step[i])}
+                 for i in range(rep.n_candidates)]
         return {"candidates": cands, "chosen": int(rep.chosen)}
 
     def profile_begin(self, every=1):
