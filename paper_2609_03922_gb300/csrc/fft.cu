@@ -259,7 +259,7 @@ template spdba_status make_pass<double>(Pass<double>*, int64_t, int, int, long l
 // Half-spectrum passes of a 3-D complex64 field (see fft_half.cuh).
 spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, TwiddleCache<float>& tw, cudaStream_t st) {
     const bool rows = mode == PASS_NL_HALF;
-    const int64_t L = rows ? hg.N2 / 2 : hg.N0;
+    const int64_t L = rows ? hg.N2 : hg.N0;
     KernelInfo ki;
     if (!get_half_kernel(L, mode, hg.NHP, &ki))
         return fail(SPDBA_ERR_UNSUPPORTED, "no half-spectrum kernel for length %lld (mode %d)", (long long)L, mode);
@@ -292,7 +292,7 @@ spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, Twidd
     s = SPDBA_OK;
     if (!(a.tw = tw.get(L, st, &s))) return s;
     a.tw4 = nullptr;
-    if (rows && !(a.tw4 = tw.get(hg.N2, st, &s))) return s;
+
     a.n4 = 1;
     a.scale = 1.f;
     a.generic = 0;

@@ -7,14 +7,12 @@
 // 0 .. N2/2 only (the "half array", rows of NHP >= N2/2 + 1 entries):
 //   z: inverse of h, from the full c_hat (PASS_HERM_INV, this file)
 //   y: plain inverse pass on the half array
-//   x: half spectrum -> real row -> g = c^3 - c -> half spectrum (PASS_NL_HALF)
+//   x: half spectrum -> real row -> g = c^3 - c -> half spectrum, two rows per
+//      complex transform (PASS_NL_HALF)
 //   y: plain forward pass on the half array
 //   z: forward pass of the half array for every x frequency, the mirrored
 //      ones from D(z, ky, kx) = conj(D(z, -ky, -kx)) (PASS_UPD_HALF with the
 //      update, PASS_MIRROR as a plain store), in fft_core.cuh.
-// The x rows use the standard length-N2/2 complex transform of a real row of
-// N2 samples: even and odd samples as real and imaginary parts, with the
-// split / merge twiddles exp(-+2 pi i k / N2).
 #pragma once
 #include "fft_core.cuh"
 
@@ -102,12 +100,12 @@ __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
 }
 
 // ---------------------------------------------------------------- x rows
-// Real-row split (inverse): Z[k] = (X[k] + conj X[M-k]) + i w^k (X[k] - conj X[M-k]),
-// w = exp(2 pi i / N2), k < M = N2/2; the length-M inverse of Z holds the real row's
-// even and odd samples as real and imaginary parts.
-// Merge (forward): with U the length-M transform of u = g_even + i g_odd,
-// G[k] = (U[k] + conj U[-k]) / 2 - i w^-k (U[k] - conj U[-k]) / 2 for k < M,
-// G[M] = Re U[0] - Im U[0].
+// Two real rows r1, r2 (half spectra X1, X2, x frequencies 0 .. N2/2) share one
+// complex transform of the full length N2: Z[k] = X1[k] + i X2[k], extended to
+// k > N2/2 by Z[k] = conj(X1[N2-k]) + i conj(X2[N2-k]), whose inverse is
+// x1 + i x2.  The nonlinearity acts on real and imaginary parts, and the
+// forward transform W of g1 + i g2 separates into
+// G1[k] = (W[k] + conj W[-k]) / 2, G2[k] = (W[k] - conj W[-k]) / (2i), k <= N2/2.
 template <typename T> struct ChNlPairMid {
     T scale, msum;
     __device__ __forceinline__ cx_t<T> operator()(int, int, cx_t<T> x) {
@@ -130,12 +128,14 @@ template <typename T, int L, class LY> struct SmemOut {
     }
 };
 
-// L = M = N2 / 2 (transform length); rows of NHP entries, P rows per tile.
-// a.tw: stage twiddles of M; a.tw4: exp(-2 pi i m / N2), m < N2.
+// L = N2 (transform length), P real rows per tile (P / 2 transform pencils),
+// rows of NHP entries.  a.tw: stage twiddles of N2.
 template <typename T, int L, int P, int NT>
-__global__ void __launch_bounds__(NT, 2) fft_nl_half_kernel(PassParams<T> a) {
+__global__ void __launch_bounds__(NT, L == 384 ? 1 : 512 / NT) fft_nl_half_kernel(PassParams<T> a) {
     using C = cx_t<T>;
-    using LY = LayoutA<L, P, true>;
+    constexpr int PP = P / 2;
+    constexpr int M = L / 2;
+    using LY = LayoutA<L, PP, true>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NHP = a.hg.NHP;
     C* rows0 = reinterpret_cast<C*>(smem_raw);
@@ -160,41 +160,42 @@ __global__ void __launch_bounds__(NT, 2) fft_nl_half_kernel(PassParams<T> a) {
         __syncthreads();
         C* rw = buf ? rows1 : rows0;
         const long long q0 = t * P;
-        // split into the length-M inverse input
-        for (int e = threadIdx.x; e < P * L; e += NT) {
-            const int p = e / L, k = e - p * L;
-            const C x = rw[p * NHP + k];
-            C y = rw[p * NHP + (L - k)];
-            y.y = -y.y;
-            C w = __ldg(a.tw4 + k);
-            w.y = -w.y;                           // exp(+2 pi i k / N2)
-            const C d = cmul(w, csub(x, y));
-            tb[LY::idx(p, k)] = mk<C>(x.x + y.x - d.y, x.y + y.y + d.x);
+        // pack row pairs into full-length Hermitian-extended complex rows
+        for (int e = threadIdx.x; e < PP * L; e += NT) {
+            const int pp = e / L, k = e - pp * L;
+            const C* r1 = rw + (2 * pp) * NHP;
+            const C* r2 = r1 + NHP;
+            C x1, x2;
+            if (k <= M) {
+                x1 = r1[k];
+                x2 = r2[k];
+            } else {
+                x1 = r1[L - k];
+                x2 = r2[L - k];
+                x1.y = -x1.y;
+                x2.y = -x2.y;
+            }
+            tb[LY::idx(pp, k)] = mk<C>(x1.x - x2.y, x1.y + x2.x);
         }
         __syncthreads();
-        // inverse, c = Re / N and g = c^3 - c on both samples of each pair, forward
+        // inverse, c = Re / N and g = c^3 - c on both rows, forward
         ChNlPairMid<T> mid{a.nl_scale, (T)0};
         SmemOut<T, L, LY> so{tb};
-        transform_pair<T, L, P, NT, +1, -1, LY>(tb, a.tw, mid, so);
+        transform_pair<T, L, PP, NT, +1, -1, LY>(tb, a.tw, mid, so);
         __syncthreads();
-        // merge into the half spectrum of g (padding entries zero)
-        for (int e = threadIdx.x; e < P * NHP; e += NT) {
-            const int p = e / NHP, k = e - p * NHP;
-            C g = mk<C>((T)0, (T)0);
-            if (k < L) {
-                const C u1 = tb[LY::idx(p, k)];
-                C u2 = tb[LY::idx(p, k == 0 ? 0 : L - k)];
-                u2.y = -u2.y;
-                const C ev = mk<C>((T)0.5 * (u1.x + u2.x), (T)0.5 * (u1.y + u2.y));
-                const C od = mk<C>((T)0.5 * (u1.y - u2.y), (T)-0.5 * (u1.x - u2.x));   // (u1 - u2) / (2i)
-                const C w = __ldg(a.tw4 + k);                                             // exp(-2 pi i k / N2)
-                const C wo = cmul(w, od);
-                g = mk<C>(ev.x + wo.x, ev.y + wo.y);
-            } else if (k == L) {
-                const C u0 = tb[LY::idx(p, 0)];
-                g = mk<C>(u0.x - u0.y, (T)0);
+        // separate the two rows' half spectra (padding entries zero)
+        for (int e = threadIdx.x; e < PP * NHP; e += NT) {
+            const int pp = e / NHP, k = e - pp * NHP;
+            C g1 = mk<C>((T)0, (T)0), g2 = g1;
+            if (k <= M) {
+                const C w = tb[LY::idx(pp, k)];
+                C v = tb[LY::idx(pp, k == 0 ? 0 : L - k)];
+                v.y = -v.y;                                                   // conj W[-k]
+                g1 = mk<C>((T)0.5 * (w.x + v.x), (T)0.5 * (w.y + v.y));
+                g2 = mk<C>((T)0.5 * (w.y - v.y), (T)-0.5 * (w.x - v.x));      // (w - v) / (2i)
             }
-            rw[e] = g;
+            rw[(2 * pp) * NHP + k] = g1;
+            rw[(2 * pp + 1) * NHP + k] = g2;
         }
         __syncthreads();
         {

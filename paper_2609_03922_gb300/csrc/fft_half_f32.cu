@@ -12,9 +12,6 @@ template <> struct HalfTile<256> { static constexpr int P = 16; };
 template <> struct HalfTile<384> { static constexpr int P = 8; };
 template <> struct HalfTile<512> { static constexpr int P = 16; };
 constexpr int kHalfNT = 256;
-// rows per tile of the x pass: enough that every butterfly of a stage has a thread
-template <int M> struct NlHalfRows { static constexpr int value = M <= 128 ? 4096 / M : 16; };
-
 template <int L> static bool pick_z(int mode, KernelInfo* ki) {
     constexpr int P = HalfTile<L>::P, NT = kHalfNT;
     using C = cx_t<float>;
@@ -40,24 +37,27 @@ template <int L> static bool pick_z(int mode, KernelInfo* ki) {
     }
 }
 
-template <int M> static bool pick_x(int nhp, KernelInfo* ki) {
-    constexpr int P = NlHalfRows<M>::value, NT = kHalfNT;
+// real rows per tile of the x pass (two rows per transform pencil)
+template <int N2> struct NlHalfRows { static constexpr int value = N2 <= 256 ? 4096 / N2 : 16; };
+
+template <int N2> static bool pick_x(int nhp, KernelInfo* ki) {
+    constexpr int P = NlHalfRows<N2>::value, NT = N2 <= 256 ? 128 : 256;
     ki->P = P;
     ki->NT = NT;
     ki->pipe = true;
-    ki->func = (const void*)fft_nl_half_kernel<float, M, P, NT>;
-    ki->smem = (2 * P * nhp + LayoutA<M, P, true>::SIZE) * (int)sizeof(cx_t<float>);
+    ki->func = (const void*)fft_nl_half_kernel<float, N2, P, NT>;
+    ki->smem = (2 * P * nhp + LayoutA<N2, P / 2, true>::SIZE) * (int)sizeof(cx_t<float>);
     return true;
 }
 
 bool get_half_kernel(int64_t L, int mode, int nhp, KernelInfo* ki) {
-    if (mode == PASS_NL_HALF) {
+    if (mode == PASS_NL_HALF) {   // L = N2, the full row length
         switch (L) {
-            case 32: return pick_x<32>(nhp, ki);
             case 64: return pick_x<64>(nhp, ki);
             case 128: return pick_x<128>(nhp, ki);
-            case 192: return pick_x<192>(nhp, ki);
             case 256: return pick_x<256>(nhp, ki);
+            case 384: return pick_x<384>(nhp, ki);
+            case 512: return pick_x<512>(nhp, ki);
             default: return false;
         }
     }
