@@ -355,8 +355,14 @@ __device__ __forceinline__ void store_tile(const cx_t<T>* sm, const PassParams<T
 // multiplies element r by W_{NS R}^{r (j mod NS)}, runs a length-R DFT and writes
 // to (j / NS) NS R + (j mod NS) + r NS (autosorting; natural order after the
 // last stage).
-template <typename T, int L, int P, int NT, int SIGN, int NS, int R, class LY>
-__device__ __forceinline__ void stockham_stage(cx_t<T>* sm, const cx_t<T>* __restrict__ tw) {
+// Reader of a stage's input element m of pencil p: the tile itself by default.
+template <typename T, class LY> struct SmemIn {
+    const cx_t<T>* sm;
+    __device__ __forceinline__ cx_t<T> operator()(int p, int m) const { return sm[LY::idx(p, m)]; }
+};
+
+template <typename T, int L, int P, int NT, int SIGN, int NS, int R, class LY, class IN>
+__device__ __forceinline__ void stockham_stage_in(cx_t<T>* sm, const cx_t<T>* __restrict__ tw, const IN& in) {
     using C = cx_t<T>;
     constexpr int Q = L / R;
     constexpr int NB = P * Q;
@@ -370,7 +376,7 @@ __device__ __forceinline__ void stockham_stage(cx_t<T>* sm, const cx_t<T>* __res
             if constexpr (LY::PMAP) { p = b % P; j = b / P; }
             else { p = b / Q; j = b % Q; }
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][r] = sm[LY::idx(p, j + r * Q)];
+            for (int r = 0; r < R; ++r) v[k][r] = in(p, j + r * Q);
             if constexpr (NS > 1) {
                 int jm = j % NS;
 #pragma unroll
@@ -398,6 +404,11 @@ __device__ __forceinline__ void stockham_stage(cx_t<T>* sm, const cx_t<T>* __res
         }
     }
     __syncthreads();
+}
+
+template <typename T, int L, int P, int NT, int SIGN, int NS, int R, class LY>
+__device__ __forceinline__ void stockham_stage(cx_t<T>* sm, const cx_t<T>* __restrict__ tw) {
+    stockham_stage_in<T, L, P, NT, SIGN, NS, R, LY>(sm, tw, SmemIn<T, LY>{sm});
 }
 
 template <typename T, int L, int P, int NT, int SIGN, class LY, int NS, int R, int... Rest>
@@ -631,6 +642,45 @@ __device__ __forceinline__ void fused_mid_stage(cx_t<T>* sm, const cx_t<T>* __re
 // SB, the second's last stage emitting through `out`.  When the first's last
 // radix equals the second's first, the two meeting stages run fused in
 // registers (fused_mid_stage); otherwise `mid` rides in the first's last stage.
+// One transform whose first stage reads through `in` and whose last stage
+// emits through `out` (at least two stages).
+template <typename T, int L, int P, int NT, int SIGN, class LY, class IN, class OUT>
+__device__ __forceinline__ void run_stages_in_out(cx_t<T>* sm, const cx_t<T>* tw, const IN& in, OUT& out) {
+    constexpr int NST = NSTAGES<L>::value;
+    static_assert(NST >= 2, "a separate first and last stage");
+    stockham_stage_in<T, L, P, NT, SIGN, 1, radix_at<L>(0), LY>(sm, tw, in);
+    run_stage_range<T, L, P, NT, SIGN, LY, 1, NST - 1>(sm, tw);
+    stockham_stage_out<T, L, P, NT, SIGN, ns_at<L>(NST - 1), radix_at<L>(NST - 1), LY>(sm, tw, out);
+}
+
+template <typename T, int L, int P, int NT, int SA, int SB, class LY, class MID, class OUT>
+__device__ __forceinline__ void transform_pair(cx_t<T>* sm, const cx_t<T>* tw, MID& mid, OUT& out);
+
+// transform_pair whose first stage reads its inputs through `in` (an
+// elementwise preparation folded into the first stage's loads); at least
+// three stages in all.
+template <typename T, int L, int P, int NT, int SA, int SB, class LY, class IN, class MID, class OUT>
+__device__ __forceinline__ void transform_pair_in(cx_t<T>* sm, const cx_t<T>* tw, const IN& in, MID& mid, OUT& out) {
+    constexpr int NST = NSTAGES<L>::value;
+    constexpr int R0 = radix_at<L>(0), RL = radix_at<L>(NST - 1);
+    static_assert(NST >= 2, "the first stage must not be the meeting stage");
+    stockham_stage_in<T, L, P, NT, SA, 1, R0, LY>(sm, tw, in);
+    if constexpr (R0 == RL) {
+        run_stage_range<T, L, P, NT, SA, LY, 1, NST - 1>(sm, tw);
+        FirstStageOut<T, L, R0, LY> fo{sm};
+        fused_mid_stage<T, L, P, NT, SA, SB, L / R0, R0, LY>(sm, tw, mid, fo);
+        __syncthreads();
+        run_stage_range<T, L, P, NT, SB, LY, 1, NST - 1>(sm, tw);
+        stockham_stage_out<T, L, P, NT, SB, ns_at<L>(NST - 1), RL, LY>(sm, tw, out);
+    } else {
+        run_stage_range<T, L, P, NT, SA, LY, 1, NST - 1>(sm, tw);
+        MidOut<T, L, LY, MID> mo{sm, mid};
+        stockham_stage_out<T, L, P, NT, SA, ns_at<L>(NST - 1), RL, LY>(sm, tw, mo);
+        __syncthreads();
+        run_stages_out<T, L, P, NT, SB, LY>(sm, tw, out);
+    }
+}
+
 template <typename T, int L, int P, int NT, int SA, int SB, class LY, class MID, class OUT>
 __device__ __forceinline__ void transform_pair(cx_t<T>* sm, const cx_t<T>* tw, MID& mid, OUT& out) {
     constexpr int NST = NSTAGES<L>::value;

@@ -59,6 +59,16 @@ __device__ __forceinline__ void issue_herm(cx_t<T>* sm, const PassParams<T>& a, 
     }
 }
 
+// (direct + conj(mirror)) / 2 of element m of pencil p
+template <typename T, class LY> struct HermIn {
+    const cx_t<T>* a;
+    const cx_t<T>* b;
+    __device__ __forceinline__ cx_t<T> operator()(int p, int m) const {
+        const cx_t<T> x = a[LY::idx(p, m)], y = b[LY::idx(p, m)];
+        return mk<cx_t<T>>((T)0.5 * (x.x + y.x), (T)0.5 * (x.y - y.y));
+    }
+};
+
 template <typename T, int L, int P, int NT>
 __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
     using C = cx_t<T>;
@@ -82,16 +92,17 @@ __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
         cp_async_wait<1>();   // the direct and mirror tiles of t have landed
         __syncthreads();
         C* sm = buf ? smA1 : smA0;
-        for (int e = threadIdx.x; e < P * L; e += NT) {
-            const C x = sm[e], y = smB[e];
-            sm[e] = mk<C>((T)0.5 * (x.x + y.x), (T)0.5 * (x.y - y.y));
-        }
-        __syncthreads();
-        // the mirror tile of the next tile streams in during this tile's transform
+        // the first stage reads (direct + conj(mirror)) / 2; the stage's barrier
+        // between its reads and writes frees the mirror buffer
+        PlainOut<T, L> out(a, t * P);
+        HermIn<T, LY> in{sm, smB};
+        stockham_stage_in<T, L, P, NT, +1, 1, radix_at<L>(0), LY>(sm, a.tw, in);
+        // the mirror tile of the next tile streams in during the rest of the transform
         if (tn < ntiles) issue_herm<T, L, P, NT, LY>(smB, a, tn * P, true);
         cp_async_commit();
-        PlainOut<T, L> out(a, t * P);
-        run_stages_out<T, L, P, NT, +1, LY>(sm, a.tw, out);
+        run_stage_range<T, L, P, NT, +1, LY, 1, NSTAGES<L>::value - 1>(sm, a.tw);
+        stockham_stage_out<T, L, P, NT, +1, ns_at<L>(NSTAGES<L>::value - 1), radix_at<L>(NSTAGES<L>::value - 1), LY>(
+            sm, a.tw, out);
         __syncthreads();
         buf ^= 1;
         t = tn;
@@ -128,6 +139,28 @@ template <typename T, int L, class LY> struct SmemOut {
     }
 };
 
+// Packed input element k of transform pencil pp: X1[k] + i X2[k] from rows
+// 2 pp and 2 pp + 1, extended past N2/2 by conjugate symmetry.
+template <typename T, int L> struct PairPackIn {
+    const cx_t<T>* rw;
+    int nhp;
+    __device__ __forceinline__ cx_t<T> operator()(int pp, int k) const {
+        const cx_t<T>* r1 = rw + (2 * pp) * nhp;
+        const cx_t<T>* r2 = r1 + nhp;
+        cx_t<T> x1, x2;
+        if (k <= L / 2) {
+            x1 = r1[k];
+            x2 = r2[k];
+        } else {
+            x1 = r1[L - k];
+            x2 = r2[L - k];
+            x1.y = -x1.y;
+            x2.y = -x2.y;
+        }
+        return mk<cx_t<T>>(x1.x - x2.y, x1.y + x2.x);
+    }
+};
+
 // L = N2 (transform length), P real rows per tile (P / 2 transform pencils),
 // rows of NHP entries.  a.tw: stage twiddles of N2.
 template <typename T, int L, int P, int NT>
@@ -160,28 +193,12 @@ __global__ void __launch_bounds__(NT, L == 384 ? 1 : 512 / NT) fft_nl_half_kerne
         __syncthreads();
         C* rw = buf ? rows1 : rows0;
         const long long q0 = t * P;
-        // pack row pairs into full-length Hermitian-extended complex rows
-        for (int e = threadIdx.x; e < PP * L; e += NT) {
-            const int pp = e / L, k = e - pp * L;
-            const C* r1 = rw + (2 * pp) * NHP;
-            const C* r2 = r1 + NHP;
-            C x1, x2;
-            if (k <= M) {
-                x1 = r1[k];
-                x2 = r2[k];
-            } else {
-                x1 = r1[L - k];
-                x2 = r2[L - k];
-                x1.y = -x1.y;
-                x2.y = -x2.y;
-            }
-            tb[LY::idx(pp, k)] = mk<C>(x1.x - x2.y, x1.y + x2.x);
-        }
-        __syncthreads();
-        // inverse, c = Re / N and g = c^3 - c on both rows, forward
+        // inverse (its first stage packing the row pairs), c = Re / N and
+        // g = c^3 - c on both rows, forward
         ChNlPairMid<T> mid{a.nl_scale, (T)0};
         SmemOut<T, L, LY> so{tb};
-        transform_pair<T, L, PP, NT, +1, -1, LY>(tb, a.tw, mid, so);
+        PairPackIn<T, L> in{rw, NHP};
+        transform_pair_in<T, L, PP, NT, +1, -1, LY>(tb, a.tw, in, mid, so);
         __syncthreads();
         // separate the two rows' half spectra (padding entries zero)
         for (int e = threadIdx.x; e < PP * NHP; e += NT) {
