@@ -36,11 +36,10 @@ spdba_status make_geom_batched(Geom* g, int ndim, const int64_t* dims, const int
 }
 
 // ------------------------------------------------------------------ activity
-// One warp per block.  The block max of |q|^2 is exact in FP64: an FP32 value
-// p32 = fma(re, re, im*im) (relative error below 2^-22) screens each mode, and
-// only modes whose p32 reaches (1 - 2^-20) times the lane's running FP64 max
-// are evaluated exactly (re*re + im*im in FP64, the oracle's formula), so a
-// mode that is skipped cannot be the max.  Non-negative doubles order like
+// One warp per block.  The block max of |q|^2 is exact in FP64: the FP32
+// screen max(|re|, |im|) (screen_abs) selects the few modes that can hold the
+// max, and only those are evaluated exactly (re*re + im*im in FP64, the
+// oracle's formula), so a mode that is skipped cannot be the max.  Non-negative doubles order like
 // their bit patterns, so the warp max is two 32-bit integer reductions
 // (high word, then low word among the lanes holding the high maximum) and
 // costs no FP64 instruction.  The ENERGY sum is accumulated per lane in FP64.
@@ -52,6 +51,17 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 }
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Screen of a mode: s = max(|re|, |im|), exact in FP32 (no squaring, so no
+// underflow).  |q|^2 lies in [s^2, 2 s^2], so a mode with s below s_max / sqrt(2)
+// cannot hold the block's largest |q|^2 in FP64 (nor exceed a tie with it), and
+// s = 0 means q = 0 exactly.  The cut uses 0.7071067 < 1/sqrt(2) by more than
+// the product's rounding; a block whose screens are all 0 has no candidate and
+// max 0.
+__device__ __forceinline__ float screen_abs(float2 q) { return fmaxf(fabsf(q.x), fabsf(q.y)); }
+__device__ __forceinline__ float screen_cut(float smax) {
+    return smax > 0.f ? smax * 0.7071067f : __int_as_float(0x7f800000);   // +inf: no candidate
+}
 
 // exact FP64 |q|^2 for the modes of `mask` (a data-dependent loop, so the FP64
 // work is not speculated for every mode)
@@ -125,15 +135,13 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
             }
 #pragma unroll
             for (int k = 0; k < 2 * K2; ++k) {
-                p32[k] = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+                p32[k] = screen_abs(v[k]);
                 lmax = fmaxf(lmax, p32[k]);
                 if (!((dcmask >> k) & 1u)) lmaxnd = fmaxf(lmaxnd, p32[k]);
                 if (ENERGY) sm += mode_sq(v[k]);
             }
-            // p32 is within 2^-22 of the exact value: anything below 1 - 2^-20 of the
-            // warp's largest p32 cannot be the block max
-            const float cut = warp_max_nonneg_f(lmax) * (1.0f - 9.5367431640625e-07f);
-            const float cutnd = warp_max_nonneg_f(lmaxnd) * (1.0f - 9.5367431640625e-07f);
+            const float cut = screen_cut(warp_max_nonneg_f(lmax));
+            const float cutnd = screen_cut(warp_max_nonneg_f(lmaxnd));
             unsigned mask = 0;
 #pragma unroll
             for (int k = 0; k < 2 * K2; ++k) {
@@ -170,12 +178,10 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
 // order (full-row 16-byte loads, the layout HBM streams best).  A thread keeps
 // one mode pair column 2u, so it stays in one block bx = 2u / B2 throughout,
 // shared with the G = B2 / 2 neighbouring lanes of its row.  Per chunk of 16
-// modes a lane forms the FP32 screens p32, the G lanes agree (shuffles) on the
-// running screen max of their block, and only modes whose p32 reaches
-// (1 - 2^-20) of it are evaluated in FP64 -- about one per block and chunk, so
-// the slow FP64 pipe stays idle (a mode below that cannot be the max, as p32
-// is within 2^-22 of the exact value).  The row groups combine through shared
-// memory at the end.
+// modes a lane forms the FP32 screens, the G lanes agree (shuffles) on the
+// running screen max of their block, and only modes that pass screen_cut are
+// evaluated in FP64 -- a few per block, so the slow FP64 pipe stays idle.  The
+// row groups combine through shared memory at the end.
 constexpr int ROWACT_NT = 256;
 __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, const float2* __restrict__ q,
                                                                          double* __restrict__ maxsq,
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
         }
 #pragma unroll
         for (int k = 0; k < 2 * U; ++k) {
-            p32[k] = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+            p32[k] = screen_abs(v[k]);
             lmax = fmaxf(lmax, p32[k]);
             if (!((dcmask >> k) & 1u)) lmaxnd = fmaxf(lmaxnd, p32[k]);
         }
@@ -235,8 +241,8 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
         }
         pm = fmaxf(pm, lmax);
         pmnd = fmaxf(pmnd, lmaxnd);
-        const float cut = pm * (1.0f - 9.5367431640625e-07f);
-        const float cutnd = pmnd * (1.0f - 9.5367431640625e-07f);
+        const float cut = screen_cut(pm);
+        const float cutnd = screen_cut(pmnd);
         unsigned mask = 0;
 #pragma unroll
         for (int k = 0; k < 2 * U; ++k) {
@@ -329,16 +335,59 @@ spdba_status launch_tau(const double* gmax, int nruns, double threshold, int tau
 // ------------------------------------------------------------------ states
 constexpr int CLS_NT = 1024;
 
-__device__ __forceinline__ long long nbr(const Geom& g, long long b, int axis, int dir) {
-    long long c[3];
-    c[2] = b % g.nb[2];
-    c[1] = (b / g.nb[2]) % g.nb[1];
-    c[0] = b / (g.nb[2] * g.nb[1]);
-    c[axis] = (c[axis] + dir + g.nb[axis]) % g.nb[axis];
-    return (c[0] * g.nb[1] + c[1]) * g.nb[2] + c[2];
+// Block coordinates (32-bit: block maps hold fewer than 2^31 blocks).
+struct BCoord {
+    int c[3];
+};
+__device__ __forceinline__ BCoord bcoord(const Geom& g, int b) {
+    const int n2 = (int)g.nb[2], n1 = (int)g.nb[1];
+    BCoord r;
+    const int q = b / n2;
+    r.c[2] = b - q * n2;
+    r.c[0] = q / n1;
+    r.c[1] = q - r.c[0] * n1;
+    return r;
+}
+__device__ __forceinline__ int bindex(const Geom& g, const BCoord& c) {
+    return (c.c[0] * (int)g.nb[1] + c.c[1]) * (int)g.nb[2] + c.c[2];
+}
+// face neighbour along `axis` (periodic wrap of the block index)
+__device__ __forceinline__ BCoord bnbr(const Geom& g, BCoord c, int axis, int dir) {
+    const int n = (int)g.nb[axis];
+    int v = c.c[axis] + dir;
+    v = v < 0 ? v + n : (v >= n ? v - n : v);
+    c.c[axis] = v;
+    return c;
 }
 
 // ACTIVE iff the block's measure meets tau (>=), or forced.
+// ACTIVE iff measure >= tau, with tau formed from the scan's maxima (tau_kernel's
+// rule) by every thread; the first block of each run records tau and resets the
+// run's counts (what tau_kernel and zero_counts_kernel do as separate launches).
+__global__ void active_tau_kernel(Geom g, const double* __restrict__ msq, int msq_is_square, const double* gmax,
+                                  double threshold, int tau_rule, int exclude_dc, int force_dc, double* tau,
+                                  DevStats* stats, uint8_t* __restrict__ active) {
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nb = g.blocks();
+    if (b >= nb) return;
+    const long long run = b / g.bpr();
+    const double amax = sqrt(gmax[2 * run + (exclude_dc ? 1 : 0)]);
+    const double t = tau_rule == SPDBA_TAU_ABS ? threshold : threshold * amax;
+    double m = msq_is_square ? sqrt(msq[b]) : msq[b];
+    bool a = (force_dc && b == run * g.bpr()) || (m >= t);
+    active[b] = a ? 1 : 0;
+    if (b == run * g.bpr()) {
+        tau[run] = t;
+        if (stats) {
+            stats[run].tau = t;
+            stats[run].max_amp = amax;
+            stats[run].n_active = 0;
+            stats[run].n_transition = 0;
+            stats[run].assessments += 1;
+        }
+    }
+}
+
 __global__ void active_kernel(Geom g, const double* __restrict__ msq, int msq_is_square, const double* tau,
                               int force_dc, int all_active, uint8_t* __restrict__ active) {
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -350,10 +399,10 @@ __global__ void active_kernel(Geom g, const double* __restrict__ msq, int msq_is
     active[b] = a ? 1 : 0;
 }
 
-__device__ __forceinline__ bool has_active_nbr(const Geom& g, const uint8_t* active, long long b) {
+__device__ __forceinline__ bool has_active_nbr(const Geom& g, const uint8_t* active, const BCoord& c) {
     const int a0 = 3 - g.ndim;
     for (int ax = a0; ax < 3; ++ax) {
-        if (active[nbr(g, b, ax, -1)] || active[nbr(g, b, ax, +1)]) return true;
+        if (active[bindex(g, bnbr(g, c, ax, -1))] || active[bindex(g, bnbr(g, c, ax, +1))]) return true;
     }
     return false;
 }
@@ -363,19 +412,24 @@ __device__ __forceinline__ bool has_active_nbr(const Geom& g, const uint8_t* act
 // = slowest axis of the field).  One CTA-sized count per CTA goes to scratch.
 __global__ void __launch_bounds__(CLS_NT) state_kernel(Geom g, const uint8_t* __restrict__ active, int transitions,
                                                        uint8_t* __restrict__ states, uint8_t* __restrict__ chi,
-                                                       int* __restrict__ cta_count, DevStats* stats) {
+                                                       int* __restrict__ cta_count, DevStats* stats,
+                                                       double* gmax_reset, int nruns) {
     long long b = (long long)blockIdx.x * CLS_NT + threadIdx.x;
     long long nb = g.blocks();
+    // the activity maxima were consumed by the previous kernel: zero them for the next scan
+    if (gmax_reset != nullptr && blockIdx.x == 0)
+        for (int r = threadIdx.x; r < 2 * nruns; r += CLS_NT) gmax_reset[r] = 0.0;
     int st = 0;
     uint8_t cb = 0;
     if (b < nb) {
+        const BCoord c = bcoord(g, (int)b);
         if (active[b]) st = SPDBA_ACTIVE;
-        else if (transitions && has_active_nbr(g, active, b)) st = SPDBA_TRANSITION;
+        else if (transitions && has_active_nbr(g, active, c)) st = SPDBA_TRANSITION;
         const int a0 = 3 - g.ndim;
         for (int ax = a0; ax < 3; ++ax) {
             for (int d = 0; d < 2; ++d) {
-                long long n = nbr(g, b, ax, d == 0 ? -1 : +1);
-                bool frozen = !active[n] && !(transitions && has_active_nbr(g, active, n));
+                const BCoord cn = bnbr(g, c, ax, d == 0 ? -1 : +1);
+                bool frozen = !active[bindex(g, cn)] && !(transitions && has_active_nbr(g, active, cn));
                 if (frozen) cb |= (uint8_t)(1u << (2 * (ax - a0) + d));
             }
         }
@@ -464,7 +518,22 @@ spdba_status launch_classify(const Geom& g, const double* msq, int msq_is_square
     if (stats) zero_counts_kernel<<<1, 256, 0, st>>>(stats, g.runs());
     active_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(g, msq, msq_is_square, tau, force_dc, all_active,
                                                                  active);
-    state_kernel<<<ncta, CLS_NT, 0, st>>>(g, active, transitions, states, chi, (int*)scratch, stats);
+    state_kernel<<<ncta, CLS_NT, 0, st>>>(g, active, transitions, states, chi, (int*)scratch, stats, nullptr, 0);
+    compact_kernel<<<ncta, CLS_NT, 0, st>>>(g, states, (const int*)scratch, ncta, list, count);
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
+}
+
+spdba_status launch_classify_from_scan(const Geom& g, const double* msq, int msq_is_square, double* gmax,
+                                       double threshold, int tau_rule, int exclude_dc, int force_dc, int transitions,
+                                       double* tau, uint8_t* active, uint8_t* states, uint8_t* chi, int32_t* list,
+                                       int32_t* count, void* scratch, DevStats* stats, cudaStream_t st) {
+    long long nb = g.blocks();
+    int ncta = (int)((nb + CLS_NT - 1) / CLS_NT);
+    active_tau_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(g, msq, msq_is_square, gmax, threshold, tau_rule,
+                                                                      exclude_dc, force_dc, tau, stats, active);
+    state_kernel<<<ncta, CLS_NT, 0, st>>>(g, active, transitions, states, chi, (int*)scratch, stats, gmax,
+                                          (int)g.runs());
     compact_kernel<<<ncta, CLS_NT, 0, st>>>(g, states, (const int*)scratch, ncta, list, count);
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;

@@ -23,6 +23,13 @@ size_t classify_scratch_bytes(long long nb);
 spdba_status launch_classify(const Geom& g, const double* msq, int msq_is_square, const double* tau, int force_dc,
                              int transitions, int all_active, uint8_t* active, uint8_t* states, uint8_t* chi,
                              int32_t* list, int32_t* count, void* scratch, DevStats* stats, cudaStream_t st);
+// Classification straight from an activity scan's maxima (gmax, 2 per run):
+// tau per run by launch_tau's rule, states, chi, list, counts; then gmax is
+// zeroed for the next scan.  Three launches.
+spdba_status launch_classify_from_scan(const Geom& g, const double* msq, int msq_is_square, double* gmax,
+                                       double threshold, int tau_rule, int exclude_dc, int force_dc, int transitions,
+                                       double* tau, uint8_t* active, uint8_t* states, uint8_t* chi, int32_t* list,
+                                       int32_t* count, void* scratch, DevStats* stats, cudaStream_t st);
 
 // Cahn-Hilliard update.  k2 tables: per axis (padded to 3 axes) |k_a|^2 in T.
 template <typename T> struct CHUpdateArgs {

@@ -31,10 +31,6 @@ template <typename T> __global__ void complex_real_part_kernel(const cx_t<T>* __
 __global__ void zero_strided_kernel(double* p, long long n, int stride) {
     for (long long i = threadIdx.x; i < n; i += blockDim.x) p[i * stride] = 0.0;
 }
-__global__ void zero_double_kernel(double* p, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = 0.0;
-}
 // per-run share of non-frozen blocks for one step (1 on all-active steps)
 __global__ void ratio_kernel(DevStats* stats, long long nruns, long long bpr, long long bmodes, int dense) {
     for (long long r = threadIdx.x; r < nruns; r += blockDim.x) {
@@ -267,6 +263,7 @@ template <typename T> static spdba_status group_buffers(spdba_plan* p, Group<T>&
     if ((s = r.alloc(&r.stats, sizeof(DevStats) * r.batch)) != SPDBA_OK) return s;
     SPDBA_CUDA(cudaMemsetAsync(r.c_hat, 0, sizeof(cx_t<T>) * tot, st));
     SPDBA_CUDA(cudaMemsetAsync(r.stats, 0, sizeof(DevStats) * r.batch, st));
+    SPDBA_CUDA(cudaMemsetAsync(r.gmax, 0, sizeof(double) * 2 * r.batch, st));
     SPDBA_CUDA(cudaMemsetAsync(r.states, SPDBA_ACTIVE, nb, st));
     SPDBA_CUDA(cudaMemsetAsync(r.chi, 0, nb, st));
     return SPDBA_OK;
@@ -455,19 +452,17 @@ template <typename T> static spdba_status group_assess(spdba_plan* p, Group<T>& 
     spdba_status s;
     ProfScope ps(p, K_ASSESS, (double)sizeof(cx_t<T>) * (double)(r.batch * r.n));
     const bool ch = p->opt.model == SPDBA_MODEL_CH;
-    zero_double_kernel<<<1, 256, 0, st>>>(r.gmax, 2 * r.batch);
+    // gmax is zero here: it starts zeroed and every classification zeroes it after use
     double* sumsq = p->opt.measure == SPDBA_MEASURE_ENERGY ? r.sumsq : nullptr;
     const Geom& ga = r.long_nls ? r.gT : r.g;   // same block numbering in both orders
     if ((s = launch_block_activity<T>(ga, r.c_hat, r.maxsq, sumsq, r.gmax, st)) != SPDBA_OK) return s;
-    if ((s = launch_tau(r.gmax, (int)r.batch, p->threshold, p->opt.tau_rule, ch ? 1 : 0, r.tau, r.stats, st)) !=
-        SPDBA_OK)
-        return s;
     const double* msq = sumsq ? r.sumsq : r.maxsq;
     const int force_dc = ch ? p->opt.force_dc : 0;
-    if ((s = launch_classify(r.g, msq, 1, r.tau, force_dc, p->opt.transitions, 0, r.active, r.states, r.chi, r.list,
-                             r.count, r.scratch, r.stats, st)) != SPDBA_OK)
+    if ((s = launch_classify_from_scan(r.g, msq, 1, r.gmax, p->threshold, p->opt.tau_rule, ch ? 1 : 0, force_dc,
+                                       p->opt.transitions, r.tau, r.active, r.states, r.chi, r.list, r.count,
+                                       r.scratch, r.stats, st)) != SPDBA_OK)
         return s;
-    p->launches += 7;
+    p->launches += 4;
     r.assessed = true;
     return SPDBA_OK;
 }
@@ -811,15 +806,19 @@ template <typename T> static bool segment_ready(spdba_plan* p) {
     if (p->pred) return false;   // judge/prediction alternate: the launch sequence varies
     for (auto& g : groups<T>(p)) {
         if (g->step % p->reassess != 0) return false;
-        for (int64_t s = g->step; s < g->step + p->reassess; ++s)
+        for (int64_t s = g->step; s < g->step + p->reassess; ++s) {
             if (all_active_step(p, s)) return false;
+            // a sampled profile records events on its steps: those run directly
+            if (p->prof && s % p->prof_every == 0) return false;
+        }
     }
     return true;
 }
 
 template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
-    // graphs need a capturable (non-legacy) stream; profiling records events per kernel
-    if (!p->opt.use_graph || p->prof || p->st == 0) return direct_steps<T>(p, n);
+    // graphs need a capturable (non-legacy) stream; a profile of every step records
+    // events per kernel (a sampled one keeps graphs for unsampled segments)
+    if (!p->opt.use_graph || (p->prof && p->prof_every <= 1) || p->st == 0) return direct_steps<T>(p, n);
     const int R = p->reassess;
     int64_t i = 0;
     while (i < n) {
