@@ -36,10 +36,10 @@ spdba_status make_geom_batched(Geom* g, int ndim, const int64_t* dims, const int
 }
 
 // ------------------------------------------------------------------ activity
-// One warp per block.  The block max of |q|^2 is exact in FP64: the FP32
-// screen max(|re|, |im|) (screen_abs) selects the few modes that can hold the
-// max, and only those are evaluated exactly (re*re + im*im in FP64, the
-// oracle's formula), so a mode that is skipped cannot be the max.  Non-negative doubles order like
+// One warp per block.  The block max of |q|^2 is exact in FP64: FP32 screens
+// (screen_sq, screen_abs below) select the few modes that can hold the max, and
+// only those are evaluated exactly (re*re + im*im in FP64, the oracle's
+// formula), so a mode that is skipped cannot be the max.  Non-negative doubles order like
 // their bit patterns, so the warp max is two 32-bit integer reductions
 // (high word, then low word among the lanes holding the high maximum) and
 // costs no FP64 instruction.  The ENERGY sum is accumulated per lane in FP64.
@@ -52,15 +52,21 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
-// Screen of a mode: s = max(|re|, |im|), exact in FP32 (no squaring, so no
-// underflow).  |q|^2 lies in [s^2, 2 s^2], so a mode with s below s_max / sqrt(2)
-// cannot hold the block's largest |q|^2 in FP64 (nor exceed a tie with it), and
-// s = 0 means q = 0 exactly.  The cut uses 0.7071067 < 1/sqrt(2) by more than
-// the product's rounding; a block whose screens are all 0 has no candidate and
-// max 0.
+// Screens of a mode.  p32 = fma(re, re, im * im) is within 2^-22 of |q|^2 when
+// |q|^2 is a normal FP32 number, so below a screen max pm >= 2^-100 a mode
+// under (1 - 2^-20) pm cannot hold the block's largest |q|^2 (any mode whose
+// |q|^2 is below the normal range lies far under pm too).  When pm < 2^-100 the
+// exact s = max(|re|, |im|) decides instead: |q|^2 lies in [s^2, 2 s^2], so a
+// mode below s_max / sqrt(2) (the cut 0.7071067 leaves room for the product's
+// rounding) cannot hold the max, and s_max = 0 means the modes are exactly 0.
+__device__ __forceinline__ float screen_sq(float2 q) { return fmaf(q.x, q.x, q.y * q.y); }
 __device__ __forceinline__ float screen_abs(float2 q) { return fmaxf(fabsf(q.x), fabsf(q.y)); }
-__device__ __forceinline__ float screen_cut(float smax) {
-    return smax > 0.f ? smax * 0.7071067f : __int_as_float(0x7f800000);   // +inf: no candidate
+constexpr float kScreenTiny = 7.8886090522101181e-31f;   // 2^-100
+__device__ __forceinline__ float screen_cut_sq(float pm) {
+    return pm >= kScreenTiny ? pm * (1.0f - 9.5367431640625e-07f) : __int_as_float(0x7f800000);
+}
+__device__ __forceinline__ float screen_cut_abs(float pm, float sm) {
+    return (pm < kScreenTiny && sm > 0.f) ? sm * 0.7071067f : __int_as_float(0x7f800000);
 }
 
 // exact FP64 |q|^2 for the modes of `mask` (a data-dependent loop, so the FP64
@@ -124,8 +130,8 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
             }
             float2 v[2 * K2];
             unsigned dcmask = 0;
-            float lmax = 0.f, lmaxnd = 0.f;
-            float p32[2 * K2];
+            float lmax = 0.f, lmaxnd = 0.f, smax = 0.f, smaxnd = 0.f;
+            float p32[2 * K2], s32[2 * K2];
 #pragma unroll
             for (int k = 0; k < K2; ++k) {
                 v[2 * k] = make_float2(w[k].x, w[k].y);
@@ -135,18 +141,26 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
             }
 #pragma unroll
             for (int k = 0; k < 2 * K2; ++k) {
-                p32[k] = screen_abs(v[k]);
+                p32[k] = screen_sq(v[k]);
+                s32[k] = screen_abs(v[k]);
                 lmax = fmaxf(lmax, p32[k]);
-                if (!((dcmask >> k) & 1u)) lmaxnd = fmaxf(lmaxnd, p32[k]);
+                smax = fmaxf(smax, s32[k]);
+                if (!((dcmask >> k) & 1u)) {
+                    lmaxnd = fmaxf(lmaxnd, p32[k]);
+                    smaxnd = fmaxf(smaxnd, s32[k]);
+                }
                 if (ENERGY) sm += mode_sq(v[k]);
             }
-            const float cut = screen_cut(warp_max_nonneg_f(lmax));
-            const float cutnd = screen_cut(warp_max_nonneg_f(lmaxnd));
+            const float pm = warp_max_nonneg_f(lmax), pmnd = warp_max_nonneg_f(lmaxnd);
+            const float cut = screen_cut_sq(pm), cutnd = screen_cut_sq(pmnd);
+            const float cuts = screen_cut_abs(pm, warp_max_nonneg_f(smax));
+            const float cutsnd = screen_cut_abs(pmnd, warp_max_nonneg_f(smaxnd));
             unsigned mask = 0;
 #pragma unroll
             for (int k = 0; k < 2 * K2; ++k) {
                 const bool isdc = (dcmask >> k) & 1u;
-                if (p32[k] >= cut || (!isdc && p32[k] >= cutnd)) mask |= 1u << k;
+                if (p32[k] >= cut || s32[k] >= cuts || (!isdc && (p32[k] >= cutnd || s32[k] >= cutsnd)))
+                    mask |= 1u << k;
             }
             exact_candidates<2 * K2>(v, mask, dcmask, mx, mxnd);
         }
@@ -179,9 +193,9 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
 // one mode pair column 2u, so it stays in one block bx = 2u / B2 throughout,
 // shared with the G = B2 / 2 neighbouring lanes of its row.  Per chunk of 16
 // modes a lane forms the FP32 screens, the G lanes agree (shuffles) on the
-// running screen max of their block, and only modes that pass screen_cut are
-// evaluated in FP64 -- a few per block, so the slow FP64 pipe stays idle.  The
-// row groups combine through shared memory at the end.
+// running screen maxima of their block, and only modes that pass the cuts are
+// evaluated in FP64 -- about one per block and chunk, so the slow FP64 pipe
+// stays idle.  The row groups combine through shared memory at the end.
 constexpr int ROWACT_NT = 256;
 __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, const float2* __restrict__ q,
                                                                          double* __restrict__ maxsq,
@@ -201,7 +215,7 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
     const long long run = blk0 / bpr;
     const long long dc = run * g.fmodes();
     const long long rowbase = ((long long)b0 * B0 * g.n[1] + (long long)b1 * B1) * n2 + 2 * u;
-    float pm = 0.f, pmnd = 0.f;                            // the block's running screen maxima
+    float pm = 0.f, pmnd = 0.f, psm = 0.f, psmnd = 0.f;   // the block's running screen maxima
     double mx = 0.0, mxnd = 0.0;
     constexpr int U = 8;
     for (int r0 = rho; rho < rpi && r0 < rows; r0 += U * rpi) {
@@ -219,9 +233,9 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
             }
         }
         float2 v[2 * U];
-        float p32[2 * U];
+        float p32[2 * U], s32[2 * U];
         unsigned dcmask = 0;
-        float lmax = 0.f, lmaxnd = 0.f;
+        float lmax = 0.f, lmaxnd = 0.f, lsmax = 0.f, lsmaxnd = 0.f;
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             v[2 * k] = make_float2(w[k].x, w[k].y);
@@ -231,23 +245,33 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
         }
 #pragma unroll
         for (int k = 0; k < 2 * U; ++k) {
-            p32[k] = screen_abs(v[k]);
+            p32[k] = screen_sq(v[k]);
+            s32[k] = screen_abs(v[k]);
             lmax = fmaxf(lmax, p32[k]);
-            if (!((dcmask >> k) & 1u)) lmaxnd = fmaxf(lmaxnd, p32[k]);
+            lsmax = fmaxf(lsmax, s32[k]);
+            if (!((dcmask >> k) & 1u)) {
+                lmaxnd = fmaxf(lmaxnd, p32[k]);
+                lsmaxnd = fmaxf(lsmaxnd, s32[k]);
+            }
         }
         for (int o = G >> 1; o > 0; o >>= 1) {
             lmax = fmaxf(lmax, __shfl_xor_sync(gmask, lmax, o));
             lmaxnd = fmaxf(lmaxnd, __shfl_xor_sync(gmask, lmaxnd, o));
+            lsmax = fmaxf(lsmax, __shfl_xor_sync(gmask, lsmax, o));
+            lsmaxnd = fmaxf(lsmaxnd, __shfl_xor_sync(gmask, lsmaxnd, o));
         }
         pm = fmaxf(pm, lmax);
         pmnd = fmaxf(pmnd, lmaxnd);
-        const float cut = screen_cut(pm);
-        const float cutnd = screen_cut(pmnd);
+        psm = fmaxf(psm, lsmax);
+        psmnd = fmaxf(psmnd, lsmaxnd);
+        const float cut = screen_cut_sq(pm), cutnd = screen_cut_sq(pmnd);
+        const float cuts = screen_cut_abs(pm, psm), cutsnd = screen_cut_abs(pmnd, psmnd);
         unsigned mask = 0;
 #pragma unroll
         for (int k = 0; k < 2 * U; ++k) {
             const bool isdc = (dcmask >> k) & 1u;
-            if (p32[k] >= cut || (!isdc && p32[k] >= cutnd)) mask |= 1u << k;
+            if (p32[k] >= cut || s32[k] >= cuts || (!isdc && (p32[k] >= cutnd || s32[k] >= cutsnd)))
+                mask |= 1u << k;
         }
         exact_candidates<2 * U>(v, mask, dcmask, mx, mxnd);
     }
