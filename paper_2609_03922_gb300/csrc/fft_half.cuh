@@ -24,8 +24,20 @@ namespace spdba {
 // direct element c_hat(kz, ky, kx) (buffer A) and the mirror element
 // c_hat(-kz, -ky, -kx) (buffer B, loaded at index j).  Padding pencils
 // (kx > N2/2) are zero.
+// Layout of the mirror tile: pencil p at slot P - p of rows of P + 2 slots.
+// Mirror columns N2 - kx descend as p rises, so an odd pencil p whose kx is odd
+// copies the 16-byte unit (N2 - kx - 1, N2 - kx) = (pencil p + 1, pencil p)
+// into slots (P - p - 1, P - p); pencil 0 copies its own column and a spare one
+// into slots (P, P + 1).  Slot 0 (reached from p = P - 1) and slot P + 1 hold
+// spares only; every other pencil copies its own column.
+template <int L, int P> struct MirLay {
+    static_assert(P % 2 == 0, "16-byte units need an even pencil count");
+    static constexpr int SIZE = L * (P + 2);
+    static __device__ __forceinline__ int idx(int p, int j) { return j * (P + 2) + (P - p); }
+};
+
 template <typename T, int L, int P, int NT, class LY>
-__device__ __forceinline__ void issue_herm(cx_t<T>* sm, const PassParams<T>& a, long long q0, bool mirror) {
+__device__ __forceinline__ void issue_herm(cx_t<T>* sm, const PassParams<T>& a, long long q0) {
     using C = cx_t<T>;
     const HalfGeo& h = a.hg;
     const int M = h.N2 >> 1;
@@ -38,33 +50,63 @@ __device__ __forceinline__ void issue_herm(cx_t<T>* sm, const PassParams<T>& a, 
         for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) sm[LY::idx(p, j)] = mk<C>((T)0, (T)0);
         return;
     }
-    if (!mirror) {
-        const C* src = a.in + ((long long)ky * h.N2 + kx);
-        // pencil pairs (p, p + 1) of one row: one 16-byte copy by the even pencil
-        const bool pair = (p & 1) == 0 && kx + 1 <= M && (kx & 1) == 0;
-        const bool covered = (p & 1) == 1 && kx >= 1 && ((kx - 1) & 1) == 0;   // copied by pencil p - 1
-        if (pair) {
+    const C* src = a.in + ((long long)ky * h.N2 + kx);
+    // pencil pairs (p, p + 1), p even, of one row: one 16-byte copy by the even pencil
+    const bool pair = (p & 1) == 0 && kx + 1 <= M && (kx & 1) == 0;
+    const bool covered = (p & 1) == 1 && kx >= 1 && ((kx - 1) & 1) == 0;   // copied by pencil p - 1
+    if (pair) {
 #pragma unroll 4
-            for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) cp_async16(sm + LY::idx(p, j), src + j * plane);
-        } else if (!covered) {
+        for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) cp_async16(sm + LY::idx(p, j), src + j * plane);
+    } else if (!covered) {
 #pragma unroll 4
-            for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) cp_async8(sm + LY::idx(p, j), src + j * plane);
-        }
-    } else {
-        const int my = ky == 0 ? 0 : h.N1 - ky, mx = kx == 0 ? 0 : h.N2 - kx;
-        const C* src = a.in + ((long long)my * h.N2 + mx);
+        for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) cp_async8(sm + LY::idx(p, j), src + j * plane);
+    }
+}
+
+// Mirror tile: element (p, j) = c_hat(-j, -ky, -kx) of pencil p = (ky, kx).
+// A tile may cross an x row, so pairing is decided per pencil: a 16-byte copy
+// needs an odd p (aligned slot) and an odd kx (aligned column), and pencil
+// p + 1 must be the next pencil of the same row and not padding, or absent.
+template <typename T, int L, int P, int NT>
+__device__ __forceinline__ void issue_herm_mirror(cx_t<T>* smb, const PassParams<T>& a, long long q0) {
+    using C = cx_t<T>;
+    using ML = MirLay<L, P>;
+    const HalfGeo& h = a.hg;
+    const int M = h.N2 >> 1;
+    const int p = (int)(threadIdx.x % P);
+    const int q = (int)q0 + p;
+    const int ky = (int)h.fd_NHP.div((uint32_t)q), kx = q - ky * h.NHP;
+    const long long plane = (long long)h.N1 * h.N2;
+    if (kx > M) {   // never reached by a neighbour's copy: that needs kx <= M here
+        for (int j = (int)(threadIdx.x / P); j < L; j += NT / P) smb[ML::idx(p, j)] = mk<C>((T)0, (T)0);
+        return;
+    }
+    const int c = kx == 0 ? 0 : h.N2 - kx;   // this pencil's mirror column
+    const bool odd_p = (p & 1) != 0, odd_k = (kx & 1) != 0;
+    const C* src = a.in + (long long)(ky == 0 ? 0 : h.N1 - ky) * h.N2;
+    if (odd_p && odd_k && (p + 1 == P || kx + 1 <= M)) {
 #pragma unroll 4
         for (int j = (int)(threadIdx.x / P); j < L; j += NT / P)
-            cp_async8(sm + LY::idx(p, j), src + (j == 0 ? 0 : L - j) * plane);
+            cp_async16(smb + ML::idx(p + 1, j), src + (c - 1) + (j == 0 ? 0 : L - j) * plane);
+    } else if (p == 0 && (c & 1) == 0) {
+#pragma unroll 4
+        for (int j = (int)(threadIdx.x / P); j < L; j += NT / P)
+            cp_async16(smb + ML::idx(0, j), src + c + (j == 0 ? 0 : L - j) * plane);
+    } else if (!odd_p && p >= 2 && !odd_k && kx >= 2) {
+        return;   // copied by pencil p - 1 (odd p - 1, odd kx - 1, kx <= M)
+    } else {
+#pragma unroll 4
+        for (int j = (int)(threadIdx.x / P); j < L; j += NT / P)
+            cp_async8(smb + ML::idx(p, j), src + c + (j == 0 ? 0 : L - j) * plane);
     }
 }
 
 // (direct + conj(mirror)) / 2 of element m of pencil p
-template <typename T, class LY> struct HermIn {
+template <typename T, int L, int P, class LY> struct HermIn {
     const cx_t<T>* a;
     const cx_t<T>* b;
     __device__ __forceinline__ cx_t<T> operator()(int p, int m) const {
-        const cx_t<T> x = a[LY::idx(p, m)], y = b[LY::idx(p, m)];
+        const cx_t<T> x = a[LY::idx(p, m)], y = b[MirLay<L, P>::idx(p, m)];
         return mk<cx_t<T>>((T)0.5 * (x.x + y.x), (T)0.5 * (x.y - y.y));
     }
 };
@@ -80,14 +122,14 @@ __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
     const long long ntiles = (a.O * a.I) / P;
     long long t = blockIdx.x;
     if (t < ntiles) {
-        issue_herm<T, L, P, NT, LY>(smA0, a, t * P, false);
-        issue_herm<T, L, P, NT, LY>(smB, a, t * P, true);
+        issue_herm<T, L, P, NT, LY>(smA0, a, t * P);
+        issue_herm_mirror<T, L, P, NT>(smB, a, t * P);
     }
     cp_async_commit();
     int buf = 0;
     while (t < ntiles) {
         const long long tn = t + gridDim.x;
-        if (tn < ntiles) issue_herm<T, L, P, NT, LY>(buf ? smA0 : smA1, a, tn * P, false);
+        if (tn < ntiles) issue_herm<T, L, P, NT, LY>(buf ? smA0 : smA1, a, tn * P);
         cp_async_commit();
         cp_async_wait<1>();   // the direct and mirror tiles of t have landed
         __syncthreads();
@@ -95,10 +137,10 @@ __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
         // the first stage reads (direct + conj(mirror)) / 2; the stage's barrier
         // between its reads and writes frees the mirror buffer
         PlainOut<T, L> out(a, t * P);
-        HermIn<T, LY> in{sm, smB};
+        HermIn<T, L, P, LY> in{sm, smB};
         stockham_stage_in<T, L, P, NT, +1, 1, radix_at<L>(0), LY>(sm, a.tw, in);
         // the mirror tile of the next tile streams in during the rest of the transform
-        if (tn < ntiles) issue_herm<T, L, P, NT, LY>(smB, a, tn * P, true);
+        if (tn < ntiles) issue_herm_mirror<T, L, P, NT>(smB, a, tn * P);
         cp_async_commit();
         run_stage_range<T, L, P, NT, +1, LY, 1, NSTAGES<L>::value - 1>(sm, a.tw);
         stockham_stage_out<T, L, P, NT, +1, ns_at<L>(NSTAGES<L>::value - 1), radix_at<L>(NSTAGES<L>::value - 1), LY>(

@@ -22,7 +22,7 @@ template <int L> static bool pick_z(int mode, KernelInfo* ki) {
     switch (mode) {
         case PASS_HERM_INV:
             ki->func = (const void*)fft_herm_inv_kernel<float, L, P, NT>;
-            ki->smem = 3 * tile;
+            ki->smem = 2 * tile + MirLay<L, P>::SIZE * (int)sizeof(C);
             return true;
         case PASS_MIRROR:
             ki->func = (const void*)fft_pass_pipe_kernel<float, L, P, NT, -1, PASS_MIRROR, true>;
