@@ -4,6 +4,7 @@
 #include <stdio.h>
 
 #include <mutex>
+#include <map>
 #include <set>
 
 #include <algorithm>
@@ -78,17 +79,19 @@ template <typename T> void TwiddleCache<T>::release() {
 
 // ------------------------------------------------------------------ passes
 static std::mutex g_attr_mu;
-static std::set<const void*> g_attr_done;
-
+static std::map<const void*, int> g_attr_smem;   // dynamic shared-memory limit set per kernel
+// Raises a kernel's dynamic shared-memory limit to `smem` (the size of some
+// kernels depends on the shape, so a later plan may need more than an earlier one).
 static spdba_status ensure_smem_attr(const void* f, int smem, bool max_carveout) {
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (g_attr_done.count(f)) return SPDBA_OK;
+    auto it = g_attr_smem.find(f);
+    if (it != g_attr_smem.end() && it->second >= smem) return SPDBA_OK;
     // always raise the dynamic limit: some kernels also carry static shared memory
     SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // pipelined tiles stream through shared memory only; give them the whole
     // carveout so that the compiled CTAs per SM fit
     if (max_carveout) SPDBA_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    g_attr_done.insert(f);
+    g_attr_smem[f] = smem;
     return SPDBA_OK;
 }
 
@@ -261,8 +264,11 @@ spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, Twidd
     const bool rows = mode == PASS_NL_HALF;
     const int64_t L = rows ? hg.N2 : hg.N0;
     KernelInfo ki;
-    if (!get_half_kernel(L, mode, hg.NHP, &ki))
+    if (!get_half_kernel(L, mode, hg.NHP, &ki)) {
+        // no message for the paired pass: the caller then takes the unpaired one
+        if (mode == PASS_PAIR_MIRROR) return SPDBA_ERR_UNSUPPORTED;
         return fail(SPDBA_ERR_UNSUPPORTED, "no half-spectrum kernel for length %lld (mode %d)", (long long)L, mode);
+    }
     Pass<float> ps;
     PassParams<float>& a = ps.p;
     if (rows) {
@@ -275,7 +281,20 @@ spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, Twidd
         a.osI = 1;
         a.osJ = a.I;
     }
-    if ((a.O * a.I) % ki.P != 0) return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum tiles do not divide the pencils");
+    const bool pair = mode == PASS_PAIR_MIRROR;
+    long long ntiles = a.O * a.I / ki.P;
+    if (pair) {
+        // tiles of P x frequencies below N2/2 within one half row, then the
+        // column N2/2 in tiles of P rows; 16-byte pencil pairs need an even row pitch
+        const long long M = hg.N2 / 2;
+        if (M % ki.P != 0 || hg.N1 % ki.P != 0 || hg.NHP % 2 != 0)
+            return SPDBA_ERR_UNSUPPORTED;
+        a.I = (long long)hg.N1 * (M + 1);
+        a.osJ = (long long)hg.N1 * hg.N2;
+        ntiles = a.I / ki.P;
+    } else if ((a.O * a.I) % ki.P != 0) {
+        return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum tiles do not divide the pencils");
+    }
     spdba_status s = ensure_smem_attr(ki.func, ki.smem, true);
     if (s != SPDBA_OK) return s;
     int per_sm = 0, nsm = 0, dev = 0;
@@ -283,7 +302,6 @@ spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, Twidd
     SPDBA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     SPDBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.func, ki.NT, ki.smem));
     if (per_sm < 1) return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum kernel does not fit an SM");
-    const long long ntiles = a.O * a.I / ki.P;
     ps.grid = std::min<long long>(ntiles, (long long)per_sm * nsm);
     ps.func = ki.func;
     ps.nt = ki.NT;

@@ -106,7 +106,7 @@ template <typename T> struct CHFuse {
 // holds x frequencies 0 .. N2/2 in rows of NHP >= N2/2 + 1 entries (the rest 0).
 struct HalfGeo {
     int N0 = 1, N1 = 1, N2 = 2, NHP = 2;
-    FastDiv fd_N2, fd_NHP;
+    FastDiv fd_N2, fd_NHP, fd_M;   // fd_M: division by N2 / 2
 };
 
 template <typename T> struct PassParams {
@@ -784,6 +784,8 @@ enum PassMode : int {
     PASS_NL_HALF = 4,    // x rows: half spectrum -> real -> g = c^3 - c -> half spectrum
     PASS_MIRROR = 5,     // forward z-transform of the half array, stored for every x frequency
     PASS_UPD_HALF = 6,   // forward z-transform of the half array, then the CH update of c_hat
+    // PASS_MIRROR with one transform per half pencil for x frequencies kx and N2 - kx
+    PASS_PAIR_MIRROR = 7,
 };
 constexpr bool is_update_mode(int m) { return m == PASS_CH_UPDATE || m == PASS_UPD_HALF; }
 constexpr bool reads_half(int m) { return m == PASS_MIRROR || m == PASS_UPD_HALF; }

@@ -273,4 +273,140 @@ __global__ void __launch_bounds__(NT, L == 384 ? 1 : 512 / NT) fft_nl_half_kerne
     cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------- z forward, paired
+// The forward z-transform of half pencil (ky, kx) gives D(kz, ky, kx) and, by
+// D(z, -ky, -kx) = conj(D(z, ky, kx)), also D(-kz, -ky, N2 - kx) =
+// conj(D(kz, ky, kx)): one transform serves both x frequencies kx and N2 - kx
+// (PASS_PAIR_MIRROR: the full z-transform stored for the separate update).
+// Tiles of P pencils kx = x0 .. x0 + P - 1 (x0 < N2/2) of one half row ky emit
+// both; the column kx = N2/2 (its own mirror) runs as tiles of P pencils along
+// y after them.  Requires (N2/2) % P == 0, N1 % P == 0 and an even NHP.
+
+// Row-major tile (element j of pencil p at j * P + p); with P < 16 every 16
+// rows are followed by P pad slots, so that the rows j R + r that a first
+// stage's lanes write fall on alternating halves of the banks.
+template <int L, int P> struct LayoutBP {
+    static constexpr int PAD = P < 16 ? P : 0;
+    static constexpr int SIZE = P * L + PAD * (L / 16);
+    static constexpr bool PMAP = true;
+    static __device__ __forceinline__ int idx(int p, int j) { return j * P + p + PAD * (j >> 4); }
+};
+
+// Half-array tile of tile t: paired tiles as 16-byte pencil pairs of one row,
+// column tiles (kx = N2/2, P rows of y) element by element.
+template <typename T, int L, int P, int NT, class LY>
+__device__ __forceinline__ void issue_pair_half(cx_t<T>* sm, const PassParams<T>& a, int t, int ntm) {
+    const HalfGeo& h = a.hg;
+    const int M = h.N2 >> 1;
+    const long long zs = (long long)h.N1 * h.NHP;
+    if (t < ntm) {
+        const int q0 = t * P;
+        const int ky = (int)h.fd_M.div((uint32_t)q0), x0 = q0 - ky * M;
+        const cx_t<T>* base = a.in + ((long long)ky * h.NHP + x0);
+        constexpr int UNITS = P * L / 2;
+#pragma unroll 4
+        for (int w = threadIdx.x; w < UNITS; w += NT) {
+            const int j = w / (P / 2), pp = (w % (P / 2)) * 2;
+            cp_async16(sm + LY::idx(pp, j), base + (j * zs + pp));
+        }
+    } else {
+        const int ky0 = (t - ntm) * P;
+        const cx_t<T>* base = a.in + ((long long)ky0 * h.NHP + M);
+        constexpr int UNITS = P * L;
+#pragma unroll 4
+        for (int w = threadIdx.x; w < UNITS; w += NT) {
+            const int j = w / P, p = w % P;
+            cp_async8(sm + LY::idx(p, j), base + (j * zs + (long long)p * h.NHP));
+        }
+    }
+}
+
+// Outputs of a paired tile's last stage stored as the full z-transform:
+// D(kz, ky, x0 + p) and conj(D) at (-kz, -ky, N2 - x0 - p).
+template <typename T, int L, int P, int R> struct PairPlainOut {
+    using C = cx_t<T>;
+    static constexpr bool SYNC = false;
+    static constexpr int NS = L / R;
+    C* pd;
+    C* pm;
+    bool has_m;
+    int osJ;
+    __device__ __forceinline__ PairPlainOut(const PassParams<T>& a, int t) {
+        const HalfGeo& h = a.hg;
+        const int q0 = t * P;
+        const int ky = (int)h.fd_M.div((uint32_t)q0), x0 = q0 - ky * (h.N2 >> 1);
+        const int my = ky == 0 ? 0 : h.N1 - ky;
+        const int xd = x0 + (int)(threadIdx.x % P);
+        has_m = xd != 0;   // column 0 is its own mirror
+        pd = a.out + ((long long)ky * h.N2 + xd);
+        pm = a.out + ((long long)my * h.N2 + (has_m ? h.N2 - xd : 0));
+        osJ = h.N1 * h.N2;
+    }
+    __device__ __forceinline__ void pre() {}
+    __device__ __forceinline__ void begin(int, int, int) {}
+    __device__ __forceinline__ void emit(int, int, int j, C (&v)[R]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int m = j + r * NS;
+            pd[m * osJ] = v[r];
+            if (has_m) pm[(m == 0 ? 0 : L - m) * osJ] = mk<C>(v[r].x, -v[r].y);
+        }
+    }
+};
+
+// Column kx = N2/2 (tile of pencils ky0 .. ky0 + P - 1, transform in shared
+// memory): plain store of every element.
+template <typename T, int L, int P, int NT, class LY>
+__device__ __forceinline__ void pair_column(const cx_t<T>* sm, const PassParams<T>& a, int ky0) {
+    const HalfGeo& h = a.hg;
+    const int M = h.N2 >> 1;
+    const long long plane = (long long)h.N1 * h.N2;
+    for (int w = threadIdx.x; w < P * L; w += NT) {
+        const int j = w / P, p = w % P;
+        a.out[(long long)j * plane + (long long)(ky0 + p) * h.N2 + M] = sm[LY::idx(p, j)];
+    }
+}
+
+// Persistent CTAs walk the tiles t = blockIdx.x + k gridDim.x with a three-deep
+// cp.async pipeline: the tiles two steps ahead stream in while one is
+// transformed (a tile's own compute is too short to hide one load).
+constexpr int kPairBufs = 3;
+template <typename T, int L, int P, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) fft_pair_kernel(PassParams<T> a) {
+    using C = cx_t<T>;
+    using LY = LayoutBP<L, P>;
+    static_assert(NT % P == 0 && NT % (P / 2) == 0, "each thread keeps one pencil");
+    static_assert(Radices_last<L>::value != 3, "the last stage emits directly");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* const smb = reinterpret_cast<C*>(smem_raw);
+    const int ntm = a.hg.N1 * (a.hg.N2 >> 1) / P, nt = ntm + a.hg.N1 / P;
+    const int G = (int)gridDim.x;
+    const int t0 = (int)blockIdx.x;
+#pragma unroll
+    for (int k = 0; k < kPairBufs - 1; ++k) {
+        if (t0 + k * G < nt) issue_pair_half<T, L, P, NT, LY>(smb + k * LY::SIZE, a, t0 + k * G, ntm);
+        cp_async_commit();
+    }
+    int slot = 0;
+    for (int t = t0; t < nt; t += G) {
+        const int ta = t + (kPairBufs - 1) * G;   // the tile that streams in now
+        const int sa = slot == 0 ? kPairBufs - 1 : slot - 1;
+        if (ta < nt) issue_pair_half<T, L, P, NT, LY>(smb + sa * LY::SIZE, a, ta, ntm);
+        cp_async_commit();
+        cp_async_wait<kPairBufs - 1>();   // tile t (the oldest pending group) has landed
+        __syncthreads();
+        C* sm = smb + slot * LY::SIZE;
+        if (t < ntm) {
+            PairPlainOut<T, L, P, Radices_last<L>::value> out(a, t);
+            run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
+        } else {
+            run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
+            pair_column<T, L, P, NT, LY>(sm, a, (t - ntm) * P);
+        }
+        __syncthreads();   // buffer `slot` is refilled two tiles on
+        slot = slot == kPairBufs - 1 ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
+}
+
 }  // namespace spdba

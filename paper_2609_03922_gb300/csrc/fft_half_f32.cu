@@ -37,6 +37,22 @@ template <int L> static bool pick_z(int mode, KernelInfo* ki) {
     }
 }
 
+// pencils per tile and threads per CTA of the paired z forward pass (one
+// butterfly per thread in the radix-16 stages; three tile buffers)
+template <int L> struct PairTileP;
+template <> struct PairTileP<64> { static constexpr int P = 16, NT = 128; };
+template <> struct PairTileP<128> { static constexpr int P = 16, NT = 128; };
+template <> struct PairTileP<256> { static constexpr int P = 8, NT = 128; };
+template <int L> static bool pick_pair(KernelInfo* ki) {
+    constexpr int P = PairTileP<L>::P, NT = PairTileP<L>::NT;
+    ki->P = P;
+    ki->NT = NT;
+    ki->pipe = true;
+    ki->func = (const void*)fft_pair_kernel<float, L, P, NT>;
+    ki->smem = kPairBufs * LayoutBP<L, P>::SIZE * (int)sizeof(cx_t<float>);
+    return true;
+}
+
 // real rows per tile of the x pass (two rows per transform pencil)
 template <int N2> struct NlHalfRows { static constexpr int value = N2 <= 256 ? 4096 / N2 : 16; };
 
@@ -58,6 +74,14 @@ bool get_half_kernel(int64_t L, int mode, int nhp, KernelInfo* ki) {
             case 256: return pick_x<256>(nhp, ki);
             case 384: return pick_x<384>(nhp, ki);
             case 512: return pick_x<512>(nhp, ki);
+            default: return false;
+        }
+    }
+    if (mode == PASS_PAIR_MIRROR) {
+        switch (L) {
+            case 64: return pick_pair<64>(ki);
+            case 128: return pick_pair<128>(ki);
+            case 256: return pick_pair<256>(ki);
             default: return false;
         }
     }

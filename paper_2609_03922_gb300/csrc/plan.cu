@@ -284,13 +284,21 @@ static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* di
     hg.N0 = (int)N0; hg.N1 = (int)N1; hg.N2 = (int)N2; hg.NHP = (int)NHP;
     hg.fd_N2.init((uint32_t)N2);
     hg.fd_NHP.init((uint32_t)NHP);
+    hg.fd_M.init((uint32_t)M);
     TwiddleCache<float>& tw = p->tw32;
     Pass<float> hz, hy_inv, hnl, hy_fwd, hmir, hupd;
     spdba_status s;
     if ((s = make_half_pass(&hz, PASS_HERM_INV, hg, tw, st)) != SPDBA_OK) return s;
     if ((s = make_half_pass(&hnl, PASS_NL_HALF, hg, tw, st)) != SPDBA_OK) return s;
-    if ((s = make_half_pass(&hmir, PASS_MIRROR, hg, tw, st)) != SPDBA_OK) return s;
-    if (N2 % hmir.P != 0) return SPDBA_ERR_UNSUPPORTED;   // z tiles must stay within one x row
+    // z forward of the staged form: one transform per half pencil for kx and
+    // N2 - kx where the paired tiles fit, else one per full pencil (the fused
+    // update pass transforms every full pencil: with the update in the same
+    // kernel, pairing saved less than it cost)
+    const bool paired = make_half_pass(&hmir, PASS_PAIR_MIRROR, hg, tw, st) == SPDBA_OK;
+    if (!paired) {
+        if ((s = make_half_pass(&hmir, PASS_MIRROR, hg, tw, st)) != SPDBA_OK) return s;
+        if (N2 % hmir.P != 0) return SPDBA_ERR_UNSUPPORTED;   // z tiles must stay within one x row
+    }
     const int64_t dh[3] = {N0, N1, NHP};
     if ((s = make_axis_pass<float>(&hy_inv, 3, dh, 1, 1, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
     if ((s = make_axis_pass<float>(&hy_fwd, 3, dh, 1, 1, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;

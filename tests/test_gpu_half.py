@@ -77,3 +77,61 @@ def test_half_threshold_zero_equals_regular():
     b = _run(dims, 7, c0, half_spectrum=1, mode=0)
     assert np.array_equal(a[1], b[1])
     assert all(np.all(m == 2) for m in a[2].values())
+
+
+# Shapes for the z forward pass of the half form: one transform per half pencil
+# serving x frequencies kx and N2 - kx (z lengths 64, 128, 256, with one or
+# several tiles of the column N2/2), and z length 384, which takes one
+# transform per full pencil.
+SHAPES = [(64, 256, 64), (128, 256, 128), (256, 128, 256), (256, 256, 64), (384, 128, 128)]
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_half_shapes_have_half_kernels(dims):
+    """Every shape of this set runs in the half form (the autotuner offers it)."""
+    from paper_2609_03922_gb300 import spdba
+    plan = spdba.Plan(dims, (8, 8, 8), threshold=3e-3, reassess=10, precision=0, half_spectrum=1)
+    plan.set_field(np.zeros(dims, dtype=np.float32))
+    rep = plan.autotune(1)
+    plan.close()
+    assert any(c["half_spectrum"] == 1 for c in rep["candidates"])
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_half_shapes_against_oracle(dims):
+    """Three steps with reassessments at steps 0 and 2: the second assessment,
+    after the stiff damping of the high modes, mixes FROZEN, TRANSITION and
+    ACTIVE blocks.  Both GPU assessments against the oracle's classifier, the
+    field against the FP64 oracle advanced with the GPU's states."""
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 124)
+    from paper_2609_03922_gb300 import spdba
+    plan = spdba.Plan(dims, (8, 8, 8), threshold=0.1, reassess=2, precision=0, half_spectrum=1)
+    plan.set_field(np.ascontiguousarray(c0.astype(np.float32)))
+    plan.step(1)
+    masks = {0: plan.get_mask()}
+    plan.step(2)
+    masks[2] = plan.get_mask()
+    field = plan.get_field()
+    plan.close()
+    assert {0, 1, 2} <= set(np.unique(masks[2]).tolist())
+    cfg = O.CHConfig(dims, (8, 8, 8), threshold=0.1, reassess=2)
+    checked = []
+
+    def on_assess(n, ch, st, tau):
+        _, _, meas = O.assess_states(ch, cfg, exclude_dc=True)
+        checked.append(states_within_tie_band(masks[n], meas, tau, cfg)[0])
+        return masks[n]
+
+    ref_hat, _ = O.run_ch(c0.astype(np.float32).astype(np.float64), cfg, 3, on_assess=on_assess)
+    assert checked == [True, True]
+    assert O.rel_l2(field, O.ch_real_field(ref_hat)) <= 1e-5
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_half_shapes_match_full_transforms(dims):
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 125)
+    fh, sph, mh, _ = _run(dims, 8, c0, half_spectrum=1, threshold=0.1, reassess=2)
+    ff, spf, mf, _ = _run(dims, 8, c0, half_spectrum=0, threshold=0.1, reassess=2)
+    assert any(np.any(m == 0) for m in mh.values())
+    assert O.rel_l2(fh, ff) <= 2e-6
+    assert O.rel_l2(sph, spf) <= 2e-6
