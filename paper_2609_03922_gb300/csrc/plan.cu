@@ -130,9 +130,9 @@ template <typename T> struct Group {
 using namespace spdba;
 
 enum ProfKind { K_FFT_PASS = 0, K_FUSED_NL, K_UPDATE_DENSE, K_UPDATE_LIST, K_ASSESS, K_NLS_STEP, K_NLS_ROW, K_NLS_COL,
-                K_FFT_UPDATE, K_COUNT };
+                K_FFT_UPDATE, K_FFT_ZFWD, K_COUNT };
 static const char* kProfName[K_COUNT] = {"fft_pass", "fft_fused_nl", "update_dense", "update_list", "assess",
-                                         "nls_step", "nls_row", "nls_col", "fft_update"};
+                                         "nls_step", "nls_row", "nls_col", "fft_update", "fft_z_forward"};
 
 struct ProfRec {
     int kind;
@@ -543,9 +543,11 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
     }
     const int dense = !adaptive || all_active_step(p, r.step);
     if (r.use_half) {
-        // Hermitian half-spectrum form: z (from c_hat), y, x (nonlinearity), y, z (update)
+        // Hermitian half-spectrum form: z (from c_hat), y, x (nonlinearity), y, z (update).
+        // Profiled bytes are algorithmic: x frequencies 0 .. N2/2 of the half array
+        // (its padding columns excluded).
         const double full_b = sizeof(cx_t<T>) * (double)(r.batch * r.n);
-        const double half_b = sizeof(cx_t<T>) * (double)r.half_n;
+        const double half_b = full_b * (double)(r.g.n[2] / 2 + 1) / (double)r.g.n[2];
         {
             ProfScope pr(p, K_FFT_PASS, full_b + half_b);
             if ((s = launch_pass<T>(r.h_inv_z, r.c_hat, r.half, st)) != SPDBA_OK) return s;
@@ -579,7 +581,7 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
             return SPDBA_OK;
         }
         {
-            ProfScope pr(p, K_FFT_PASS, half_b + full_b);
+            ProfScope pr(p, K_FFT_ZFWD, half_b + full_b);
             if ((s = launch_pass<T>(r.h_mirror, r.half, r.work, st)) != SPDBA_OK) return s;
             p->launches += 1;
         }
