@@ -271,6 +271,7 @@ spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, Twidd
     }
     Pass<float> ps;
     PassParams<float>& a = ps.p;
+    a.fu = CHFuse<float>{};   // no states: the paired z forward then stores every mode
     if (rows) {
         a.O = hg.N0;
         a.I = hg.N1;

@@ -904,6 +904,8 @@ __device__ __forceinline__ void ch_update_tile_rows(const cx_t<T>* sm, const Pas
 // Per-tile table of the update: entry (bp, bx) = state | chi << 2 of the block
 // in block row bp of the pass axis and x-block bx0 + bx (bytes).
 constexpr int kUpdTable = 4096;
+// Capacity of each of the two state tables of a paired z tile (direct and mirror columns).
+constexpr int kPairTable = 1024;
 __host__ __device__ __forceinline__ int upd_table_cols(int P, int bx) { return (P + bx - 2) / bx + 1; }
 // The update pass stages c_hat in a third tile buffer for row-major tiles of
 // L <= 256 whose last stage emits directly (not the radix-3 tail of 192).

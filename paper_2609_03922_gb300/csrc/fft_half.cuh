@@ -321,26 +321,112 @@ __device__ __forceinline__ void issue_pair_half(cx_t<T>* sm, const PassParams<T>
     }
 }
 
+// Blocks of a paired tile (32-bit; every thread derives the same values):
+// x-blocks of the direct columns x0 .. x0 + P - 1 in row ky and of the mirror
+// columns N2 - x0 - P + 1 .. N2 - x0 (column N2 excluded: x0 = 0 has no mirror
+// of column 0) in row my.
+struct PairBlocks {
+    int bxd0, nbxd, bxm0, nbxm;
+    long long boffd, boffm;   // block ids of (z block row 0, first x-block) in rows ky and my
+    int bstride;              // block id step per z block row
+};
+template <typename T, int P>
+__device__ __forceinline__ PairBlocks pair_blocks(const PassParams<T>& a, int t) {
+    const HalfGeo& h = a.hg;
+    const CHFuse<T>& f = a.fu;
+    const Geom& g = f.g;
+    const int q0 = t * P;
+    const int ky = (int)h.fd_M.div((uint32_t)q0), x0 = q0 - ky * (h.N2 >> 1);
+    const int my = ky == 0 ? 0 : h.N1 - ky;
+    PairBlocks u;
+    u.bxd0 = (int)f.fd_b2.div((uint32_t)x0);
+    u.nbxd = (int)f.fd_b2.div((uint32_t)(x0 + P - 1)) - u.bxd0 + 1;
+    const int mlo = h.N2 - x0 - (P - 1), mhi = x0 == 0 ? h.N2 - 1 : h.N2 - x0;
+    u.bxm0 = (int)f.fd_b2.div((uint32_t)mlo);
+    u.nbxm = (int)f.fd_b2.div((uint32_t)mhi) - u.bxm0 + 1;
+    u.boffd = (long long)f.fd_b1.div((uint32_t)ky) * g.nb[2] + u.bxd0;
+    u.boffm = (long long)f.fd_b1.div((uint32_t)my) * g.nb[2] + u.bxm0;
+    u.bstride = (int)(g.nb[1] * g.nb[2]);
+    return u;
+}
+
+// With block states (masked): a paired tile is live when any block of its
+// direct or mirror columns is not FROZEN (warp-uniform); column tiles always.
+template <typename T, int P>
+__device__ __forceinline__ bool pair_live(const PassParams<T>& a, bool masked, int t, int ntm) {
+    if (!masked || t >= ntm) return true;
+    const PairBlocks u = pair_blocks<T, P>(a, t);
+    const int npass = (int)a.fu.g.nb[0];
+    const uint8_t* st = a.fu.states;
+    bool live = false;
+    for (int bp = threadIdx.x & 31; bp < npass && !live; bp += 32) {
+        const long long r = (long long)bp * u.bstride;
+        for (int bx = 0; bx < u.nbxd; ++bx) live |= st[u.boffd + r + bx] != SPDBA_FROZEN;
+        for (int bx = 0; bx < u.nbxm; ++bx) live |= st[u.boffm + r + bx] != SPDBA_FROZEN;
+    }
+    return __any_sync(0xffffffffu, live);
+}
+// next live tile of this CTA's sequence at or after t
+template <typename T, int P>
+__device__ __forceinline__ int pair_next(const PassParams<T>& a, bool masked, int t, int nt, int ntm) {
+    while (t < nt && !pair_live<T, P>(a, masked, t, ntm)) t += (int)gridDim.x;
+    return t;
+}
+
+// Per-tile state tables (masked): tabd[bp * nbxd + bx], tabm[bp * nbxm + bx]
+// for z block row bp.  Visible after the next barrier.
+template <typename T, int NT>
+__device__ __forceinline__ void pair_tables(uint8_t* tabd, uint8_t* tabm, const PassParams<T>& a,
+                                            const PairBlocks& u) {
+    const int npass = (int)a.fu.g.nb[0];
+    const uint8_t* st = a.fu.states;
+    for (int k = threadIdx.x; k < npass * u.nbxd; k += NT) {
+        const int bp = k / u.nbxd;
+        tabd[k] = st[u.boffd + (long long)bp * u.bstride + (k - bp * u.nbxd)];
+    }
+    for (int k = threadIdx.x; k < npass * u.nbxm; k += NT) {
+        const int bp = k / u.nbxm;
+        tabm[k] = st[u.boffm + (long long)bp * u.bstride + (k - bp * u.nbxm)];
+    }
+}
+
 // Outputs of a paired tile's last stage stored as the full z-transform:
-// D(kz, ky, x0 + p) and conj(D) at (-kz, -ky, N2 - x0 - p).
+// D(kz, ky, x0 + p) and conj(D) at (-kz, -ky, N2 - x0 - p); masked, only the
+// modes of non-FROZEN blocks (the staged update reads no others).
 template <typename T, int L, int P, int R> struct PairPlainOut {
     using C = cx_t<T>;
     static constexpr bool SYNC = false;
     static constexpr int NS = L / R;
     C* pd;
     C* pm;
-    bool has_m;
+    bool has_m, masked;
     int osJ;
-    __device__ __forceinline__ PairPlainOut(const PassParams<T>& a, int t) {
+    const uint8_t* tabd;
+    const uint8_t* tabm;
+    int nbxd, nbxm, bxsd, bxsm;
+    FastDiv fd_bp;
+    __device__ __forceinline__ PairPlainOut(const PassParams<T>& a, int t, bool masked_, const uint8_t* td,
+                                            const uint8_t* tm)
+        : masked(masked_), tabd(td), tabm(tm) {
         const HalfGeo& h = a.hg;
         const int q0 = t * P;
         const int ky = (int)h.fd_M.div((uint32_t)q0), x0 = q0 - ky * (h.N2 >> 1);
         const int my = ky == 0 ? 0 : h.N1 - ky;
         const int xd = x0 + (int)(threadIdx.x % P);
         has_m = xd != 0;   // column 0 is its own mirror
+        const int xm = has_m ? h.N2 - xd : 0;
         pd = a.out + ((long long)ky * h.N2 + xd);
-        pm = a.out + ((long long)my * h.N2 + (has_m ? h.N2 - xd : 0));
+        pm = a.out + ((long long)my * h.N2 + xm);
         osJ = h.N1 * h.N2;
+        if (masked) {
+            const PairBlocks u = pair_blocks<T, P>(a, t);
+            const CHFuse<T>& f = a.fu;
+            nbxd = u.nbxd;
+            nbxm = u.nbxm;
+            bxsd = (int)f.fd_b2.div((uint32_t)xd) - u.bxd0;
+            bxsm = (int)f.fd_b2.div((uint32_t)xm) - u.bxm0;
+            fd_bp = f.fd_bp;
+        }
     }
     __device__ __forceinline__ void pre() {}
     __device__ __forceinline__ void begin(int, int, int) {}
@@ -348,8 +434,12 @@ template <typename T, int L, int P, int R> struct PairPlainOut {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int m = j + r * NS;
-            pd[m * osJ] = v[r];
-            if (has_m) pm[(m == 0 ? 0 : L - m) * osJ] = mk<C>(v[r].x, -v[r].y);
+            if (!masked || tabd[(int)fd_bp.div((uint32_t)m) * nbxd + bxsd] != SPDBA_FROZEN) pd[m * osJ] = v[r];
+            if (has_m) {
+                const int mz = m == 0 ? 0 : L - m;
+                if (!masked || tabm[(int)fd_bp.div((uint32_t)mz) * nbxm + bxsm] != SPDBA_FROZEN)
+                    pm[mz * osJ] = mk<C>(v[r].x, -v[r].y);
+            }
         }
     }
 };
@@ -367,9 +457,10 @@ __device__ __forceinline__ void pair_column(const cx_t<T>* sm, const PassParams<
     }
 }
 
-// Persistent CTAs walk the tiles t = blockIdx.x + k gridDim.x with a three-deep
-// cp.async pipeline: the tiles two steps ahead stream in while one is
-// transformed (a tile's own compute is too short to hide one load).
+// Persistent CTAs walk the tiles t = blockIdx.x + k gridDim.x (masked: the
+// live ones) with a three-deep cp.async pipeline: the tile two steps ahead
+// streams in while one is transformed (a tile's own compute is too short to
+// hide one load).
 constexpr int kPairBufs = 3;
 template <typename T, int L, int P, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) fft_pair_kernel(PassParams<T> a) {
@@ -377,34 +468,40 @@ __global__ void __launch_bounds__(NT, 512 / NT) fft_pair_kernel(PassParams<T> a)
     using LY = LayoutBP<L, P>;
     static_assert(NT % P == 0 && NT % (P / 2) == 0, "each thread keeps one pencil");
     static_assert(Radices_last<L>::value != 3, "the last stage emits directly");
+    static_assert(kPairBufs == 3, "the loop keeps two tiles in flight");
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint8_t s_tab[2 * kPairTable];
     C* const smb = reinterpret_cast<C*>(smem_raw);
     const int ntm = a.hg.N1 * (a.hg.N2 >> 1) / P, nt = ntm + a.hg.N1 / P;
     const int G = (int)gridDim.x;
-    const int t0 = (int)blockIdx.x;
-#pragma unroll
-    for (int k = 0; k < kPairBufs - 1; ++k) {
-        if (t0 + k * G < nt) issue_pair_half<T, L, P, NT, LY>(smb + k * LY::SIZE, a, t0 + k * G, ntm);
-        cp_async_commit();
-    }
+    const bool masked = a.fu.states != nullptr && !a.fu.dense;
+    int t = pair_next<T, P>(a, masked, (int)blockIdx.x, nt, ntm);
+    if (t < nt) issue_pair_half<T, L, P, NT, LY>(smb, a, t, ntm);
+    cp_async_commit();
+    int t1 = t < nt ? pair_next<T, P>(a, masked, t + G, nt, ntm) : nt;
+    if (t1 < nt) issue_pair_half<T, L, P, NT, LY>(smb + LY::SIZE, a, t1, ntm);
+    cp_async_commit();
     int slot = 0;
-    for (int t = t0; t < nt; t += G) {
-        const int ta = t + (kPairBufs - 1) * G;   // the tile that streams in now
-        const int sa = slot == 0 ? kPairBufs - 1 : slot - 1;
-        if (ta < nt) issue_pair_half<T, L, P, NT, LY>(smb + sa * LY::SIZE, a, ta, ntm);
+    while (t < nt) {
+        const int t2 = t1 < nt ? pair_next<T, P>(a, masked, t1 + G, nt, ntm) : nt;
+        const int s2 = slot == 0 ? 2 : slot - 1;   // (slot + 2) mod 3: freed by the previous tile
+        if (t2 < nt) issue_pair_half<T, L, P, NT, LY>(smb + s2 * LY::SIZE, a, t2, ntm);
         cp_async_commit();
-        cp_async_wait<kPairBufs - 1>();   // tile t (the oldest pending group) has landed
+        if (masked && t < ntm) pair_tables<T, NT>(s_tab, s_tab + kPairTable, a, pair_blocks<T, P>(a, t));
+        cp_async_wait<2>();   // tile t (the oldest pending group) has landed
         __syncthreads();
         C* sm = smb + slot * LY::SIZE;
         if (t < ntm) {
-            PairPlainOut<T, L, P, Radices_last<L>::value> out(a, t);
+            PairPlainOut<T, L, P, Radices_last<L>::value> out(a, t, masked, s_tab, s_tab + kPairTable);
             run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
         } else {
             run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
             pair_column<T, L, P, NT, LY>(sm, a, (t - ntm) * P);
         }
-        __syncthreads();   // buffer `slot` is refilled two tiles on
-        slot = slot == kPairBufs - 1 ? 0 : slot + 1;
+        __syncthreads();   // buffer `slot` and the tables are free again
+        t = t1;
+        t1 = t2;
+        slot = slot == 2 ? 0 : slot + 1;
     }
     cp_async_wait<0>();
 }

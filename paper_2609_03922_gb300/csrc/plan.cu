@@ -269,6 +269,24 @@ template <typename T> static spdba_status group_buffers(spdba_plan* p, Group<T>&
     return SPDBA_OK;
 }
 
+// The update's view of a CH group (states, tables, divisors) for the kernels
+// that fuse the update or skip frozen blocks.
+template <typename T> static void fill_fuse(const spdba_plan* p, const Group<T>& r, CHFuse<T>& f) {
+    f.c_hat = r.c_hat;
+    for (int ax = 0; ax < 3; ++ax) { f.k2ax[ax] = r.k2ax[ax]; f.taper[ax] = r.taper[ax]; }
+    f.states = r.states;
+    f.chi = r.chi;
+    f.dt = (T)p->opt.dt;
+    f.dtkappa = (T)(p->opt.dt * p->opt.kappa);
+    f.dense = 1;
+    f.stats = r.stats;
+    f.g = r.g;
+    f.fd_bp.init((uint32_t)(r.g.ndim == 3 ? r.g.b[0] : r.g.b[1]));
+    f.fd_b2.init((uint32_t)r.g.b[2]);
+    f.fd_b1.init((uint32_t)r.g.b[1]);
+    f.fd_n2.init((uint32_t)r.g.n[2]);
+}
+
 // Half-spectrum passes of a 3-D complex64 group; SPDBA_ERR_UNSUPPORTED (and
 // no change) where the shape has no half-spectrum kernels or gains nothing.
 static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* dims) {
@@ -298,6 +316,10 @@ static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* di
     if (!paired) {
         if ((s = make_half_pass(&hmir, PASS_MIRROR, hg, tw, st)) != SPDBA_OK) return s;
         if (N2 % hmir.P != 0) return SPDBA_ERR_UNSUPPORTED;   // z tiles must stay within one x row
+    } else if (r.g.nb[0] * upd_table_cols(hmir.P, r.g.b[2]) <= kPairTable) {
+        // the paired pass skips frozen tiles and stores g_hat of non-frozen blocks only
+        // (the staged update reads no other); without states it stores everything
+        fill_fuse<float>(p, r, hmir.p.fu);
     }
     const int64_t dh[3] = {N0, N1, NHP};
     if ((s = make_axis_pass<float>(&hy_inv, 3, dh, 1, 1, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
@@ -366,20 +388,7 @@ static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const in
             // 32-bit mode indices inside the kernel
             if (sf == SPDBA_OK && r.batch * r.n >= 0x7fffffffLL) sf = SPDBA_ERR_UNSUPPORTED;
             if (sf == SPDBA_OK) {
-                CHFuse<T>& f = ps.p.fu;
-                f.c_hat = r.c_hat;
-                for (int ax = 0; ax < 3; ++ax) { f.k2ax[ax] = r.k2ax[ax]; f.taper[ax] = r.taper[ax]; }
-                f.states = r.states;
-                f.chi = r.chi;
-                f.dt = (T)p->opt.dt;
-                f.dtkappa = (T)(p->opt.dt * p->opt.kappa);
-                f.dense = 1;
-                f.stats = r.stats;
-                f.g = r.g;
-                f.fd_bp.init((uint32_t)(ndim == 3 ? r.g.b[0] : r.g.b[1]));
-                f.fd_b2.init((uint32_t)r.g.b[2]);
-                f.fd_b1.init((uint32_t)r.g.b[1]);
-                f.fd_n2.init((uint32_t)r.g.n[2]);
+                fill_fuse<T>(p, r, ps.p.fu);
                 r.upd_pass = ps;
                 r.has_fused = true;
                 r.fused_update = true;
@@ -581,8 +590,10 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
             return SPDBA_OK;
         }
         {
+            Pass<T> ps = r.h_mirror;
+            ps.p.fu.dense = dense;
             ProfScope pr(p, K_FFT_ZFWD, half_b + full_b);
-            if ((s = launch_pass<T>(r.h_mirror, r.half, r.work, st)) != SPDBA_OK) return s;
+            if ((s = launch_pass<T>(ps, r.half, r.work, st)) != SPDBA_OK) return s;
             p->launches += 1;
         }
         return ch_staged_update<T>(p, r, dense);

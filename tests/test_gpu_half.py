@@ -97,15 +97,17 @@ def test_half_shapes_have_half_kernels(dims):
     assert any(c["half_spectrum"] == 1 for c in rep["candidates"])
 
 
+@pytest.mark.parametrize("fuse", [1, 0])
 @pytest.mark.parametrize("dims", SHAPES)
-def test_half_shapes_against_oracle(dims):
+def test_half_shapes_against_oracle(dims, fuse):
     """Three steps with reassessments at steps 0 and 2: the second assessment,
     after the stiff damping of the high modes, mixes FROZEN, TRANSITION and
     ACTIVE blocks.  Both GPU assessments against the oracle's classifier, the
-    field against the FP64 oracle advanced with the GPU's states."""
+    field against the FP64 oracle advanced with the GPU's states; the update
+    fused into the z forward pass and staged after the (paired) z forward."""
     c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 124)
     from paper_2609_03922_gb300 import spdba
-    plan = spdba.Plan(dims, (8, 8, 8), threshold=0.1, reassess=2, precision=0, half_spectrum=1)
+    plan = spdba.Plan(dims, (8, 8, 8), threshold=0.1, reassess=2, precision=0, half_spectrum=1, fuse_update=fuse)
     plan.set_field(np.ascontiguousarray(c0.astype(np.float32)))
     plan.step(1)
     masks = {0: plan.get_mask()}
