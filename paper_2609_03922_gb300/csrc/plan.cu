@@ -155,6 +155,8 @@ struct spdba_plan {
     size_t ev_used = 0;
     long long launches = 0;
     double prof_list_bytes0 = 0;
+    long long list_updates = 0;    // list-driven update launches so far (graph replays included)
+    long long prof_list0 = 0;      // list_updates when the profile began
     double threshold = 0;
     int reassess = 1;
     int precision = SPDBA_C64;
@@ -170,6 +172,7 @@ struct spdba_plan {
     int horizon = 0, judge_every = 0;
     float prob_thr = 0.5f;
     long long seg_launches = 0;
+    long long seg_list_updates = 0;   // list-driven updates in one captured segment
     // groups step concurrently on their own streams, forked from and joined to st
     std::vector<cudaStream_t> gstreams;
     std::vector<cudaEvent_t> gevents;
@@ -660,6 +663,7 @@ template <typename T> static spdba_status ch_staged_update(spdba_plan* p, Group<
                      dense ? 3.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n) : 0.0);
         if ((s = launch_ch_update<T>(r.g, a, dense, st)) != SPDBA_OK) return s;
         p->launches += 1;
+        if (!dense) p->list_updates += 1;
     }
     r.step += 1;
     return SPDBA_OK;
@@ -845,7 +849,7 @@ template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
     while (i < n) {
         if (n - i >= R && segment_ready<T>(p)) {
             if (!p->seg_exec) {
-                const long long l0 = p->launches;
+                const long long l0 = p->launches, u0 = p->list_updates;
                 SPDBA_CUDA(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
                 spdba_status s = direct_steps<T>(p, R);
                 cudaGraph_t graph = nullptr;
@@ -862,6 +866,7 @@ template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
                     return cuda_fail(e, "cudaGraphInstantiate");
                 }
                 p->seg_launches = p->launches - l0;
+                p->seg_list_updates = p->list_updates - u0;
                 // the capture advanced the host-side step counters; run what it recorded
                 SPDBA_CUDA(cudaGraphLaunch(p->seg_exec, p->st));
             } else {
@@ -871,6 +876,7 @@ template <typename T> static spdba_status plan_step(spdba_plan* p, int64_t n) {
                     if (p->opt.mode == SPDBA_MODE_ADAPTIVE) g->assessed = true;
                 }
                 p->launches += p->seg_launches;
+                p->list_updates += p->seg_list_updates;
             }
             i += R;
         } else {
@@ -1359,6 +1365,7 @@ extern "C" spdba_status spdba_profile_begin_sampled(spdba_plan* p, int32_t every
     p->prof_recs.clear();
     p->ev_used = 0;
     p->launches = 0;
+    p->prof_list0 = p->list_updates;
     spdba_status s = p->precision == SPDBA_C64 ? list_bytes_now<float>(p, &p->prof_list_bytes0)
                                                : list_bytes_now<double>(p, &p->prof_list_bytes0);
     if (s != SPDBA_OK) return latch(p, s);
@@ -1387,7 +1394,10 @@ extern "C" spdba_status spdba_profile_end(spdba_plan* p, spdba_kernel_time* out,
     double lb = 0;
     spdba_status s = p->precision == SPDBA_C64 ? list_bytes_now<float>(p, &lb) : list_bytes_now<double>(p, &lb);
     if (s != SPDBA_OK) return latch(p, s);
-    agg[K_UPDATE_LIST].bytes += lb - p->prof_list_bytes0;
+    // the device counts the list traffic of every step; keep the timed (sampled) steps' share
+    const long long all_list = p->list_updates - p->prof_list0;
+    if (all_list > 0)
+        agg[K_UPDATE_LIST].bytes += (lb - p->prof_list_bytes0) * (double)agg[K_UPDATE_LIST].launches / (double)all_list;
     int n = 0;
     for (int k = 0; k < K_COUNT && n < capacity; ++k)
         if (agg[k].launches > 0 && out) out[n++] = agg[k];
