@@ -27,6 +27,10 @@
 
 namespace spdba {
 
+// Twiddle load: from a CTA's shared copy of the table (the compiler sees the
+// shared address space after inlining) or through the read-only cache.
+template <class C> __device__ __forceinline__ C tw_load(const C* p) { return __isShared(p) ? *p : __ldg(p); }
+
 // Radix schedule per pencil length (product of radices == L).
 template <int L> struct Radices;
 template <int... R> struct RList {};
@@ -381,7 +385,7 @@ __device__ __forceinline__ void stockham_stage_in(cx_t<T>* sm, const cx_t<T>* __
                 int jm = j % NS;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    C w = __ldg(tw + r * jm * (L / (NS * R)));
+                    C w = tw_load(tw + r * jm * (L / (NS * R)));
                     if constexpr (SIGN > 0) w.y = -w.y;
                     v[k][r] = cmul(v[k][r], w);
                 }
@@ -463,7 +467,7 @@ __device__ __forceinline__ void stockham_stage_out(cx_t<T>* sm, const cx_t<T>* _
             if constexpr (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    C w = __ldg(tw + r * j);
+                    C w = tw_load(tw + r * j);
                     if constexpr (SIGN > 0) w.y = -w.y;
                     v[k][r] = cmul(v[k][r], w);
                 }
@@ -614,7 +618,7 @@ __device__ __forceinline__ void fused_mid_stage(cx_t<T>* sm, const cx_t<T>* __re
             if constexpr (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    C w = __ldg(tw + r * j);
+                    C w = tw_load(tw + r * j);
                     if constexpr (SA > 0) w.y = -w.y;
                     v[k][r] = cmul(v[k][r], w);
                 }
@@ -1129,6 +1133,12 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
         const T* kpg = a.fu.g.ndim == 3 ? a.fu.k2ax[0] : a.fu.k2ax[1];
         for (int j = threadIdx.x; j < L; j += NT) s_kp[j] = kpg[j];   // visible after the loop's first barrier
     }
+    // complex64 passes up to 512 points keep the twiddle table in shared memory
+    constexpr bool STW = sizeof(T) == 4 && L <= 512;
+    __shared__ C s_tw[STW ? L : 1];
+    if constexpr (STW)
+        for (int j = threadIdx.x; j < L; j += NT) s_tw[j] = a.tw[j];   // visible after the loop's first barrier
+    const C* const tw = STW ? s_tw : a.tw;
     // direct stores from the last stage stay coalesced when a warp's lanes
     // cover at least 32 contiguous bytes of each output row
     // (the radix-3 tails of 192 and 384 hold too many registers to emit directly)
@@ -1158,7 +1168,7 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
         const long long q0 = t * P;
         if constexpr (MODE == PASS_MIRROR) {
             MirrorPlainOut<T, L, P> out(a, q0);
-            run_stages_out<T, L, P, NT, SIGN, LY>(sm, a.tw, out);
+            run_stages_out<T, L, P, NT, SIGN, LY>(sm, tw, out);
         } else if constexpr (!is_update_mode(MODE) && !DIRECT) {
             // short pencil-major pencils: the staged store keeps 16-byte coalesced writes
             tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
@@ -1170,13 +1180,13 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
                 store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
             } else {
                 PlainOut<T, L> out(a, q0);
-                run_stages_out<T, L, P, NT, SIGN, LY>(sm, a.tw, out);
+                run_stages_out<T, L, P, NT, SIGN, LY>(sm, tw, out);
             }
         } else if constexpr (MODE == PASS_CH_NL) {
             // inverse transform, the nonlinearity, forward transform (last stage storing)
             ChNlMid<T> mid{a.nl_scale, (T)0};
             PlainOut<T, L> out(a, q0);
-            transform_pair<T, L, P, NT, +1, -1, LY>(sm, a.tw, mid, out);
+            transform_pair<T, L, P, NT, +1, -1, LY>(sm, tw, mid, out);
             const T msum = mid.msum;
             if (a.mass != nullptr) {
                 double ms = warp_sum((double)msum);
@@ -1186,7 +1196,7 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
             const UpdTile u = upd_tile<T, P>(a, (int)q0);
             if (u.rows) {
                 // the tile spans several rows of a small grid
-                run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
+                run_stages<T, L, P, NT, -1, LY>(sm, tw);
                 ch_update_tile_rows<T, L, P, NT, LY>(sm, a, q0);
             } else if constexpr (upd_stages_chat<T, L>()) {
                 // c_hat of the tile's non-frozen rows streams in during the transform
@@ -1196,10 +1206,10 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
                 issue_chat<T, L, P, NT, LY>(smc, a, u, s_tab);
                 UpdOut<T, L, P, NT, Radices_last<L>::value, true, LY, MODE == PASS_UPD_HALF> out(a, u, s_tab, s_kp,
                                                                                                smc);
-                run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
+                run_stages_out<T, L, P, NT, -1, LY>(sm, tw, out);
             } else {
                 ch_update_table<T, L, P, NT>(s_tab, a, u);
-                run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
+                run_stages<T, L, P, NT, -1, LY>(sm, tw);
                 UpdOut<T, L, P, NT, 4, false, LY, MODE == PASS_UPD_HALF> out(a, u, s_tab, s_kp, nullptr);
                 drain_tile<T, L, P, NT, 4, LY>(sm, out);
             }

@@ -119,6 +119,12 @@ __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
     C* smA0 = reinterpret_cast<C*>(smem_raw);
     C* smA1 = smA0 + LY::SIZE;
     C* smB = smA1 + LY::SIZE;
+    // complex64 passes up to 512 points keep the twiddle table in shared memory
+    constexpr bool STW = sizeof(T) == 4 && L <= 512;
+    __shared__ C s_tw[STW ? L : 1];
+    if constexpr (STW)
+        for (int j = threadIdx.x; j < L; j += NT) s_tw[j] = a.tw[j];   // visible after the loop's first barrier
+    const C* const tw = STW ? s_tw : a.tw;
     const long long ntiles = (a.O * a.I) / P;
     long long t = blockIdx.x;
     if (t < ntiles) {
@@ -138,13 +144,13 @@ __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
         // between its reads and writes frees the mirror buffer
         PlainOut<T, L> out(a, t * P);
         HermIn<T, L, P, LY> in{sm, smB};
-        stockham_stage_in<T, L, P, NT, +1, 1, radix_at<L>(0), LY>(sm, a.tw, in);
+        stockham_stage_in<T, L, P, NT, +1, 1, radix_at<L>(0), LY>(sm, tw, in);
         // the mirror tile of the next tile streams in during the rest of the transform
         if (tn < ntiles) issue_herm_mirror<T, L, P, NT>(smB, a, tn * P);
         cp_async_commit();
-        run_stage_range<T, L, P, NT, +1, LY, 1, NSTAGES<L>::value - 1>(sm, a.tw);
+        run_stage_range<T, L, P, NT, +1, LY, 1, NSTAGES<L>::value - 1>(sm, tw);
         stockham_stage_out<T, L, P, NT, +1, ns_at<L>(NSTAGES<L>::value - 1), radix_at<L>(NSTAGES<L>::value - 1), LY>(
-            sm, a.tw, out);
+            sm, tw, out);
         __syncthreads();
         buf ^= 1;
         t = tn;
@@ -470,6 +476,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) fft_pair_kernel(PassParams<T> a)
     static_assert(Radices_last<L>::value != 3, "the last stage emits directly");
     static_assert(kPairBufs == 3, "the loop keeps two tiles in flight");
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // complex64 passes up to 512 points keep the twiddle table in shared memory
+    constexpr bool STW = sizeof(T) == 4 && L <= 512;
+    __shared__ C s_tw[STW ? L : 1];
+    if constexpr (STW)
+        for (int j = threadIdx.x; j < L; j += NT) s_tw[j] = a.tw[j];   // visible after the loop's first barrier
+    const C* const tw = STW ? s_tw : a.tw;
     __shared__ uint8_t s_tab[2 * kPairTable];
     C* const smb = reinterpret_cast<C*>(smem_raw);
     const int ntm = a.hg.N1 * (a.hg.N2 >> 1) / P, nt = ntm + a.hg.N1 / P;
@@ -493,9 +505,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) fft_pair_kernel(PassParams<T> a)
         C* sm = smb + slot * LY::SIZE;
         if (t < ntm) {
             PairPlainOut<T, L, P, Radices_last<L>::value> out(a, t, masked, s_tab, s_tab + kPairTable);
-            run_stages_out<T, L, P, NT, -1, LY>(sm, a.tw, out);
+            run_stages_out<T, L, P, NT, -1, LY>(sm, tw, out);
         } else {
-            run_stages<T, L, P, NT, -1, LY>(sm, a.tw);
+            run_stages<T, L, P, NT, -1, LY>(sm, tw);
             pair_column<T, L, P, NT, LY>(sm, a, (t - ntm) * P);
         }
         __syncthreads();   // buffer `slot` and the tables are free again
