@@ -132,6 +132,9 @@ template <typename T> struct PassParams {
     CHFuse<T> fu;                         // PASS_CH_UPDATE only
     FastDiv fd_I;                         // division by I (pipelined kernel, O * I < 2^31)
     HalfGeo hg;                           // half-spectrum passes only
+    // paired z forward with block states: its live tiles (any order) and their count
+    const int* live_tiles = nullptr;
+    const int* live_count = nullptr;
 };
 
 // Address of element (p, j) of the tile starting at pencil q0.

@@ -372,11 +372,16 @@ __device__ __forceinline__ bool pair_live(const PassParams<T>& a, bool masked, i
     }
     return __any_sync(0xffffffffu, live);
 }
-// next live tile of this CTA's sequence at or after t
+// Live tiles of the paired z forward under the block states, in any order:
+// one warp per tile, appended to list[]; *count must be zero on entry.  Run
+// once per state setting, so that the pass deals equal shares of live tiles
+// to its CTAs (liveness clusters in the spectrum).
 template <typename T, int P>
-__device__ __forceinline__ int pair_next(const PassParams<T>& a, bool masked, int t, int nt, int ntm) {
-    while (t < nt && !pair_live<T, P>(a, masked, t, ntm)) t += (int)gridDim.x;
-    return t;
+__global__ void __launch_bounds__(256) pair_live_list_kernel(PassParams<T> a, int* list, int* count) {
+    const int ntm = a.hg.N1 * (a.hg.N2 >> 1) / P, nt = ntm + a.hg.N1 / P;
+    const int t = (int)(blockIdx.x * 8 + (threadIdx.x >> 5));
+    if (t >= nt) return;   // warp-uniform
+    if (pair_live<T, P>(a, true, t, ntm) && (threadIdx.x & 31) == 0) list[atomicAdd(count, 1)] = t;
 }
 
 // Per-tile state tables (masked): tabd[bp * nbxd + bx], tabm[bp * nbxm + bx]
@@ -485,17 +490,26 @@ __global__ void __launch_bounds__(NT, 512 / NT) fft_pair_kernel(PassParams<T> a)
     __shared__ uint8_t s_tab[2 * kPairTable];
     C* const smb = reinterpret_cast<C*>(smem_raw);
     const int ntm = a.hg.N1 * (a.hg.N2 >> 1) / P, nt = ntm + a.hg.N1 / P;
-    const int G = (int)gridDim.x;
     const bool masked = a.fu.states != nullptr && !a.fu.dense;
-    int t = pair_next<T, P>(a, masked, (int)blockIdx.x, nt, ntm);
+    // this CTA's k-th tile: every tile in turn, or (masked) every live one from the list
+    const int G = (int)gridDim.x;
+    const int nlist = masked ? *a.live_count : 0;
+    auto tile_at = [&](int k) -> int {
+        const int i = (int)blockIdx.x + k * G;
+        if (masked) return i < nlist ? a.live_tiles[i] : nt;
+        return i < nt ? i : nt;
+    };
+    int t = tile_at(0);
     if (t < nt) issue_pair_half<T, L, P, NT, LY>(smb, a, t, ntm);
     cp_async_commit();
-    int t1 = t < nt ? pair_next<T, P>(a, masked, t + G, nt, ntm) : nt;
+    int t1 = tile_at(1);
     if (t1 < nt) issue_pair_half<T, L, P, NT, LY>(smb + LY::SIZE, a, t1, ntm);
     cp_async_commit();
+    int tn = tile_at(2);   // the tile to issue at the next iteration's start
     int slot = 0;
-    while (t < nt) {
-        const int t2 = t1 < nt ? pair_next<T, P>(a, masked, t1 + G, nt, ntm) : nt;
+    for (int k = 3; t < nt; ++k) {
+        const int t2 = tn;
+        tn = tile_at(k);   // in flight during this tile's work
         const int s2 = slot == 0 ? 2 : slot - 1;   // (slot + 2) mod 3: freed by the previous tile
         if (t2 < nt) issue_pair_half<T, L, P, NT, LY>(smb + s2 * LY::SIZE, a, t2, ntm);
         cp_async_commit();

@@ -1,5 +1,6 @@
 // Half-spectrum pass kernels of 3-D complex64 Cahn-Hilliard steps.
 #include "fft_half.cuh"
+#include "internal.h"
 #include "kernel_table.h"
 
 namespace spdba {
@@ -93,6 +94,24 @@ bool get_half_kernel(int64_t L, int mode, int nhp, KernelInfo* ki) {
         case 512: return pick_z<512>(mode, ki);
         default: return false;
     }
+}
+
+long long pair_tile_count(const Pass<float>& ps) {
+    const HalfGeo& h = ps.p.hg;
+    return (long long)h.N1 * (h.N2 / 2) / ps.P + h.N1 / ps.P;
+}
+
+spdba_status launch_pair_live_list(const Pass<float>& ps, int* list, int* count, cudaStream_t st) {
+    const long long nt = pair_tile_count(ps);
+    const unsigned grid = (unsigned)((nt + 7) / 8);   // a warp per tile, 8 per CTA
+    SPDBA_CUDA(cudaMemsetAsync(count, 0, sizeof(int), st));
+    switch (ps.P) {
+        case 8: pair_live_list_kernel<float, 8><<<grid, 256, 0, st>>>(ps.p, list, count); break;
+        case 16: pair_live_list_kernel<float, 16><<<grid, 256, 0, st>>>(ps.p, list, count); break;
+        default: return SPDBA_ERR_UNSUPPORTED;
+    }
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
 }
 
 }  // namespace spdba

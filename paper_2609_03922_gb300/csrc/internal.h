@@ -67,6 +67,11 @@ template <typename T> struct FftEngine {
 // Half-spectrum pass of a 3-D complex64 field (PASS_HERM_INV, PASS_NL_HALF,
 // PASS_MIRROR, PASS_UPD_HALF); the caller fills the update / mass fields.
 spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, TwiddleCache<float>& tw, cudaStream_t st);
+// List the live tiles of a paired z forward pass (one with block states) into
+// list[] (at most its tile count) and their number into *count.
+spdba_status launch_pair_live_list(const Pass<float>& ps, int* list, int* count, cudaStream_t st);
+// Tiles of a paired z forward pass.
+long long pair_tile_count(const Pass<float>& ps);
 // Pencils per tile of the pass kernels of length L (0 if none).
 template <typename T> int pass_tile_pencils(int64_t L);
 

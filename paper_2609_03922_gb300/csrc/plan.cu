@@ -85,6 +85,9 @@ template <typename T> struct Group {
     C* half = nullptr;
     long long half_n = 0;           // elements of the half array
     Pass<T> h_inv_z, h_inv_y, h_nl, h_fwd_y, h_mirror, h_upd;
+    int* pair_list = nullptr;       // live tiles of the paired z forward (with block states)
+    int* pair_count = nullptr;
+    long long pair_list_n = 0;      // capacity of pair_list
     bool fused_update = false;      // the last forward pass carries the update (upd_pass)
     bool has_fused = false;         // upd_pass exists (else only the staged form)
     Pass<T> upd_pass;               // forward pass of the first axis with the update fused
@@ -321,8 +324,15 @@ static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* di
         if (N2 % hmir.P != 0) return SPDBA_ERR_UNSUPPORTED;   // z tiles must stay within one x row
     } else if (r.g.nb[0] * upd_table_cols(hmir.P, r.g.b[2]) <= kPairTable) {
         // the paired pass skips frozen tiles and stores g_hat of non-frozen blocks only
-        // (the staged update reads no other); without states it stores everything
+        // (the staged update reads no other); without states it stores everything.
+        // Its live tiles are listed at every state setting.
         fill_fuse<float>(p, r, hmir.p.fu);
+        r.pair_list_n = pair_tile_count(hmir);
+        if ((s = r.alloc(&r.pair_list, sizeof(int) * (size_t)r.pair_list_n)) != SPDBA_OK) return s;
+        if ((s = r.alloc(&r.pair_count, sizeof(int))) != SPDBA_OK) return s;
+        SPDBA_CUDA(cudaMemsetAsync(r.pair_count, 0, sizeof(int), st));
+        hmir.p.live_tiles = r.pair_list;
+        hmir.p.live_count = r.pair_count;
     }
     const int64_t dh[3] = {N0, N1, NHP};
     if ((s = make_axis_pass<float>(&hy_inv, 3, dh, 1, 1, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
@@ -552,6 +562,12 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
     if (reassess) {
         s = p->pred ? group_assess_predicted<T>(p, r) : group_assess<T>(p, r);
         if (s != SPDBA_OK) return s;
+        if constexpr (std::is_same<T, float>::value) {
+            if (r.pair_list) {
+                if ((s = launch_pair_live_list(r.h_mirror, r.pair_list, r.pair_count, st)) != SPDBA_OK) return s;
+                p->launches += 1;
+            }
+        }
     }
     const int dense = !adaptive || all_active_step(p, r.step);
     if (r.use_half) {
@@ -1174,6 +1190,10 @@ template <typename T> static spdba_status snap_take(spdba_plan* p, Group<T>& r, 
                {r.chi, (size_t)nb},
                {r.list, sizeof(int32_t) * (size_t)nb},
                {r.count, sizeof(int32_t) * 2}};
+    if (r.pair_list) {
+        sn.bufs.push_back({r.pair_list, sizeof(int) * (size_t)r.pair_list_n});
+        sn.bufs.push_back({r.pair_count, sizeof(int)});
+    }
     for (auto& b : sn.bufs) {
         void* q = nullptr;
         cudaError_t e = cudaMalloc(&q, b.second);
