@@ -42,10 +42,10 @@ PROF_EVERY = 37
 # DRAM bytes (read + write) per launch from an ncu capture of the current
 # kernels on the 256^3 field (cold L2 at the start of each launch):
 # the z forward + update pass of the half-spectrum form: 250.95 MB read, 87.26 MB written;
-# the paired z forward of the staged form, with block states (autotuner at step 50): 69.96 MB read, 33.29 MB written;
+# the paired z forward of the staged form, with block states (autotuner at step 50): 79.77 MB read, 38.01 MB written;
 # the FFT passes (z inverse 144.23 + 37.44, y inverse 75.55 + 15.15, y forward 75.55 + 15.43 MB), averaged.
 UPDATE_PASS_DRAM_BYTES = 250.95e6 + 87.26e6
-ZFWD_PASS_DRAM_BYTES = 69.96e6 + 33.29e6
+ZFWD_PASS_DRAM_BYTES = 79.77e6 + 38.01e6
 FFT_PASS_DRAM_BYTES = (144.23e6 + 37.44e6 + 75.55e6 + 15.15e6 + 75.55e6 + 15.43e6) / 3
 METRIC = "spectral steps/s adaptive vs dense on 1 GB300 at rel-L2<=1e-4; % of HBM roofline"
 WORKLOAD = "ch3d-256^3-c64-B8-tau1e-6rel-R10"
