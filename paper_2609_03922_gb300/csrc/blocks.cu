@@ -463,14 +463,28 @@ __global__ void __launch_bounds__(CLS_NT) state_kernel(Geom g, const uint8_t* __
     unsigned nf = __ballot_sync(0xffffffffu, st != 0);
     unsigned na = __ballot_sync(0xffffffffu, st == SPDBA_ACTIVE);
     unsigned nt = __ballot_sync(0xffffffffu, st == SPDBA_TRANSITION);
-    __shared__ int s_nf;
-    if (threadIdx.x == 0) s_nf = 0;
+    __shared__ int s_nf, s_na, s_nt;
+    if (threadIdx.x == 0) s_nf = s_na = s_nt = 0;
     __syncthreads();
     const long long bpr = g.bpr();
     if ((threadIdx.x & 31) == 0) atomicAdd(&s_nf, __popc(nf));
     if (stats) {
-        // per-run counts: one atomic per warp when a warp never straddles runs
-        if (bpr % 32 == 0) {
+        // per-run counts: one atomic per CTA when a CTA never straddles runs (the
+        // counters of a run are one address: per-warp atomics would queue on it),
+        // else one per warp when a warp never straddles runs
+        if (bpr % CLS_NT == 0) {
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&s_na, __popc(na));
+                atomicAdd(&s_nt, __popc(nt));
+            }
+            __syncthreads();
+            const long long b0 = (long long)blockIdx.x * CLS_NT;
+            if (threadIdx.x == 0 && b0 < nb) {
+                const long long run = b0 / bpr;
+                if (s_na) atomicAdd(&stats[run].n_active, (unsigned long long)s_na);
+                if (s_nt) atomicAdd(&stats[run].n_transition, (unsigned long long)s_nt);
+            }
+        } else if (bpr % 32 == 0) {
             if ((threadIdx.x & 31) == 0 && b < nb) {
                 long long run = b / bpr;
                 if (na) atomicAdd(&stats[run].n_active, (unsigned long long)__popc(na));
