@@ -18,7 +18,8 @@ def _rand(shape, seed, dtype, scale_blocks=None):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("shape,block", [((64, 64), (16, 16)), ((32, 32, 32), (8, 8, 8)), ((4096,), (64,)),
-                                         ((48, 96), (16, 8)), ((256, 256, 256), (8, 8, 8))])
+                                         ((48, 96), (16, 8)), ((256, 256, 256), (8, 8, 8)),
+                                         ((256, 320, 96), (8, 8, 8)), ((256, 256, 128), (8, 8, 16))])
 def test_block_activity_matches_oracle(shape, block, precision):
     import torch
     from paper_2609_03922_gb300 import spdba
@@ -39,6 +40,32 @@ def test_block_activity_matches_oracle(shape, block, precision):
     mx, sm = O.block_measures(q64, block)
     assert np.array_equal(maxsq.cpu().numpy(), mx)            # same FP64 formula: bit-exact
     assert np.allclose(sumsq.cpu().numpy(), sm, rtol=1e-12, atol=0)
+    g = gmax.cpu().numpy()
+    assert g[0] == O.global_max_sq(q64, exclude_dc=False)
+    assert g[1] == O.global_max_sq(q64, exclude_dc=True)
+
+
+@pytest.mark.parametrize("shape,block", [((256, 256, 256), (8, 8, 8)), ((256, 320, 96), (8, 8, 8)),
+                                         ((256, 256, 128), (8, 8, 16)), ((128, 160, 512), (8, 4, 8))])
+def test_block_max_only_matches_oracle(shape, block):
+    """The maximum alone (no energy sum): complex64 fields with enough rows of
+    blocks take the streaming rows kernel (whole rows of blocks per CTA, lane
+    groups of 4 or 8 per block); bit-exact FP64 maxima, the global maxima with
+    and without k = 0."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    r = np.random.default_rng(4)
+    scale = np.exp(-6 * r.random(shape))
+    q = _rand(shape, 2, np.complex64, scale)
+    nb = tuple(s // b for s, b in zip(shape, block))
+    qd = torch.from_numpy(q).cuda()
+    maxsq = torch.empty(nb, dtype=torch.float64, device="cuda")
+    gmax = torch.zeros(2, dtype=torch.float64, device="cuda")
+    spdba.block_activity(qd, block, maxsq, None, gmax, precision=0)
+    torch.cuda.synchronize()
+    q64 = q.astype(np.complex128)
+    mx, _ = O.block_measures(q64, block)
+    assert np.array_equal(maxsq.cpu().numpy(), mx)
     g = gmax.cpu().numpy()
     assert g[0] == O.global_max_sq(q64, exclude_dc=False)
     assert g[1] == O.global_max_sq(q64, exclude_dc=True)
