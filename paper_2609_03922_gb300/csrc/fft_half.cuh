@@ -11,8 +11,10 @@
 //      complex transform (PASS_NL_HALF)
 //   y: plain forward pass on the half array
 //   z: forward pass of the half array for every x frequency, the mirrored
-//      ones from D(z, ky, kx) = conj(D(z, -ky, -kx)) (PASS_UPD_HALF with the
-//      update, PASS_MIRROR as a plain store), in fft_core.cuh.
+//      ones from D(z, ky, kx) = conj(D(z, -ky, -kx)): with the update
+//      (PASS_UPD_HALF, fft_core.cuh), or stored for the separate update, one
+//      transform per half pencil for kx and N2 - kx (PASS_PAIR_MIRROR, this
+//      file; PASS_MIRROR in fft_core.cuh where the paired tiles do not fit).
 #pragma once
 #include "fft_core.cuh"
 
