@@ -221,6 +221,46 @@ def test_graph_replay_equals_direct_launches(model):
         assert ta["step"] == tb["step"] == 22 and ta["assessments"] == tb["assessments"]
 
 
+def test_autotune_mid_run_restores_half_form_state():
+    """3-D 128^3 in the half-spectrum form, tuned after 15 steps (frozen blocks,
+    a live-tile list for the paired z forward in force): the trial steps leave
+    no trace (spectrum, mask and statistics bit for bit), and 12 more steps
+    match an untuned half-form plan bit for bit when the half form is chosen
+    (its update forms and graph replay agree bit for bit), else to rounding."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    dims = (128, 128, 128)
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 85).astype(np.float32)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        plan = spdba.Plan(dims, (8, 8, 8), threshold=1e-2, reassess=5, precision=0, half_spectrum=1)
+        plan.set_field(c0)
+        plan.step(15)
+        before = (plan.get_spectrum(), plan.get_mask(), plan.get_stats())
+        rep = plan.autotune(5)
+        chosen = rep["candidates"][rep["chosen"]]
+        after = (plan.get_spectrum(), plan.get_mask(), plan.get_stats())
+        plan.step(12)
+        tuned = (plan.get_spectrum(), plan.get_mask(), plan.get_stats())
+        plan.close()
+        ref = spdba.Plan(dims, (8, 8, 8), threshold=1e-2, reassess=5, precision=0, half_spectrum=1)
+        ref.set_field(c0)
+        ref.step(27)
+        untuned = (ref.get_spectrum(), ref.get_mask(), ref.get_stats())
+        ref.close()
+    side.synchronize()
+    assert np.any(before[1] == 0)
+    assert np.array_equal(after[0], before[0]) and np.array_equal(after[1], before[1])
+    assert after[2]["step"] == before[2]["step"] == 15
+    assert after[2]["assessments"] == before[2]["assessments"]
+    assert tuned[2]["step"] == untuned[2]["step"] == 27
+    if chosen["half_spectrum"] == 1:
+        assert np.array_equal(tuned[0], untuned[0]), chosen
+        assert np.array_equal(tuned[1], untuned[1]), chosen
+    else:
+        assert O.rel_l2(tuned[0], untuned[0]) <= 1e-5, chosen
+
+
 def test_autotune_restores_state_and_keeps_results():
     """The autotuner tries every launch configuration from the same state and
     leaves no trace: after it, the plan's step count, fields, masks and
