@@ -38,7 +38,18 @@ THRESHOLD = 1e-6
 REASSESS = 10
 DT, KAPPA = 0.01, 1.0
 MEAN, AMP = 0.1, 0.05
-PROF_EVERY = 37
+PROF_EVERY = 37   # at least this many steps between sampled steps
+
+
+def prof_every(k):
+    """Sampling interval of the per-kernel events: about 20 sampled steps per run
+    (at least PROF_EVERY apart), coprime with the reassessment interval so that
+    every phase of a reassessment segment gets sampled."""
+    import math
+    e = max(PROF_EVERY, k // 20)
+    while math.gcd(e, REASSESS) != 1:
+        e += 1
+    return e
 # DRAM bytes (read + write) per launch from an ncu capture of the current
 # kernels on the 256^3 field (cold L2 at the start of each launch):
 # the z forward + update pass of the half-spectrum form: 250.95 MB read, 87.26 MB written;
@@ -147,9 +158,9 @@ def run_ours(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         if profile:
-            # kernel events on one step in PROF_EVERY (coprime with the reassessment interval;
+            # kernel events on one step in prof_every(K) (coprime with the reassessment interval;
             # segments without a sampled step still replay as graphs)
-            plan.profile_begin(PROF_EVERY)
+            plan.profile_begin(prof_every(K))
         t0 = time.time()
         e0.record(st)
         plan.step(K)
