@@ -50,6 +50,8 @@ def prof_every(k):
     while math.gcd(e, REASSESS) != 1:
         e += 1
     return e
+
+
 # DRAM bytes (read + write) per launch from an ncu capture of the current
 # kernels on the 256^3 field (cold L2 at the start of each launch):
 # the z forward + update pass of the half-spectrum form: 250.95 MB read, 87.26 MB written;
@@ -57,6 +59,10 @@ def prof_every(k):
 # the FFT passes (z inverse 144.23 + 37.44, y inverse 75.55 + 15.15, y forward 75.55 + 15.43 MB), averaged.
 UPDATE_PASS_DRAM_BYTES = 250.95e6 + 87.26e6
 ZFWD_PASS_DRAM_BYTES = 79.77e6 + 38.01e6
+# the x pass (two real rows per transform): 75.54 MB read, 15.38 MB written;
+XPASS_DRAM_BYTES = 75.54e6 + 15.38e6
+# the list-driven update (autotuner's staged candidates at step 50): 173.46 MB read, 44.28 MB written;
+LIST_DRAM_BYTES = 173.46e6 + 44.28e6
 FFT_PASS_DRAM_BYTES = (144.23e6 + 37.44e6 + 75.55e6 + 15.15e6 + 75.55e6 + 15.43e6) / 3
 METRIC = "spectral steps/s adaptive vs dense on 1 GB300 at rel-L2<=1e-4; % of HBM roofline"
 WORKLOAD = "ch3d-256^3-c64-B8-tau1e-6rel-R10"
@@ -295,11 +301,43 @@ def run_ours(args, rank, world, local_rank):
                    "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (cold L2; part "
                                    "of the 134 MB output is still in L2 when the launch ends)",
                    "algorithmic_bytes_per_launch": zf_bytes}
+    # staged form: the list-driven update (24 B per mode of a listed block, counted on the device)
+    ul = prof[0].get("update_list")
+    ul_roof = None
+    if ul and ul["launches"] > 0 and ul["bytes"] > 0:
+        ul_bytes = ul["bytes"] / ul["launches"]
+        ul_ach = ul_bytes / (ul["total_ms"] / ul["launches"] / 1e3) / 1e9
+        ul_roof = {"bound": "hbm", "kernel": "list-driven CH update of the non-frozen blocks (c64)",
+                   "achieved": ul_ach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": ul_ach / hbm,
+                   "traffic": LIST_DRAM_BYTES,
+                   "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (autotuner's "
+                                   "staged candidates at step 50)",
+                   "algorithmic_bytes_per_launch": ul_bytes}
+    # the x pass: half array read and written once
+    xp = prof[0].get("fft_fused_nl")
+    xp_roof = None
+    if xp and xp["launches"] > 0:
+        xp_bytes = xp["bytes"] / xp["launches"]
+        xp_ach = xp_bytes / (xp["total_ms"] / xp["launches"] / 1e3) / 1e9
+        xp_roof = {"bound": "hbm", "kernel": "x pass: two real rows per transform, c^3 - c (L=256, c64)",
+                   "achieved": xp_ach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": xp_ach / hbm,
+                   "traffic": XPASS_DRAM_BYTES,
+                   "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (cold L2)",
+                   "algorithmic_bytes_per_launch": xp_bytes}
     fft_roof = {"bound": "hbm", "kernel": "FFT passes (Stockham, L=256, c64)", "achieved": achieved, "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": FFT_PASS_DRAM_BYTES,
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, averaged over the "
                                 "z inverse and the two y passes (cold L2 at each launch start)",
                 "algorithmic_bytes_per_launch": fp["bytes"] / fp["launches"]}
+    # the dominant kernel: the single kernel with the longest average launch among
+    # those with a roofline object (each runs once per step)
+    def avg_ms(kind):
+        v = prof[0].get(kind)
+        return v["total_ms"] / v["launches"] if v and v["launches"] > 0 else -1.0
+    cands = [(avg_ms("fft_update"), upd_roof), (avg_ms("fft_z_forward"), zf_roof),
+             (avg_ms("update_list"), ul_roof), (avg_ms("fft_fused_nl"), xp_roof)]
+    cands = [c for c in cands if c[1] is not None]
+    dominant = max(cands, key=lambda c: c[0])[1] if cands else fft_roof
     upd_a, upd_d = staged["adaptive"]["update_stage_ms"], staged["dense"]["update_stage_ms"]
     line = {
         "metric": METRIC,
@@ -332,9 +370,11 @@ def run_ours(args, rank, world, local_rank):
         "rel_l2_adaptive_vs_dense": rel_ada_dense,
         "kernels": kinds,
         "kernels_dense": kind_summary(prof_dense),
-        "roofline": upd_roof if upd_roof is not None else zf_roof if zf_roof is not None else fft_roof,
+        "roofline": dominant,
         "roofline_fft_passes": fft_roof,
         "roofline_z_forward": zf_roof,
+        "roofline_update_list": ul_roof,
+        "roofline_x_pass": xp_roof,
         "e2e": {"value": steps_total / (e2e_ms / 1e3), "unit": "steps/s",
                 "h2d_bytes_per_step": 4.0 * n / K, "d2h_bytes_per_step": 4.0 * n / K,
                 "note": "set_field from pinned host + %d steps + get_field to pinned host" % K},
