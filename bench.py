@@ -319,9 +319,11 @@ def run_ours(args, rank, world, local_rank):
     if xp and xp["launches"] > 0:
         xp_bytes = xp["bytes"] / xp["launches"]
         xp_ach = xp_bytes / (xp["total_ms"] / xp["launches"] / 1e3) / 1e9
-        xp_roof = {"bound": "hbm", "kernel": "x pass: two real rows per transform, c^3 - c (L=256, c64)",
+        half = bool(tune["candidates"][tune["chosen"]]["half_spectrum"])
+        xp_roof = {"bound": "hbm", "kernel": ("x pass: two real rows per transform, c^3 - c (L=256, c64)" if half
+                                              else "x pass: inverse, c^3 - c, forward (L=256, c64)"),
                    "achieved": xp_ach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": xp_ach / hbm,
-                   "traffic": XPASS_DRAM_BYTES,
+                   "traffic": XPASS_DRAM_BYTES if half else None,
                    "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (cold L2)",
                    "algorithmic_bytes_per_launch": xp_bytes}
     fft_roof = {"bound": "hbm", "kernel": "FFT passes (Stockham, L=256, c64)", "achieved": achieved, "peak": hbm,
