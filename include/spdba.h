@@ -218,6 +218,21 @@ spdba_status spdba_profile_end(spdba_plan* plan, spdba_kernel_time* out, int32_t
 const char* spdba_last_error(void);
 const char* spdba_status_string(spdba_status s);
 
+/*
+ * Host-side fault injection for the out-of-memory path (no counterpart in the
+ * paper).  After spdba_debug_fail_alloc(k), the k-th device allocation the
+ * library makes from then on (k >= 1; plans, FFT plans, predictors and the
+ * autotuner's snapshot all count) fails as if the device were out of memory,
+ * without calling cudaMalloc: the call that needed it returns SPDBA_ERR_OOM,
+ * spdba_last_error() names the allocation, and everything the call had
+ * allocated is freed.  k <= 0 switches the injection off; it also ends by
+ * itself after the failing allocation.  spdba_debug_live_allocs() returns the
+ * number of device buffers the library holds right now (a leak check).
+ * Process-wide; not for concurrent use from several threads.
+ */
+void spdba_debug_fail_alloc(int64_t k);
+int64_t spdba_debug_live_allocs(void);
+
 /* ------------------------------------------------------------------------------ */
 /* Kernel-level entry points (device pointers, caller-owned buffers).               */
 /* ------------------------------------------------------------------------------ */
@@ -332,9 +347,11 @@ spdba_status spdba_plan_attach_predictor(spdba_plan* plan, spdba_predictor* pr, 
  * is a fixed array of about 1 MiB compiled into the library (every GPU that
  * loads the library holds it until the process exits).  At most
  * SPDBA_CLASSIFY_STATIC_MAX_BLOCKS blocks; larger maps return
- * SPDBA_ERR_UNSUPPORTED.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Calls never call cudaMalloc or
+ * SPDBA_ERR_UNSUPPORTED.  Each call made outside stream capture looks up the
+ * array's device address (cudaGetSymbolAddress) with the current device, so a
+ * device reset between calls is harmless; a call made during capture reuses
+ * the address of that device's last uncaptured call, so make one call on the
+ * device before any stream capture (else SPDBA_ERR_STATE).  Calls never call cudaMalloc or
  * cudaFree.  All calls share the one array and it keeps the previous call's
  * contents (nothing in it needs to start at zero: each call writes what it
  * reads), so calls whose kernels overlap on the GPU (different streams, or

@@ -635,16 +635,25 @@ std::mutex g_static_mu;
 void* g_static_ptr[kMaxDevices] = {nullptr};
 }  // namespace
 
-static spdba_status static_scratch_for_current_device(void** out) {
+// The array's device address on the current device.  Outside stream capture it
+// is looked up on every call (a host-side table lookup), so that a context
+// torn down and re-created (cudaDeviceReset) never leaves a stale address
+// behind; during capture, where the lookup may not be issued, the address
+// of the device's last uncaptured call is used.
+static spdba_status static_scratch_for_current_device(cudaStream_t st, void** out) {
     int dev = 0;
     SPDBA_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(SPDBA_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SPDBA_CUDA(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_classify_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(classify scratch)");
         g_static_ptr[dev] = p;
+    } else if (!g_static_ptr[dev]) {
+        return fail(SPDBA_ERR_STATE, "spdba_classify_static: first call on device %d made during stream capture", dev);
     }
     *out = g_static_ptr[dev];
     return SPDBA_OK;
@@ -666,7 +675,7 @@ extern "C" spdba_status spdba_classify_static(int32_t ndim, const int64_t* nbloc
         return fail(SPDBA_ERR_UNSUPPORTED, "spdba_classify_static: %lld blocks exceed the fixed capacity of %d",
                     g.blocks(), SPDBA_CLASSIFY_STATIC_MAX_BLOCKS);
     void* scratch = nullptr;
-    if ((s = static_scratch_for_current_device(&scratch)) != SPDBA_OK) return s;
+    if ((s = static_scratch_for_current_device((cudaStream_t)stream, &scratch)) != SPDBA_OK) return s;
     // layout as in spdba_classify: per-CTA counts first, then one flag per block;
     // every byte a call reads is written earlier in the same call
     size_t cbytes = classify_scratch_bytes(g.blocks());

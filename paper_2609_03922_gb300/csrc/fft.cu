@@ -1,5 +1,6 @@
 // Host side of the Stockham FFT: FP64 twiddle tables, pass planning, the
 // kernel-level FFT entry points, and the library's error reporting.
+#include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
 
@@ -35,6 +36,24 @@ spdba_status cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? SPDBA_ERR_OOM : SPDBA_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ device allocations
+static std::atomic<long long> g_live_allocs{0};
+static std::atomic<long long> g_fail_countdown{0};
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (g_fail_countdown.load() > 0 && g_fail_countdown.fetch_sub(1) == 1) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+    else *p = nullptr;
+    return e;
+}
+void dev_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    g_live_allocs.fetch_sub(1);
+}
+
 bool length_ok(int64_t n) {
     if (n < 1) return false;
     while (n % 2 == 0) n /= 2;
@@ -64,16 +83,16 @@ template <typename T> cx_t<T>* TwiddleCache<T>::get(int64_t n, cudaStream_t st, 
     auto it = tables.find(n);
     if (it != tables.end()) return it->second;
     cx_t<T>* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sizeof(cx_t<T>) * (size_t)n);
-    if (e != cudaSuccess) { *err = cuda_fail(e, "cudaMalloc(twiddles)"); return nullptr; }
+    cudaError_t e = dev_alloc((void**)&p, sizeof(cx_t<T>) * (size_t)n);
+    if (e != cudaSuccess) { *err = cuda_fail(e, "device allocation (twiddle table)"); return nullptr; }
     twiddle_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, (long long)n);
     e = cudaGetLastError();
-    if (e != cudaSuccess) { cudaFree(p); *err = cuda_fail(e, "twiddle_kernel"); return nullptr; }
+    if (e != cudaSuccess) { dev_free(p); *err = cuda_fail(e, "twiddle_kernel"); return nullptr; }
     tables[n] = p;
     return p;
 }
 template <typename T> void TwiddleCache<T>::release() {
-    for (auto& kv : tables) cudaFree(kv.second);
+    for (auto& kv : tables) dev_free(kv.second);
     tables.clear();
 }
 
@@ -206,7 +225,10 @@ spdba_status FftEngine<T>::init(int nd, const int64_t* d, int64_t b, TwiddleCach
             v.push_back(p1); so.push_back(1);
             v.push_back(p2); so.push_back(0);
         }
-        if (!scratch) SPDBA_CUDA(cudaMalloc(&scratch, sizeof(cx_t<T>) * (size_t)total));
+        if (!scratch) {
+            cudaError_t e = dev_alloc((void**)&scratch, sizeof(cx_t<T>) * (size_t)total);
+            if (e != cudaSuccess) return cuda_fail(e, "device allocation (FFT scratch)");
+        }
         return SPDBA_OK;
     }
     for (int a = 0; a < nd; ++a) {
@@ -245,7 +267,7 @@ spdba_status FftEngine<T>::exec(const cx_t<T>* in, cx_t<T>* out, int direction, 
 }
 
 template <typename T> void FftEngine<T>::release() {
-    if (scratch) cudaFree(scratch);
+    if (scratch) dev_free(scratch);
     scratch = nullptr;
 }
 
@@ -399,3 +421,7 @@ extern "C" const char* spdba_status_string(spdba_status s) {
         default: return "unknown status";
     }
 }
+
+extern "C" void spdba_debug_fail_alloc(int64_t k) { spdba::g_fail_countdown.store(k > 0 ? (long long)k : 0); }
+
+extern "C" int64_t spdba_debug_live_allocs(void) { return (int64_t)spdba::g_live_allocs.load(); }

@@ -16,6 +16,12 @@ namespace spdba {
 void set_error(const char* fmt, ...);
 spdba_status fail(spdba_status s, const char* fmt, ...);
 spdba_status cuda_fail(cudaError_t e, const char* what);
+// Every device buffer of the library is allocated and freed here: the two
+// count the live buffers, and dev_alloc fails one chosen allocation when told
+// to (spdba_debug_fail_alloc), so the out-of-memory path can be tested on the
+// host without exhausting a GPU.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
 #define SPDBA_CUDA(call)                                              \
     do {                                                              \
         cudaError_t e_ = (call);                                      \

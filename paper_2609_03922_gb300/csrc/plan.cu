@@ -115,14 +115,14 @@ template <typename T> struct Group {
 
     template <typename P> spdba_status alloc(P** p, size_t bytes) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        cudaError_t e = dev_alloc(&q, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "device allocation (plan buffer)");
         allocs.push_back(q);
         *p = (P*)q;
         return SPDBA_OK;
     }
     void release() {
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs) dev_free(p);
         allocs.clear();
         fft1.release();
     }
@@ -1172,7 +1172,7 @@ struct GroupSnap {
     int64_t step = 0;
     bool assessed = false;
     void release() {
-        for (void* q : copies) cudaFree(q);
+        for (void* q : copies) dev_free(q);
         copies.clear();
     }
 };
@@ -1196,8 +1196,8 @@ template <typename T> static spdba_status snap_take(spdba_plan* p, Group<T>& r, 
     }
     for (auto& b : sn.bufs) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, b.second);
-        if (e != cudaSuccess) { sn.release(); return cuda_fail(e, "cudaMalloc(autotune snapshot)"); }
+        cudaError_t e = dev_alloc(&q, b.second);
+        if (e != cudaSuccess) { sn.release(); return cuda_fail(e, "device allocation (autotune snapshot)"); }
         sn.copies.push_back(q);
         SPDBA_CUDA(cudaMemcpyAsync(q, b.first, b.second, cudaMemcpyDeviceToDevice, p->st));
     }

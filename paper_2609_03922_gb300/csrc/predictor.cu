@@ -332,8 +332,8 @@ struct spdba_predictor {
     std::vector<void*> allocs;
     template <typename Q> spdba_status alloc(Q** p, size_t bytes) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        cudaError_t e = spdba::dev_alloc(&q, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "device allocation (predictor buffer)");
         allocs.push_back(q);
         *p = (Q*)q;
         return SPDBA_OK;
@@ -400,7 +400,7 @@ extern "C" int64_t spdba_predictor_num_params(void) { return NPARAM; }
 extern "C" void spdba_predictor_destroy(spdba_predictor* pr) {
     if (!pr) return;
     cudaDeviceSynchronize();
-    for (void* p : pr->allocs) cudaFree(p);
+    for (void* p : pr->allocs) spdba::dev_free(p);
     delete pr;
 }
 

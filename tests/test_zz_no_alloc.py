@@ -43,18 +43,35 @@ def _classify_both(nb, meas, tau, force_dc, transitions):
     return outs
 
 
+def _check_pair(a, b):
+    assert a[3] == b[3]
+    assert np.array_equal(a[0], b[0])
+    trans = a[0] == 1
+    assert np.array_equal(a[1][trans], b[1][trans])
+    assert np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("force_dc", [0, 1])
+@pytest.mark.parametrize("transitions", [0, 1])
 @pytest.mark.parametrize("nb", [(32, 32, 32), (48, 48, 48)])
-def test_static_classify_matches_allocating_classify_twice(nb):
-    r = np.random.default_rng(11)
+def test_static_classify_matches_allocating_classify_twice(nb, transitions, force_dc):
+    r = np.random.default_rng(11 + 2 * transitions + force_dc)
     for call in range(2):   # two calls in a row: the second sees the first call's leftovers
         meas = np.exp(-8 * r.random(nb))
         tau = float(np.quantile(meas, 0.85 if call == 0 else 0.6))
+        a, b = _classify_both(nb, meas, tau, force_dc, transitions)
+        _check_pair(a, b)
+
+
+def test_static_classify_at_exact_capacity():
+    """A map of exactly 2^20 blocks (the largest the fixed array serves)."""
+    nb = (128, 128, 64)
+    r = np.random.default_rng(5)
+    for call in range(2):
+        meas = np.exp(-8 * r.random(nb))
+        tau = float(np.quantile(meas, 0.9 if call == 0 else 0.5))
         a, b = _classify_both(nb, meas, tau, 1, 1)
-        assert a[3] == b[3]
-        assert np.array_equal(a[0], b[0])
-        trans = a[0] == 1
-        assert np.array_equal(a[1][trans], b[1][trans])
-        assert np.array_equal(a[2], b[2])
+        _check_pair(a, b)
 
 
 def test_static_classify_rejects_oversized_maps():
