@@ -15,6 +15,10 @@ Parity status of each piece (what pins it, see tests/test_oracle_*.py):
   sigma_field ................. closed form of the taper product (Eq. S.2, S.3)
   masked steps ................ threshold 0 == Regular bit for bit; infinite threshold
                                 leaves every block but the k=0 block untouched
+  threshold_control /
+  ThresholdController ......... hand-traced threshold sequences on synthetic ratio
+                                histories (every branch and both deadband edges);
+                                control steps are full-activation steps (== Regular)
   nls_* ....................... CW exact solution, dispersion-only closed form,
                                 unitarity, forward/backward recovery
 No function here is "parity unpinned".
@@ -31,6 +35,11 @@ Paper conventions restated (section / equation of arXiv 2609.03922):
   * The block holding the zero-frequency mode is kept active (S6.1).
   * Periodic refresh activates every block every F steps (S1.3); a warm-up of
     all-active steps precedes adaptive operation (S3.2).
+  * Dynamic threshold control (S1.3): every control interval the measured
+    mean share r of non-frozen (active + transition) blocks is compared with
+    a target r_tar; outside the relative deadband eta the threshold is scaled
+    by 1 + eta or 1 - eta, and by 2 or 1/2 when r / r_tar > 2 or < 0.5; each
+    check is followed by one full-activation step (S1.3, S3.2 parameters).
   * Semi-implicit Fourier update of a conserved (Cahn-Hilliard form) field
     (S3.1 dynamics, S4.2 semi-implicit update with M = 1).
   * Symmetric split-step Fourier with the linear operator applied in two
@@ -62,6 +71,7 @@ __all__ = [
     "ch_real_field", "ch_mass", "CHConfig", "run_ch", "nls_omega", "nls_half_factor",
     "nls_kerr", "nls_masked_half", "nls_regular_step", "nls_masked_step", "NLSConfig",
     "run_nls", "rel_l2", "nmse_db", "field_corr", "assess_states", "effective_states",
+    "threshold_control", "ThresholdController", "is_control_step",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -314,7 +324,8 @@ class CHConfig:
 
     def __init__(self, dims, block, threshold=1e-6, reassess=10, dt=0.01, kappa=1.0,
                  mode=1, measure=MEASURE_MAXAMP, tau_rule=TAU_REL_MAX, transitions=True,
-                 refresh_every=0, warmup_steps=0, force_dc=True):
+                 refresh_every=0, warmup_steps=0, force_dc=True, target_ratio=0.0, control_every=50,
+                 control_eta=0.05):
         self.dims = tuple(int(x) for x in dims)
         self.block = tuple(int(x) for x in block)
         self.threshold = float(threshold)
@@ -328,40 +339,117 @@ class CHConfig:
         self.refresh_every = int(refresh_every)
         self.warmup_steps = int(warmup_steps)
         self.force_dc = bool(force_dc)
+        self.target_ratio = float(target_ratio)   # dynamic threshold control (S1.3), 0 = off
+        self.control_every = int(control_every)
+        self.control_eta = float(control_eta)
 
 
-def assess_states(q, cfg, exclude_dc):
-    """Measure, threshold and classify a transformed field; returns (states, tau, measure)."""
+def assess_states(q, cfg, exclude_dc, threshold=None):
+    """Measure, threshold and classify a transformed field; returns (states, tau, measure).
+    `threshold` overrides cfg.threshold (the coefficient dynamic control adjusts)."""
     maxsq, sumsq = block_measures(q, cfg.block)
     measure = np.sqrt(maxsq if cfg.measure == MEASURE_MAXAMP else sumsq)
-    tau = threshold_value(q, cfg.threshold, cfg.tau_rule, exclude_dc)
+    tau = threshold_value(q, cfg.threshold if threshold is None else threshold, cfg.tau_rule, exclude_dc)
     states = classify(measure, tau, force_dc=cfg.force_dc, transitions=cfg.transitions)
     return states, tau, measure
 
 
+def is_control_step(step, cfg):
+    """Dynamic threshold control checks the ratio at every control_every-th step
+    once the warm-up is over (S1.3; control starts after the full-activation
+    stage, S3.2).  The step right after a check -- here the step at which the
+    check is made, before its update -- runs with every block active."""
+    return (getattr(cfg, "target_ratio", 0.0) > 0 and step > cfg.warmup_steps
+            and step % cfg.control_every == 0)
+
+
 def effective_states(assessed, step, cfg):
-    """All blocks ACTIVE on warm-up and refresh steps (S1.3, S3.2), else the last assessment."""
+    """All blocks ACTIVE on warm-up, refresh and control steps (S1.3, S3.2), else the last assessment."""
     if step < cfg.warmup_steps or (cfg.refresh_every > 0 and step > 0
-                                   and step % cfg.refresh_every == 0):
+                                   and step % cfg.refresh_every == 0) or is_control_step(step, cfg):
         return np.full_like(assessed, STATE_ACTIVE)
     return assessed
 
 
-def run_ch(c0, cfg, steps, start_step=0, c_hat=None, on_assess=None, states=None):
+def threshold_control(threshold, r, r_tar, eta):
+    """One dynamic threshold-control decision (S1.3).
+
+    r is the measured mean share of non-frozen (active + transition) blocks
+    over the control interval and r_tar the target.  With q = r / r_tar:
+    q > 2 doubles the threshold, q < 0.5 halves it; otherwise a deviation
+    outside the relative deadband (q > 1 + eta or q < 1 - eta) scales it by
+    1 + eta or 1 - eta; inside the deadband (edges included) it is kept.
+    """
+    q = r / r_tar
+    if q > 2.0:
+        return threshold * 2.0
+    if q < 0.5:
+        return threshold * 0.5
+    if q > 1.0 + eta:
+        return threshold * (1.0 + eta)
+    if q < 1.0 - eta:
+        return threshold * (1.0 - eta)
+    return threshold
+
+
+class ThresholdController:
+    """The threshold coefficient of a run under dynamic control (S1.3).
+
+    Each adaptive step (not a warm-up, refresh or control step) adds the
+    number of non-frozen blocks of the states in force; at a control step the
+    interval's mean share r = sum / (steps * nblocks) drives one
+    threshold_control decision (when at least one adaptive step was seen) and
+    the interval restarts.  `log` records (step, threshold) after each
+    decision.
+    """
+
+    def __init__(self, cfg, nblocks):
+        self.cfg = cfg
+        self.nblocks = int(nblocks)
+        self.threshold = float(cfg.threshold)
+        self.sum_nonfrozen = 0
+        self.steps = 0
+        self.log = []
+
+    def begin_step(self, step):
+        """Called before the step's reassessment; returns the threshold in force."""
+        if is_control_step(step, self.cfg) and self.steps > 0:
+            r = float(self.sum_nonfrozen) / (float(self.steps) * float(self.nblocks))
+            self.threshold = threshold_control(self.threshold, r, self.cfg.target_ratio, self.cfg.control_eta)
+            self.sum_nonfrozen = 0
+            self.steps = 0
+            self.log.append((step, self.threshold))
+        return self.threshold
+
+    def end_step(self, step, states_in_force):
+        """Called after the step with the assessed states in force (not the forced ones)."""
+        forced = step < self.cfg.warmup_steps or (self.cfg.refresh_every > 0 and step > 0
+                                                  and step % self.cfg.refresh_every == 0) \
+            or is_control_step(step, self.cfg)
+        if not forced:
+            self.sum_nonfrozen += int(np.count_nonzero(np.asarray(states_in_force) != STATE_FROZEN))
+            self.steps += 1
+
+
+def run_ch(c0, cfg, steps, start_step=0, c_hat=None, on_assess=None, states=None, controller=None):
     """Advance a CH field `steps` steps.  Returns (c_hat, history) where history
     lists (step, states, tau) at each reassessment.  `on_assess(step, c_hat,
     states, tau)` may return replacement states (lock-step mask parity).  To
-    continue a run, pass its c_hat, start_step and the states in force."""
+    continue a run, pass its c_hat, start_step, the states in force and its
+    ThresholdController (one is made when cfg.target_ratio > 0)."""
     k2 = k_squared(cfg.dims)
     if c_hat is None:
         c_hat = fftn(np.asarray(c0, dtype=np.float64))
+    if controller is None and getattr(cfg, "target_ratio", 0.0) > 0:
+        controller = ThresholdController(cfg, np.prod(block_counts(cfg.dims, cfg.block)))
     history = []
     for n in range(start_step, start_step + steps):
         if cfg.mode == 0:
             c_hat = ch_regular_step(c_hat, k2, cfg.dt, cfg.kappa)
             continue
+        thr = controller.begin_step(n) if controller is not None else None
         if states is None or n % cfg.reassess == 0:
-            states, tau, _ = assess_states(c_hat, cfg, exclude_dc=True)
+            states, tau, _ = assess_states(c_hat, cfg, exclude_dc=True, threshold=thr)
             if on_assess is not None:
                 repl = on_assess(n, c_hat, states, tau)
                 if repl is not None:
@@ -369,6 +457,8 @@ def run_ch(c0, cfg, steps, start_step=0, c_hat=None, on_assess=None, states=None
             history.append((n, states.copy(), tau))
         eff = effective_states(states, n, cfg)
         c_hat = ch_masked_step(c_hat, eff, cfg.block, k2, cfg.dt, cfg.kappa)
+        if controller is not None:
+            controller.end_step(n, states)
     return c_hat, history
 
 
@@ -424,7 +514,8 @@ def nls_masked_step(E, states, block, H, gamma, h, sigma=None):
 class NLSConfig:
     def __init__(self, n, block, threshold=1e-6, reassess=10, beta2=-21.7, gamma=1.3, h=0.1,
                  dt_sample=1.0, mode=1, measure=MEASURE_MAXAMP, tau_rule=TAU_REL_MAX,
-                 transitions=True, refresh_every=0, warmup_steps=0):
+                 transitions=True, refresh_every=0, warmup_steps=0, target_ratio=0.0, control_every=50,
+                 control_eta=0.05):
         self.dims = (int(n),)
         self.block = (int(block),)
         self.threshold = float(threshold)
@@ -440,22 +531,29 @@ class NLSConfig:
         self.refresh_every = int(refresh_every)
         self.warmup_steps = int(warmup_steps)
         self.force_dc = False
+        self.target_ratio = float(target_ratio)   # dynamic threshold control (S1.3), 0 = off
+        self.control_every = int(control_every)
+        self.control_eta = float(control_eta)
 
 
-def run_nls(E0, cfg, steps, on_assess=None):
+def run_nls(E0, cfg, steps, on_assess=None, controller=None):
     """Propagate E0 by `steps` split steps; states are assessed on FFT(E) at the
-    start of a step, every `reassess` steps (S5.3: total spectral power, M = 1)."""
+    start of a step, every `reassess` steps (S5.3: total spectral power, M = 1).
+    With cfg.target_ratio > 0 the threshold follows dynamic control (S1.3)."""
     n = cfg.dims[0]
     H = nls_half_factor(nls_omega(n, cfg.dt_sample), cfg.beta2, cfg.h)
     E = np.asarray(E0, dtype=np.complex128)
+    if controller is None and cfg.target_ratio > 0:
+        controller = ThresholdController(cfg, n // cfg.block[0])
     history = []
     states = None
     for s in range(steps):
         if cfg.mode == 0:
             E = nls_regular_step(E, H, cfg.gamma, cfg.h)
             continue
+        thr = controller.begin_step(s) if controller is not None else None
         if states is None or s % cfg.reassess == 0:
-            states, tau, _ = assess_states(fftn(E), cfg, exclude_dc=False)
+            states, tau, _ = assess_states(fftn(E), cfg, exclude_dc=False, threshold=thr)
             if on_assess is not None:
                 repl = on_assess(s, E, states, tau)
                 if repl is not None:
@@ -463,6 +561,8 @@ def run_nls(E0, cfg, steps, on_assess=None):
             history.append((s, states.copy(), tau))
         eff = effective_states(states, s, cfg)
         E = nls_masked_step(E, eff, cfg.block, H, cfg.gamma, cfg.h)
+        if controller is not None:
+            controller.end_step(s, states)
     return E, history
 
 
