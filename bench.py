@@ -83,6 +83,9 @@ TOUCHED_NOTE = {
     "update_list": "ncu DRAM read + write of one launch (autotuner's staged candidates at step 50)",
     "fft_pass": "ncu DRAM read + write per launch, averaged over the z inverse and the two y passes (cold L2)",
 }
+CONTROL_TARGETS = (0.05, 0.1, 0.2)   # dynamic threshold control targets (S1.3: 5-20 %)
+CONTROL_EVERY = 50                   # control interval (S3.2, S4.2, S5.3)
+CONTROL_ETA = 0.05                   # adjustment factor (S3.2, S5.3)
 TUNE_AT = 500          # step of the run where the plans are tuned and the timed window starts
 FULL_RUN = 2000        # the configuration's whole run
 MIN_TIMED_S = 1.0      # the timed region is repeated until it adds up to this (clock samples)
@@ -218,9 +221,9 @@ def run_ours(args, rank, world, local_rank, parity=None):
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         return float(t.item())
 
-    def make(mode, fuse):
+    def make(mode, fuse, **kw):
         return spdba.Plan(DIMS, BLOCK, threshold=THRESHOLD, reassess=REASSESS, precision=spdba.SPDBA_C64,
-                          mode=mode, dt=DT, kappa=KAPPA, fuse_update=fuse)
+                          mode=mode, dt=DT, kappa=KAPPA, fuse_update=fuse, **kw)
 
     def prepare(plan):
         """From c0 to step TUNE_AT (blocks have frozen there), where the plan's
@@ -328,6 +331,28 @@ def run_ours(args, rank, world, local_rank, parity=None):
     dense.get_field(field_dense)
     rel_ada_dense = float(((field_ada.double() - field_dense.double()).norm() / field_dense.double().norm()).item())
     dense.close()
+
+    # ---- dynamic threshold control (the paper's comparison mode): whole runs at
+    # fixed target shares of non-frozen blocks, against the dense run
+    control = {}
+    for target in CONTROL_TARGETS:
+        pl = make(spdba.SPDBA_MODE_ADAPTIVE, 1, target_ratio=target, control_every=CONTROL_EVERY,
+                  control_eta=CONTROL_ETA)
+        tune_c, snap = prepare(pl)
+        del snap
+        ms_c, _ = full_run(pl)
+        st_c = pl.get_stats()
+        f_c = torch.empty(DIMS, dtype=torch.float32, device=dev)
+        pl.get_field(f_c)
+        rel_c = float(((f_c.double() - field_dense.double()).norm() / field_dense.double().norm()).item())
+        control["%g" % target] = {
+            "steps_per_s": world * FULL_RUN / (ms_c / 1e3),
+            "adaptive_over_dense": ms_full_dense / ms_c,
+            "mean_nonfrozen_ratio": st_c["active_ratio_sum"] / max(1, st_c["step"]),
+            "rel_l2_vs_dense": rel_c, "final_threshold": st_c["threshold"], "controls": st_c["controls"],
+            "autotune_chosen": tune_c["candidates"][tune_c["chosen"]]}
+        pl.close()
+        del f_c
 
     # ---- staged form (a separate update kernel, the paper's workflow): update-stage time
     staged = {}
@@ -483,6 +508,11 @@ def run_ours(args, rank, world, local_rank, parity=None):
                      "rel_l2_adaptive_vs_dense": rel_ada_dense,
                      "kernels": kinds_full,
                      "note": "each plan in the configuration its autotuner chose at step %d" % TUNE_AT},
+        "threshold_control": {"targets": control, "control_every": CONTROL_EVERY, "eta": CONTROL_ETA,
+                              "initial_threshold": THRESHOLD,
+                              "note": "dynamic threshold control (S1.3); whole %d-step runs from c0, each plan "
+                                      "autotuned at step %d; mean_nonfrozen_ratio counts the all-active steps "
+                                      "(one per check) as 1" % (FULL_RUN, TUNE_AT)},
         "staged_form": {"adaptive_steps_per_s": staged["adaptive"]["steps_per_s"],
                         "dense_steps_per_s": staged["dense"]["steps_per_s"],
                         "update_stage_steps_per_s": {"adaptive": 1e3 / sa if sa > 0 else None,

@@ -81,6 +81,17 @@ typedef struct spdba_options {
     double dt, kappa, dx;   /* Cahn-Hilliard: time step, gradient coefficient, spacing  */
     double beta2, gamma, h, dt_sample; /* NLS: ps^2/km, 1/(W km), km step, ps sample     */
     void* stream;           /* cudaStream_t the plan enqueues on                         */
+    /* Dynamic threshold control (S1.3), adaptive plans without a predictor.  Every
+       control_every steps (once the warm-up is over) each run compares its mean share
+       r of non-frozen blocks over the adaptive steps since the last check with
+       target_ratio: with q = r / target_ratio the threshold coefficient is doubled
+       (q > 2), halved (q < 0.5), scaled by 1 + control_eta (q > 1 + eta) or
+       1 - control_eta (q < 1 - eta), or kept; the check step itself runs with every
+       block ACTIVE (the full-activation step that follows each check).  The
+       coefficient is `threshold` of spdba_plan_create under either tau_rule. */
+    double target_ratio;    /* 0 = control off (default)                                   */
+    double control_eta;     /* relative deadband and step factor, default 0.05             */
+    int32_t control_every;  /* control interval in steps, default 50                       */
 } spdba_options;
 
 /* Per-run statistics, refreshed at each reassessment. */
@@ -98,6 +109,8 @@ typedef struct spdba_stats {
     int64_t predictions;     /* reassessments answered by an attached predictor            */
     int64_t missed_blocks;   /* blocks an exact judge found non-frozen that the prediction
                                 in force had frozen (summed over judges)                  */
+    double threshold;        /* threshold coefficient in force (moves under dynamic control) */
+    int64_t controls;        /* dynamic-control decisions made                             */
 } spdba_stats;
 
 typedef struct spdba_plan spdba_plan;         /* opaque; owns all of its device buffers */
@@ -105,7 +118,8 @@ typedef struct spdba_fft_plan spdba_fft_plan; /* opaque; owns its twiddle tables
 
 /* Fill *opt with the defaults: CH, C64, ADAPTIVE, MAXAMP, REL_MAX, transitions on,
    force_dc on (CH), refresh and warm-up off, graphs on, fused update on, dt = 0.01, kappa = 1,
-   dx = 1, beta2 = -21.7, gamma = 1.3, h = 0.1, dt_sample = 1, default stream. */
+   dx = 1, beta2 = -21.7, gamma = 1.3, h = 0.1, dt_sample = 1, default stream, threshold
+   control off (target_ratio 0, control_eta 0.05, control_every 50). */
 void spdba_options_default(spdba_options* opt);
 
 /*

@@ -396,7 +396,9 @@ __global__ void active_tau_kernel(Geom g, const double* __restrict__ msq, int ms
     if (b >= nb) return;
     const long long run = b / g.bpr();
     const double amax = sqrt(gmax[2 * run + (exclude_dc ? 1 : 0)]);
-    const double t = tau_rule == SPDBA_TAU_ABS ? threshold : threshold * amax;
+    // the run's coefficient in force (dynamic threshold control moves it)
+    const double eps = stats ? stats[run].eps : threshold;
+    const double t = tau_rule == SPDBA_TAU_ABS ? eps : eps * amax;
     double m = msq_is_square ? sqrt(msq[b]) : msq[b];
     bool a = (force_dc && b == run * g.bpr()) || (m >= t);
     active[b] = a ? 1 : 0;

@@ -879,7 +879,11 @@ template <typename T, int NT> __device__ __forceinline__ void ch_update_stats(co
     for (long long r = threadIdx.x; r < g.runs(); r += NT) {
         double nf = f.dense ? (double)g.bpr() : (double)(f.stats[r].n_active + f.stats[r].n_transition);
         f.stats[r].ratio_sum += nf * inv;
-        if (!f.dense) f.stats[r].list_modes += nf * (double)bm;
+        if (!f.dense) {
+            f.stats[r].list_modes += nf * (double)bm;
+            f.stats[r].ctl_nf += f.stats[r].n_active + f.stats[r].n_transition;   // control interval
+            f.stats[r].ctl_steps += 1;
+        }
     }
 }
 

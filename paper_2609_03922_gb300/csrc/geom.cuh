@@ -39,6 +39,10 @@ struct DevStats {
     double list_modes;   // modes touched by list-driven updates (for traffic accounting)
     unsigned long long predictions;
     unsigned long long missed;
+    double eps;                     // threshold coefficient in force (dynamic control moves it)
+    unsigned long long ctl_nf;      // non-frozen blocks summed over the control interval's adaptive steps
+    unsigned long long ctl_steps;   // adaptive steps in the control interval
+    unsigned long long controls;    // control decisions made
 };
 
 }  // namespace spdba

@@ -36,7 +36,45 @@ __global__ void ratio_kernel(DevStats* stats, long long nruns, long long bpr, lo
     for (long long r = threadIdx.x; r < nruns; r += blockDim.x) {
         double nf = dense ? (double)bpr : (double)(stats[r].n_active + stats[r].n_transition);
         stats[r].ratio_sum += nf / (double)bpr;
-        if (!dense) stats[r].list_modes += nf * (double)bmodes;
+        if (!dense) {
+            stats[r].list_modes += nf * (double)bmodes;
+            stats[r].ctl_nf += stats[r].n_active + stats[r].n_transition;   // control interval
+            stats[r].ctl_steps += 1;
+        }
+    }
+}
+// Statistics of runs [0, n) reset, with the threshold coefficient in force set to eps.
+__global__ void stats_reset_kernel(DevStats* stats, long long n, double eps) {
+    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+        stats[r] = DevStats{};
+        stats[r].eps = eps;
+    }
+}
+
+// Dynamic threshold control (S1.3): with q = r / r_tar the coefficient is
+// doubled (q > 2) or halved (q < 0.5), else scaled by 1 + eta or 1 - eta
+// outside the relative deadband, else kept.
+__device__ __forceinline__ double control_decision(double eps, double r, double r_tar, double eta) {
+    const double q = r / r_tar;
+    if (q > 2.0) return eps * 2.0;
+    if (q < 0.5) return eps * 0.5;
+    if (q > 1.0 + eta) return eps * (1.0 + eta);
+    if (q < 1.0 - eta) return eps * (1.0 - eta);
+    return eps;
+}
+// One decision per run from the control interval's mean non-frozen share
+// r = ctl_nf / (ctl_steps * blocks per run) (exact integer counts, one
+// rounding in the quotient); the interval restarts.  Runs without an adaptive
+// step in the interval keep their coefficient.
+__global__ void control_kernel(DevStats* stats, long long nruns, long long bpr, double r_tar, double eta) {
+    for (long long r = threadIdx.x; r < nruns; r += blockDim.x) {
+        DevStats& s = stats[r];
+        if (s.ctl_steps == 0) continue;
+        const double ratio = (double)s.ctl_nf / ((double)s.ctl_steps * (double)bpr);
+        s.eps = control_decision(s.eps, ratio, r_tar, eta);
+        s.ctl_nf = 0;
+        s.ctl_steps = 0;
+        s.controls += 1;
     }
 }
 
@@ -268,7 +306,8 @@ template <typename T> static spdba_status group_buffers(spdba_plan* p, Group<T>&
     if ((s = r.alloc(&r.scratch, classify_scratch_bytes(nb))) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.stats, sizeof(DevStats) * r.batch)) != SPDBA_OK) return s;
     SPDBA_CUDA(cudaMemsetAsync(r.c_hat, 0, sizeof(cx_t<T>) * tot, st));
-    SPDBA_CUDA(cudaMemsetAsync(r.stats, 0, sizeof(DevStats) * r.batch, st));
+    stats_reset_kernel<<<1, 256, 0, st>>>(r.stats, r.batch, p->threshold);
+    SPDBA_CUDA(cudaGetLastError());
     SPDBA_CUDA(cudaMemsetAsync(r.gmax, 0, sizeof(double) * 2 * r.batch, st));
     SPDBA_CUDA(cudaMemsetAsync(r.states, SPDBA_ACTIVE, nb, st));
     SPDBA_CUDA(cudaMemsetAsync(r.chi, 0, nb, st));
@@ -541,8 +580,25 @@ template <typename T> static spdba_status group_assess_predicted(spdba_plan* p, 
     return SPDBA_OK;
 }
 
+// A dynamic-control check happens at the start of this step (S1.3): every
+// control_every steps once the warm-up is over.
+static bool control_step(const spdba_plan* p, int64_t step) {
+    return p->opt.mode == SPDBA_MODE_ADAPTIVE && p->opt.target_ratio > 0 && step > p->opt.warmup_steps &&
+           step % p->opt.control_every == 0;
+}
+
+// Warm-up, refresh and control steps update every block.
 static bool all_active_step(const spdba_plan* p, int64_t step) {
-    return step < p->opt.warmup_steps || (p->opt.refresh_every > 0 && step > 0 && step % p->opt.refresh_every == 0);
+    return step < p->opt.warmup_steps || (p->opt.refresh_every > 0 && step > 0 && step % p->opt.refresh_every == 0) ||
+           control_step(p, step);
+}
+
+// The control decision of a group's runs, before the step's reassessment.
+template <typename T> static spdba_status group_control(spdba_plan* p, Group<T>& r) {
+    control_kernel<<<1, 256, 0, p->st>>>(r.stats, r.batch, r.g.bpr(), p->opt.target_ratio, p->opt.control_eta);
+    SPDBA_CUDA(cudaGetLastError());
+    p->launches += 1;
+    return SPDBA_OK;
 }
 
 // Whether the kernels of step `step` are recorded by an active profile.
@@ -559,6 +615,7 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
     const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
     const int interval = p->pred ? p->horizon : p->reassess;
     const bool reassess = adaptive && (!r.assessed || r.step % interval == 0);
+    if (control_step(p, r.step) && (s = group_control<T>(p, r)) != SPDBA_OK) return s;
     if (reassess) {
         s = p->pred ? group_assess_predicted<T>(p, r) : group_assess<T>(p, r);
         if (s != SPDBA_OK) return s;
@@ -735,6 +792,7 @@ template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T
         prof_select(p, r.step);
         const bool reassess = adaptive && (!r.assessed || r.step % p->reassess == 0);
         const int dense = !adaptive || all_active_step(p, r.step);
+        if (control_step(p, r.step) && (s = group_control<T>(p, r)) != SPDBA_OK) return s;
         NLSArgs<T> a = nls_args<T>(p, r, r.c_hat, r.batch, dense);
         if (r.long_nls) {
             // close the previous step unless this step's row pass can take it over
@@ -933,7 +991,8 @@ static spdba_status run_set_field(spdba_plan* p, Group<T>& r, long long sub, con
     r.assessed = false;
     r.has_snap = false;
     r.has_pred = false;
-    SPDBA_CUDA(cudaMemsetAsync(r.stats + sub, 0, sizeof(DevStats), st));
+    stats_reset_kernel<<<1, 32, 0, st>>>(r.stats + sub, 1, p->threshold);
+    SPDBA_CUDA(cudaGetLastError());
     SPDBA_CUDA(cudaMemsetAsync(r.states + sub * r.g.bpr(), SPDBA_ACTIVE, r.g.bpr(), st));
     return SPDBA_OK;
 }
@@ -1027,9 +1086,16 @@ extern "C" void spdba_options_default(spdba_options* o) {
     o->h = 0.1;
     o->dt_sample = 1.0;
     o->stream = nullptr;
+    o->target_ratio = 0.0;
+    o->control_eta = 0.05;
+    o->control_every = 50;
 }
 
 static spdba_status check_opts(const spdba_options* o, int ndim) {
+    if (!(o->target_ratio >= 0.0 && o->target_ratio <= 1.0))
+        return fail(SPDBA_ERR_ARG, "target_ratio must lie in [0, 1]");
+    if (o->target_ratio > 0 && (!(o->control_eta > 0.0 && o->control_eta < 1.0) || o->control_every < 1))
+        return fail(SPDBA_ERR_ARG, "threshold control needs 0 < control_eta < 1 and control_every >= 1");
     if (o->model != SPDBA_MODEL_CH && o->model != SPDBA_MODEL_NLS) return fail(SPDBA_ERR_ARG, "bad model %d", o->model);
     if (o->precision != SPDBA_C64 && o->precision != SPDBA_C128)
         return fail(SPDBA_ERR_ARG, "bad precision %d", o->precision);
@@ -1355,6 +1421,8 @@ template <typename T> static spdba_status get_stats_t(spdba_plan* p, Group<T>& r
     out->active_ratio_sum = d.ratio_sum;
     out->predictions = (int64_t)d.predictions;
     out->missed_blocks = (int64_t)d.missed;
+    out->threshold = d.eps;
+    out->controls = (int64_t)d.controls;
     return SPDBA_OK;
 }
 
@@ -1449,6 +1517,8 @@ template <typename T> static spdba_status attach_t(spdba_plan* p, spdba_predicto
     auto& gs = groups<T>(p);
     if (gs.size() != 1 || gs[0]->ndim != 3 || gs[0]->batch != 1 || p->opt.model != SPDBA_MODEL_CH)
         return fail(SPDBA_ERR_UNSUPPORTED, "a predictor attaches to a 3-D Cahn-Hilliard plan with one run");
+    if (p->opt.target_ratio > 0)
+        return fail(SPDBA_ERR_STATE, "a predictor does not attach to a plan under dynamic threshold control");
     Group<T>& r = *gs[0];
     if (!spdba_predictor_map_matches(pr, r.g.nb[0], r.g.nb[1], r.g.nb[2]))
         return fail(SPDBA_ERR_ARG, "predictor block map does not match the plan's");

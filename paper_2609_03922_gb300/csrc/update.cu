@@ -79,9 +79,12 @@ __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
     if (blockIdx.x == 0 && a.stats) {
         const double inv = 1.0 / (double)g.bpr();
         for (long long r = threadIdx.x; r < g.runs(); r += blockDim.x) {
-            double nf = (double)(a.stats[r].n_active + a.stats[r].n_transition);
+            const unsigned long long nfi = a.stats[r].n_active + a.stats[r].n_transition;
+            double nf = (double)nfi;
             a.stats[r].ratio_sum += nf * inv;
             a.stats[r].list_modes += nf * (double)nmodes;
+            a.stats[r].ctl_nf += nfi;       // an adaptive step of the control interval
+            a.stats[r].ctl_steps += 1;
         }
     }
     const int H = B2 / 2;

@@ -30,14 +30,17 @@ class spdba_options(ctypes.Structure):
                 ("half_spectrum", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("dx", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("gamma", ctypes.c_double), ("h", ctypes.c_double),
-                ("dt_sample", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("dt_sample", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("target_ratio", ctypes.c_double), ("control_eta", ctypes.c_double),
+                ("control_every", ctypes.c_int32)]
 
 
 class spdba_stats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("assessments", ctypes.c_int64), ("nblocks", ctypes.c_int64),
                 ("n_active", ctypes.c_int64), ("n_transition", ctypes.c_int64), ("tau", ctypes.c_double),
                 ("max_amp", ctypes.c_double), ("mass", ctypes.c_double), ("active_ratio_sum", ctypes.c_double),
-                ("predictions", ctypes.c_int64), ("missed_blocks", ctypes.c_int64)]
+                ("predictions", ctypes.c_int64), ("missed_blocks", ctypes.c_int64),
+                ("threshold", ctypes.c_double), ("controls", ctypes.c_int64)]
 
 
 class spdba_tune_report(ctypes.Structure):
