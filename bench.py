@@ -573,9 +573,10 @@ def start_oracle(full_steps, small_steps):
 
 
 def oracle_rel_l2(x, ref):
-    """rel-L2 = ||x - ref||_2 / ||ref||_2 (FP64)."""
-    x = np.asarray(x, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
+    """rel-L2 = ||x - ref||_2 / ||ref||_2 (FP64; complex fields in complex128)."""
+    dt = np.complex128 if (np.iscomplexobj(x) or np.iscomplexobj(ref)) else np.float64
+    x = np.asarray(x, dtype=dt)
+    ref = np.asarray(ref, dtype=dt)
     return float(np.linalg.norm((x - ref).ravel()) / np.linalg.norm(ref.ravel()))
 
 
@@ -653,28 +654,35 @@ def run_ch2d128(args, oracle_fut=None):
             res[mode] = (ms, pl.get_field(), pl.get_stats())
             pl.close()
     rel = float(np.linalg.norm(res[1][1] - res[0][1]) / np.linalg.norm(res[0][1]))
+    extra = {"dtype": "f64", "dense_steps_per_s": steps / (res[0][0] / 1e3),
+             "rel_l2_adaptive_vs_dense": rel,
+             "mean_nonfrozen_ratio": res[1][2]["active_ratio_sum"] / steps}
+    extra.update(_oracle_leg(oracle_fut, {"run0": res[1][1]}, "the whole 200-step adaptive run (FP64 oracle)"))
     return _line("spectral steps/s adaptive vs dense, 2-D CH 128^2 FP64", steps / (res[1][0] / 1e3), "steps/s", steps,
-                 steps, res[1][0], {"workload": "ch2d-128^2-c128-B16-R10", "steps": steps},
-                 {"dtype": "f64", "dense_steps_per_s": steps / (res[0][0] / 1e3),
-                  "rel_l2_adaptive_vs_dense": rel,
-                  "mean_nonfrozen_ratio": res[1][2]["active_ratio_sum"] / steps})
+                 steps, res[1][0], {"workload": "ch2d-128^2-c128-B16-R10", "steps": steps}, extra)
 
 
 def run_nls512(args, oracle_fut=None):
     """512 NLS signals, lengths 2^e (e uniform 12..18), 8 QPSK channels each, 64 blocks/signal,
-    h = 0.1 km over 80 km (800 steps), one plan (groups by length), graphs on a side stream."""
+    h = 0.1 km over 80 km (800 steps), one plan (groups by length), graphs on a side stream;
+    adaptive at the fixed threshold, dense, and dynamic threshold control at 5/10/20 %."""
     import torch
     from paper_2609_03922_gb300 import spdba
     import workloads as W
     lengths = W.nls_lengths(512)
     steps = 800
     sigs = [W.nls_signal(n, seed=W.BASE_SEED + 1 + i).astype(np.complex64) for i, n in enumerate(lengths)]
+    pick = _nls_oracle_pick()
     side = torch.cuda.Stream()
     res = {}
     with torch.cuda.stream(side):
-        for mode in (1, 0):
-            pl = spdba.Plan(None, (-64,), threshold=1e-6, reassess=10, batch_dims=[(n,) for n in lengths],
-                            model=spdba.SPDBA_MODEL_NLS, precision=spdba.SPDBA_C64, mode=mode)
+        for name, mode, kw in ([("adaptive", 1, {}), ("dense", 0, {})] +
+                               [("control_%g" % t, 1, {"target_ratio": t, "control_every": CONTROL_EVERY,
+                                                       "control_eta": CONTROL_ETA}) for t in CONTROL_TARGETS]):
+            # under control the threshold starts at the paper's DBP value (S5.3: 1e-4)
+            thr0 = NLS_CONTROL_THRESHOLD0 if "target_ratio" in kw else 1e-6
+            pl = spdba.Plan(None, (-64,), threshold=thr0, reassess=10, batch_dims=[(n,) for n in lengths],
+                            model=spdba.SPDBA_MODEL_NLS, precision=spdba.SPDBA_C64, mode=mode, **kw)
 
             def setin():
                 for r, x in enumerate(sigs):
@@ -682,24 +690,38 @@ def run_nls512(args, oracle_fut=None):
             _timed_steps(pl, 20, setin, side)
             ms = _timed_steps(pl, steps, setin, side)
             ratio = float(np.mean([pl.get_stats(run=r)["active_ratio_sum"] / steps for r in range(0, 512, 37)]))
-            f0 = pl.get_field(run=0)
+            fields = {i: pl.get_field(run=i) for i in pick}
             kinds = None
-            if mode == 1:
+            if name == "adaptive":
                 # per-kernel event timing of a short stretch (graph replay off while profiling)
                 pl.profile_begin()
                 pl.step(40)
                 kinds = _kind_summary(pl.profile_end())
-            res[mode] = (ms, ratio, f0, kinds)
+            res[name] = (ms, ratio, fields, kinds)
             pl.close()
     total = int(sum(lengths))
-    rel = float(np.linalg.norm(res[1][2] - res[0][2]) / np.linalg.norm(res[0][2]))
-    return _line("NLS batch steps/s (512 signals, all advance one split step)", steps / (res[1][0] / 1e3), "steps/s",
-                 steps, 20, res[1][0], {"workload": "nls-512-signals-2^12..2^18-c64-64blocks", "samples": total},
-                 {"dtype": "c64", "dense_steps_per_s": steps / (res[0][0] / 1e3),
-                  "samples_per_s": total * steps / (res[1][0] / 1e3),
-                  "hbm_gbs_at_two_passes_per_step": 2 * 16 * total * steps / (res[1][0] / 1e3) / 1e9,
-                  "mean_nonfrozen_ratio_sampled": res[1][1], "rel_l2_adaptive_vs_dense_signal0": rel,
-                  "kernels": res[1][3]})
+
+    def rel_vs_dense(name):
+        return max(float(np.linalg.norm(res[name][2][i] - res["dense"][2][i]) / np.linalg.norm(res["dense"][2][i]))
+                   for i in pick)
+    extra = {"dtype": "c64", "dense_steps_per_s": steps / (res["dense"][0] / 1e3),
+             "samples_per_s": total * steps / (res["adaptive"][0] / 1e3),
+             "hbm_gbs_at_two_passes_per_step": 2 * 16 * total * steps / (res["adaptive"][0] / 1e3) / 1e9,
+             "mean_nonfrozen_ratio_sampled": res["adaptive"][1],
+             "rel_l2_adaptive_vs_dense_max_over_subset": rel_vs_dense("adaptive"),
+             "threshold_control": {"%g" % t: {"steps_per_s": steps / (res["control_%g" % t][0] / 1e3),
+                                              "over_dense": res["dense"][0] / res["control_%g" % t][0],
+                                              "mean_nonfrozen_ratio_sampled": res["control_%g" % t][1],
+                                              "rel_l2_vs_dense_max_over_subset": rel_vs_dense("control_%g" % t)}
+                                   for t in CONTROL_TARGETS},
+             "kernels": res["adaptive"][3]}
+    extra.update(_oracle_leg(oracle_fut, res["adaptive"][2],
+                             "signals %s (the first of each length), all 800 steps from the complex64-rounded "
+                             "input (FP64 oracle); complex64 error includes the FP32 floor of the modulation "
+                             "instability" % pick))
+    return _line("NLS batch steps/s (512 signals, all advance one split step)", steps / (res["adaptive"][0] / 1e3),
+                 "steps/s", steps, 20, res["adaptive"][0],
+                 {"workload": "nls-512-signals-2^12..2^18-c64-64blocks", "samples": total}, extra)
 
 
 def run_ensemble64(args, oracle_fut=None):
@@ -722,6 +744,8 @@ def run_ensemble64(args, oracle_fut=None):
         _timed_steps(pl, 20, setin, side)
         ms_g = _timed_steps(pl, steps, setin, side)
         ratio = float(np.mean([pl.get_stats(run=r)["active_ratio_sum"] / steps for r in range(64)]))
+        pick = [r for r, (sd, _, _) in enumerate(members) if sd <= 256][:ENSEMBLE_ORACLE_RUNS]
+        fields = {r: pl.get_field(run=r) for r in pick}
         pl.close()
         plans = [spdba.Plan((sd, sd), (16, 16), threshold=1e-6, reassess=10, precision=spdba.SPDBA_C64, use_graph=0)
                  for sd, _, _ in members]
@@ -744,10 +768,12 @@ def run_ensemble64(args, oracle_fut=None):
         for p_ in plans:
             p_.close()
     pts = sum(sd * sd for sd, _, _ in members)
+    extra = {"dtype": "c64", "per_run_plans_steps_per_s": steps / (ms_p / 1e3),
+             "grouped_over_per_run": ms_p / ms_g, "mean_nonfrozen_ratio": ratio}
+    extra.update(_oracle_leg(oracle_fut, fields, "runs %s (the first of side <= 256), all 1000 steps (FP64 "
+                                                 "oracle, own scans)" % pick))
     return _line("ensemble steps/s (64 uneven CH runs, all advance one step)", steps / (ms_g / 1e3), "steps/s", steps,
-                 20, ms_g, {"workload": "ch2d-ensemble-64-runs-128..512-c64-B16", "points": pts},
-                 {"dtype": "c64", "per_run_plans_steps_per_s": steps / (ms_p / 1e3),
-                  "grouped_over_per_run": ms_p / ms_g, "mean_nonfrozen_ratio": ratio})
+                 20, ms_g, {"workload": "ch2d-ensemble-64-runs-128..512-c64-B16", "points": pts}, extra)
 
 
 def run_ch3d384pred(args, oracle_fut=None):
@@ -785,6 +811,18 @@ def run_ch3d384pred(args, oracle_fut=None):
         pl.close()
     d = out["dense"]["field"].astype(np.float64)
     rel = {k: float(np.linalg.norm(out[k]["field"] - d) / np.linalg.norm(d)) for k in ("predictor", "exact")}
+    # the same predictor at 64^3 (8^3 map) over the configuration's 5000 steps, against the
+    # oracle's exact adaptive run (its own scans): the predictor's method error plus arithmetic
+    pr8 = spdba.Predictor((8,) * 3, max_batch=1, params=pr32.params())
+    c0s = W.ch_initial_condition(PRED_SMALL, mean=0.1, seed=W.BASE_SEED).astype(np.float32)
+    small = {}
+    for name, pred in (("predictor", pr8), ("exact", None)):
+        with spdba.Plan(PRED_SMALL, (8, 8, 8), threshold=1e-6, reassess=10, precision=spdba.SPDBA_C64) as pl:
+            if pred is not None:
+                pl.attach_predictor(pred, 20, 100, 0.5)
+            pl.set_field(c0s)
+            pl.step(steps)
+            small[name] = pl.get_field()
     sp, se = out["predictor"]["stats"], out["exact"]["stats"]
     return _line("spectral steps/s with the learned predictor, 3-D CH 384^3", steps / (out["predictor"]["ms"] / 1e3),
                  "steps/s", steps, 0, out["predictor"]["ms"], {"workload": "ch3d-384^3-c64-B8-K20-J100"},
@@ -795,14 +833,91 @@ def run_ch3d384pred(args, oracle_fut=None):
                   "predictions": sp["predictions"], "missed_blocks": sp["missed_blocks"],
                   "mean_nonfrozen_ratio": {"predictor": sp["active_ratio_sum"] / steps,
                                            "exact": se["active_ratio_sum"] / steps},
-                  "training": {"loss_first_last": [hist[0], hist[-1]], "seconds": t_train}})
+                  "training": {"loss_first_last": [hist[0], hist[-1]], "seconds": t_train},
+                  **_oracle_leg(oracle_fut, {"small": small["predictor"]},
+                                "64^3 (8^3 blocks), 5000 steps, the oracle's exact adaptive run (R = 10) against "
+                                "the GPU predictor-driven run (K = 20, J = 100) with the same network"),
+                  "rel_l2_exact_gpu_vs_oracle_64cubed": (oracle_rel_l2(small["exact"], oracle_fut.result()["fields"]
+                                                                       ["small"]) if oracle_fut else None)})
 
 
-ORACLE_JOBS = {}
+# ------------------------------------------------------------------ oracle legs of the other workloads
+NLS_ORACLE_SUBSET = 7        # the first signal of each length 2^12..2^18
+ENSEMBLE_ORACLE_RUNS = 8     # the first runs of side <= 256
+PRED_SMALL = (64, 64, 64)    # the predictor configuration at a size the oracle finishes
+NLS_CONTROL_THRESHOLD0 = 1e-4  # initial threshold of the DBP runs under control (S5.3)
+
+
+def _nls_oracle_pick():
+    import workloads as W
+    seen, pick = set(), []
+    for i, n in enumerate(W.nls_lengths(512)):
+        if n not in seen:
+            seen.add(n)
+            pick.append(i)
+    return sorted(pick)[:NLS_ORACLE_SUBSET]
+
+
+def workload_oracle_job(workload, threads):
+    """The FP64 oracle's own free-running runs (its own scans) on a bounded subset
+    of a workload, timed: returns {"fields": {key: field}, "seconds", "steps", "cores"}."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import oracle as O
+    import workloads as W
+    out, t0 = {}, time.perf_counter()
+    units = 0
+    if workload == "ch2d128":
+        c0 = W.ch_initial_condition((128, 128), mean=0.0, seed=W.BASE_SEED)
+        ch, _ = O.run_ch(c0, O.CHConfig((128, 128), (16, 16), threshold=1e-6, reassess=10), 200)
+        out["run0"] = O.ch_real_field(ch)
+        units = 200
+    elif workload == "nls512":
+        lengths = W.nls_lengths(512)
+        for i in _nls_oracle_pick():
+            n = lengths[i]
+            E0 = W.nls_signal(n, seed=W.BASE_SEED + 1 + i).astype(np.complex64).astype(np.complex128)
+            E, _ = O.run_nls(E0, O.NLSConfig(n, n // 64, threshold=1e-6, reassess=10), 800)
+            out[i] = E
+            units += 800
+    elif workload == "ensemble64":
+        members = W.ensemble_members(64)
+        pick = [r for r, (sd, _, _) in enumerate(members) if sd <= 256][:ENSEMBLE_ORACLE_RUNS]
+        for r in pick:
+            sd, m, seed = members[r]
+            c0 = W.ch_initial_condition((sd, sd), mean=m, seed=seed).astype(np.float32).astype(np.float64)
+            ch, _ = O.run_ch(c0, O.CHConfig((sd, sd), (16, 16), threshold=1e-6, reassess=10), 1000)
+            out[r] = O.ch_real_field(ch)
+            units += 1000
+    elif workload == "ch3d384pred":
+        c0 = W.ch_initial_condition(PRED_SMALL, mean=0.1, seed=W.BASE_SEED).astype(np.float32).astype(np.float64)
+        ch, _ = O.run_ch(c0, O.CHConfig(PRED_SMALL, (8, 8, 8), threshold=1e-6, reassess=10), 5000)
+        out["small"] = O.ch_real_field(ch)
+        units = 5000
+    return {"fields": out, "seconds": time.perf_counter() - t0, "steps": units, "cores": O.num_threads()}
+
+
+ORACLE_JOBS = ("ch2d128", "nls512", "ensemble64", "ch3d384pred")
 
 
 def start_workload_oracle(workload):
-    return None
+    """Start the workload's oracle leg in a spawned process (before any CUDA call)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    threads = max(1, (os.cpu_count() or 2) - 2)
+    ex = cf.ProcessPoolExecutor(max_workers=1, mp_context=mp.get_context("spawn"))
+    return ex.submit(workload_oracle_job, workload, threads)
+
+
+def _oracle_leg(fut, gpu_fields, sample):
+    """cpu_baseline and rel_l2_vs_oracle of a workload line from its oracle leg."""
+    if fut is None:
+        return {}
+    o = fut.result()
+    rel = {str(k): oracle_rel_l2(gpu_fields[k], o["fields"][k]) for k in o["fields"] if k in gpu_fields}
+    return {"cpu_baseline": {"value": o["steps"] / o["seconds"], "unit": "run-steps/s", "cores": o["cores"],
+                             "kind": "oracle", "sample": sample},
+            "rel_l2_vs_oracle": rel,
+            "rel_l2_vs_oracle_max": max(rel.values()) if rel else None}
 
 
 def main():

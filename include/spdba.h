@@ -125,7 +125,10 @@ void spdba_options_default(spdba_options* opt);
 /*
  * Create a plan for one field (spdba_init of S2.1).
  *   ndim        1, 2 or 3 (NLS: 1; CH: 2 or 3)
- *   dims[ndim]  grid extents, each of the form 2^a 3^b; CH axes 8..512, NLS 64..2^18
+ *   dims[ndim]  grid extents; CH axes in {16, 32, 64, 128, 192, 256, 384, 512};
+ *               NLS lengths 64..4096 (powers of two) and n1 * 512 with n1 in
+ *               {16, 32, ..., 512} (up to 2^18); other lengths of the form
+ *               2^a 3^b return SPDBA_ERR_UNSUPPORTED
  *   block[ndim] block edge per axis; must divide dims; the block map is
  *               dims[a]/block[a] per axis, row-major, slowest axis first
  *               (block b along an axis covers FFT indices [b*B, b*B + B - 1])
@@ -255,8 +258,11 @@ int64_t spdba_debug_live_allocs(void);
  * Batched multi-dimensional complex FFT (Stockham, shared-memory staged), the
  * transform that surrounds every sp-DBA update (Methods, Fig. 1b).
  * `batch` transforms of shape dims[0..ndim-1], contiguous one after another.
- * Each axis must be 2^a 3^b; axes of 2-D/3-D transforms 8..512, 1-D lengths
- * 8..2^18.  Twiddles are computed in FP64 once, at plan creation.
+ * Supported lengths: axes of 2-D/3-D transforms in {16, 32, 64, 128, 192,
+ * 256, 384, 512}; 1-D lengths in {16, ..., 4096} of that set plus 1024, 2048,
+ * 4096, and n1 * 512 with n1 in {16, 32, 64, 128, 192, 256, 384, 512} (up to
+ * 2^18); anything else returns SPDBA_ERR_UNSUPPORTED.  Twiddles are computed
+ * in FP64 once, at plan creation.
  */
 spdba_status spdba_fft_plan_create(spdba_fft_plan** out, int32_t precision, int32_t ndim,
                                    const int64_t* dims, int64_t batch);

@@ -17,6 +17,8 @@
  * Lengths with a prime factor above 3 fall back to the O(n^2) definition.
  * Twiddles are cos/sin of 2*pi*m/n in double precision for the integer
  * m = (r*k) mod n, reduced before the multiply.  Nothing is blocked or fused.
+ * A single long 1-D transform runs its top recursion levels' sub-transforms
+ * as parallel tasks; that changes the schedule, not one operation.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -46,6 +48,24 @@ static cplx* make_table(long n, int sign) {
 }
 
 /*
+ * Recombination of the p sub-transforms X_r (in out[r*q .. r*q+q-1], q = n/p):
+ * X[k] = sum_r W_n^{r k} X_r[k mod q], formed in scratch and copied back to out.
+ */
+static void recombine(long n, long p, const cplx* tab, long ts, cplx* out, cplx* scratch) {
+    long q = n / p;
+    for (long k = 0; k < n; ++k) {
+        cplx acc = {0.0, 0.0};
+        for (long r = 0; r < p; ++r) {
+            long m = (r * k) % n;
+            cplx v = cmul(out[r * q + (k % q)], tab[m * ts]);
+            acc.re += v.re; acc.im += v.im;
+        }
+        scratch[k] = acc;
+    }
+    memcpy(out, scratch, sizeof(cplx) * (size_t)n);
+}
+
+/*
  * Transform n values x[0], x[xs], x[2 xs], ... into out[0..n-1].
  * tab holds W_{n0}^m for the top-level length n0; this level uses
  * W_n^m = tab[m * ts] with ts = n0 / n.  scratch has room for n values.
@@ -72,17 +92,30 @@ static void fft_rec(const cplx* x, long xs, long n, const cplx* tab, long ts, lo
     /* sub-transforms X_r of the subsequences x[p*m + r] land in out[r*q .. r*q+q-1] */
     for (long r = 0; r < p; ++r)
         fft_rec(x + r * xs, xs * p, q, tab, ts * p, n0, out + r * q, scratch + r * q);
-    /* recombine into scratch, then copy back */
-    for (long k = 0; k < n; ++k) {
-        cplx acc = {0.0, 0.0};
-        for (long r = 0; r < p; ++r) {
-            long m = (r * k) % n;
-            cplx v = cmul(out[r * q + (k % q)], tab[m * ts]);
-            acc.re += v.re; acc.im += v.im;
-        }
-        scratch[k] = acc;
+    recombine(n, p, tab, ts, out, scratch);
+}
+
+/*
+ * fft_rec with the p sub-transforms of the top `depth_left` levels run as
+ * OpenMP tasks (they read disjoint inputs and write disjoint parts of out and
+ * scratch).  Every output is formed by exactly the same operations in the same
+ * order as in fft_rec: only the schedule differs.  Call inside a parallel
+ * region, from one thread.
+ */
+static void fft_rec_tasks(const cplx* x, long xs, long n, const cplx* tab, long ts, long n0,
+                          cplx* out, cplx* scratch, int depth_left) {
+    long p = (n % 2 == 0) ? 2 : (n % 3 == 0) ? 3 : 0;
+    if (depth_left <= 0 || p == 0 || n < 4096) {
+        fft_rec(x, xs, n, tab, ts, n0, out, scratch);
+        return;
     }
-    memcpy(out, scratch, sizeof(cplx) * (size_t)n);
+    long q = n / p;
+    for (long r = 0; r < p; ++r) {
+#pragma omp task firstprivate(r)
+        fft_rec_tasks(x + r * xs, xs * p, q, tab, ts * p, n0, out + r * q, scratch + r * q, depth_left - 1);
+    }
+#pragma omp taskwait
+    recombine(n, p, tab, ts, out, scratch);
 }
 
 /*
@@ -106,6 +139,19 @@ int oracle_fftn(double* data, int ndim, const long* dims, int sign, int normaliz
         cplx* tab = make_table(n, sign);
         if (!tab) return -2;
         long npencil = outer * inner;
+        if (npencil == 1) {
+            /* one long transform: its recursion's sub-transforms run as tasks */
+            cplx* buf = (cplx*)malloc(sizeof(cplx) * (size_t)n * 3);
+            if (!buf) { free(tab); return -2; }
+            memcpy(buf, z, sizeof(cplx) * (size_t)n);
+#pragma omp parallel
+#pragma omp single
+            fft_rec_tasks(buf, 1, n, tab, 1, n, buf + n, buf + 2 * n, 4);
+            memcpy(z, buf + n, sizeof(cplx) * (size_t)n);
+            free(buf);
+            free(tab);
+            continue;
+        }
 #pragma omp parallel
         {
             cplx* buf = (cplx*)malloc(sizeof(cplx) * (size_t)n * 3);

@@ -73,3 +73,14 @@ def test_single_mode_lands_on_its_bin():
     expect = np.zeros(n, dtype=complex)
     expect[m] = n
     assert np.max(np.abs(X - expect)) <= 1e-12 * n
+
+
+@pytest.mark.parametrize("n", [1 << 18, 3 * (1 << 13), 4096 * 27])
+def test_long_transform_task_schedule_is_bit_identical(n):
+    """A single long 1-D transform runs its recursion's sub-transforms as tasks;
+    the batched entry point runs the same recursion serially.  Same operations,
+    same order: the results must be identical bit for bit."""
+    r = np.random.default_rng(n)
+    x = r.standard_normal(n) + 1j * r.standard_normal(n)
+    assert np.array_equal(O.fftn(x), O.fft_batch(x[None, :])[0])
+    assert np.array_equal(O.ifftn(x), O.ifft_batch(x[None, :])[0])
