@@ -21,6 +21,10 @@ Parity status of each piece (what pins it, see tests/test_oracle_*.py):
                                 control steps are full-activation steps (== Regular)
   nls_* ....................... CW exact solution, dispersion-only closed form,
                                 unitarity, forward/backward recovery
+  rcd_* ....................... circulant eigenvalues in closed form, hand-computed
+                                reaction values, direct solve == eigen form,
+                                linearised single-mode growth matrix, threshold 0 ==
+                                Regular bit for bit
 No function here is "parity unpinned".
 
 Paper conventions restated (section / equation of arXiv 2609.03922):
@@ -42,6 +46,11 @@ Paper conventions restated (section / equation of arXiv 2609.03922):
     check is followed by one full-activation step (S1.3, S3.2 parameters).
   * Semi-implicit Fourier update of a conserved (Cahn-Hilliard form) field
     (S3.1 dynamics, S4.2 semi-implicit update with M = 1).
+  * Reaction-cross-diffusion (S4.1-S4.3): M components, symmetric circulant
+    cross-diffusion matrix D, generalised Lotka-Volterra reaction evaluated in
+    real space, semi-implicit update (I + dt k^2 D)^{-1}[u + dt R] per mode,
+    directly or through D = V Lambda V^T; activation by the component RMS
+    Fourier amplitude, one state per block for all M components.
   * Symmetric split-step Fourier with the linear operator applied in two
     frequency-domain half-steps and the Kerr phase in the time domain (S5.1,
     S5.2); recovery metrics NMSE and field correlation (S5.3).
@@ -72,6 +81,9 @@ __all__ = [
     "nls_kerr", "nls_masked_half", "nls_regular_step", "nls_masked_step", "NLSConfig",
     "run_nls", "rel_l2", "nmse_db", "field_corr", "assess_states", "effective_states",
     "threshold_control", "ThresholdController", "is_control_step",
+    "rcd_diffusion_matrix", "rcd_interaction_matrix", "rcd_reaction", "rcd_homogeneous_state",
+    "rcd_eigen", "rcd_update_direct", "rcd_update_eigen", "rcd_mode_amplitude_sq", "RCDConfig",
+    "rcd_assess_states", "rcd_real_field", "rcd_new", "rcd_masked_step", "run_rcd",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -564,6 +576,194 @@ def run_nls(E0, cfg, steps, on_assess=None, controller=None):
         if controller is not None:
             controller.end_step(s, states)
     return E, history
+
+
+# --------------------------------------------------------------------------------------
+# Reaction-cross-diffusion with M components (S4.1-S4.3)
+# --------------------------------------------------------------------------------------
+def rcd_diffusion_matrix(M, d_diag, d_cross):
+    """Symmetric circulant cross-diffusion matrix (S4.1): D_ii = d_diag + 2 d_cross,
+    D_{i,i+1} = D_{i,i-1} = -d_cross with periodic component index; for M = 2
+    the two neighbours coincide and the single off-diagonal entry is -d_cross."""
+    D = np.zeros((M, M), dtype=np.float64)
+    for i in range(M):
+        D[i, i] = d_diag + 2.0 * d_cross
+        if M > 1:
+            D[i, (i + 1) % M] = -d_cross
+            D[i, (i - 1) % M] = -d_cross
+    return D
+
+
+def rcd_interaction_matrix(M, alpha, beta):
+    """Off-diagonal Lotka-Volterra interactions alpha_ij (S4.1): beta + alpha for the
+    two neighbouring components (periodic index; one entry for M = 2), beta for
+    every other j != i; zero diagonal (self-limitation is a_i)."""
+    A = np.full((M, M), float(beta), dtype=np.float64)
+    np.fill_diagonal(A, 0.0)
+    for i in range(M):
+        if M > 1:
+            A[i, (i + 1) % M] = beta + alpha
+            A[i, (i - 1) % M] = beta + alpha
+    return A
+
+
+def rcd_reaction(u, r, a, A):
+    """Generalised Lotka-Volterra reaction R_i(u) = u_i (r_i - a_i u_i - sum_{j != i}
+    alpha_ij u_j) (S4.1), u of shape (M, ...) (component first)."""
+    M = u.shape[0]
+    inter = np.tensordot(A, u, axes=(1, 0))          # sum_j alpha_ij u_j (alpha_ii = 0)
+    r = np.asarray(r, dtype=np.float64).reshape((M,) + (1,) * (u.ndim - 1))
+    a = np.asarray(a, dtype=np.float64).reshape((M,) + (1,) * (u.ndim - 1))
+    return u * (r - a * u - inter)
+
+
+def rcd_homogeneous_state(M, r, a, alpha, beta):
+    """The equal-concentration fixed point of the reaction: r = u (a + sum_{j != i} alpha_ij)."""
+    return float(r) / (float(a) + float(rcd_interaction_matrix(M, alpha, beta)[0].sum()))
+
+
+def rcd_eigen(D):
+    """D = V diag(lam) V^T (symmetric D; V orthogonal), computed once (S4.3)."""
+    lam, V = np.linalg.eigh(D)
+    return lam, V
+
+
+def rcd_update_direct(b, k2, dt, D):
+    """u_new(k) = (I + dt k^2 D)^{-1} b(k) for every mode (S4.2), one dense M x M
+    solve per distinct |k|^2; b of shape (M, ...) complex."""
+    M = b.shape[0]
+    flat_b = b.reshape(M, -1)
+    flat_k2 = np.asarray(k2, dtype=np.float64).reshape(-1)
+    out = np.empty_like(flat_b)
+    for val in np.unique(flat_k2):
+        sel = flat_k2 == val
+        A = np.eye(M) + dt * val * D
+        out[:, sel] = np.linalg.solve(A, flat_b[:, sel])
+    return out.reshape(b.shape)
+
+
+def rcd_update_eigen(b, k2, dt, V, lam):
+    """The same update through the eigendecomposition (S4.3):
+    V (I + dt k^2 Lambda)^{-1} V^T b."""
+    M = b.shape[0]
+    y = np.tensordot(V.T, b, axes=(1, 0))
+    den = 1.0 + dt * np.asarray(k2, dtype=np.float64)[None, ...] * lam.reshape((M,) + (1,) * (b.ndim - 1))
+    return np.tensordot(V, y / den, axes=(1, 0))
+
+
+def rcd_mode_amplitude_sq(q):
+    """A(k)^2 = (1/M) sum_m |q_m(k)|^2 (S4.2: component RMS Fourier amplitude), FP64."""
+    return np.sum(_mode_sq(q), axis=0) / float(q.shape[0])
+
+
+class RCDConfig:
+    """Parameters of an RCD run (S4.2 defaults: dx = 0.5, dt = 0.01, D_diag = 0.5,
+    D_cross = 0.05, alpha = 1, beta = 0.3, r_i = a_i = 1)."""
+
+    def __init__(self, dims, block, M, threshold=1e-6, reassess=10, dt=0.01, dx=0.5, d_diag=0.5,
+                 d_cross=0.05, alpha=1.0, beta=0.3, r=1.0, a=1.0, mode=1, tau_rule=TAU_REL_MAX,
+                 transitions=True, refresh_every=0, warmup_steps=0, force_dc=True, eigen=True,
+                 target_ratio=0.0, control_every=50, control_eta=0.1):
+        self.dims = tuple(int(x) for x in dims)
+        self.block = tuple(int(x) for x in block)
+        self.M = int(M)
+        self.threshold = float(threshold)
+        self.reassess = int(reassess)
+        self.dt, self.dx = float(dt), float(dx)
+        self.d_diag, self.d_cross = float(d_diag), float(d_cross)
+        self.alpha, self.beta, self.r, self.a = float(alpha), float(beta), float(r), float(a)
+        self.mode = int(mode)
+        self.measure = MEASURE_MAXAMP
+        self.tau_rule = int(tau_rule)
+        self.transitions = bool(transitions)
+        self.refresh_every = int(refresh_every)
+        self.warmup_steps = int(warmup_steps)
+        self.force_dc = bool(force_dc)
+        self.eigen = bool(eigen)
+        self.target_ratio = float(target_ratio)
+        self.control_every = int(control_every)
+        self.control_eta = float(control_eta)
+
+
+def rcd_assess_states(u_hat, cfg, threshold=None):
+    """States from the component RMS amplitude (S4.2): a block is ACTIVE when one of
+    its modes has A(k) >= tau; the state applies to all M components.  tau is
+    threshold * max_{k != 0} A(k) (REL_MAX) or threshold (ABS)."""
+    a2 = rcd_mode_amplitude_sq(u_hat)
+    blk = _blockify(a2, cfg.block)
+    maxsq = blk.max(axis=tuple(range(1, blk.ndim, 2)))
+    measure = np.sqrt(maxsq)
+    thr = cfg.threshold if threshold is None else threshold
+    if cfg.tau_rule == TAU_ABS:
+        tau = float(thr)
+    else:
+        a2x = a2.copy()
+        a2x.flat[0] = 0.0
+        tau = float(thr) * math.sqrt(float(a2x.max()))
+    states = classify(measure, tau, force_dc=cfg.force_dc, transitions=cfg.transitions)
+    return states, tau, measure
+
+
+def rcd_real_field(u_hat):
+    """u_m = Re(IFFT(u_hat_m)) for every component."""
+    return np.stack([np.real(ifftn(q)) for q in u_hat])
+
+
+def rcd_new(u_hat, cfg, k2, D, eig):
+    """The update core of every mode: (I + dt k^2 D)^{-1} [u_hat + dt FFT(R(u))] (S4.2)."""
+    u = rcd_real_field(u_hat)
+    A = rcd_interaction_matrix(cfg.M, cfg.alpha, cfg.beta)
+    R = rcd_reaction(u, np.full(cfg.M, cfg.r), np.full(cfg.M, cfg.a), A)
+    b = u_hat + cfg.dt * np.stack([fftn(x) for x in R])
+    if cfg.eigen:
+        return rcd_update_eigen(b, k2, cfg.dt, eig[1], eig[0])
+    return rcd_update_direct(b, k2, cfg.dt, D)
+
+
+def rcd_masked_step(u_hat, states, cfg, k2, D, eig, sigma=None):
+    """sp-DBA step: ACTIVE blocks take the update core's result for all M
+    components, TRANSITION blocks u + sigma (new - u), FROZEN blocks keep u (S4.2)."""
+    new = rcd_new(u_hat, cfg, k2, D, eig)
+    if states is None:
+        return new
+    if sigma is None:
+        sigma = sigma_field(states, cfg.block)
+    st = _state_field(states, cfg.block)
+    out = np.where(st[None] == STATE_ACTIVE, new, u_hat)
+    tr = st == STATE_TRANSITION
+    out[:, tr] = u_hat[:, tr] + sigma[tr][None, :] * (new[:, tr] - u_hat[:, tr])
+    return out
+
+
+def run_rcd(u0, cfg, steps, u_hat=None, on_assess=None, controller=None):
+    """Advance M real component fields u0 (M, *dims) `steps` steps; returns (u_hat,
+    history of (step, states, tau)).  Same state schedule as run_ch."""
+    k2 = k_squared(cfg.dims, cfg.dx)
+    D = rcd_diffusion_matrix(cfg.M, cfg.d_diag, cfg.d_cross)
+    eig = rcd_eigen(D)
+    if u_hat is None:
+        u_hat = np.stack([fftn(np.asarray(x, dtype=np.float64)) for x in u0])
+    if controller is None and cfg.target_ratio > 0:
+        controller = ThresholdController(cfg, np.prod(block_counts(cfg.dims, cfg.block)))
+    history = []
+    states = None
+    for n in range(steps):
+        if cfg.mode == 0:
+            u_hat = rcd_masked_step(u_hat, None, cfg, k2, D, eig)
+            continue
+        thr = controller.begin_step(n) if controller is not None else None
+        if states is None or n % cfg.reassess == 0:
+            states, tau, _ = rcd_assess_states(u_hat, cfg, threshold=thr)
+            if on_assess is not None:
+                repl = on_assess(n, u_hat, states, tau)
+                if repl is not None:
+                    states = repl
+            history.append((n, states.copy(), tau))
+        eff = effective_states(states, n, cfg)
+        u_hat = rcd_masked_step(u_hat, eff, cfg, k2, D, eig)
+        if controller is not None:
+            controller.end_step(n, states)
+    return u_hat, history
 
 
 # --------------------------------------------------------------------------------------

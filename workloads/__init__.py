@@ -79,3 +79,24 @@ def gaussian_pulse(n, width, amplitude=1.0, center=None):
     t = np.arange(n, dtype=np.float64)
     t0 = n / 2.0 if center is None else center
     return amplitude * np.exp(-((t - t0) ** 2) / (2.0 * width * width)).astype(np.complex128)
+
+
+def rcd_initial_condition(dims, M, base, rel_amplitude=0.1, seed=BASE_SEED):
+    """M component fields near a homogeneous state: base * (1 + rel_amplitude *
+    U[-1, 1]) independently per component and grid point (FP64, (M, *dims))."""
+    u = _rng(seed).random((int(M),) + tuple(int(d) for d in dims))
+    return float(base) * (1.0 + float(rel_amplitude) * (2.0 * u - 1.0))
+
+
+def rcd_lv_homogeneous(M, r=1.0, a=1.0, alpha=1.0, beta=0.3):
+    """Equal-concentration fixed point of the Lotka-Volterra reaction with
+    interactions beta + alpha to the two neighbouring components (one for M = 2)
+    and beta to the others: u* = r / (a + sum_{j != i} alpha_ij).  The base of the
+    RCD initial condition."""
+    if M <= 1:
+        off = 0.0
+    elif M == 2:
+        off = beta + alpha
+    else:
+        off = 2.0 * (beta + alpha) + (M - 3) * beta
+    return float(r) / (float(a) + off)
