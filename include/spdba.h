@@ -46,7 +46,9 @@ typedef enum {
     SPDBA_ERR_STATE = 6         /* call not valid in the plan's current state            */
 } spdba_status;
 
-enum { SPDBA_MODEL_CH = 0, SPDBA_MODEL_NLS = 1 };
+/* CH: Cahn-Hilliard-form semi-implicit step (S3.1, S4.2 with M = 1); NLS: split-step
+   Fourier (S5.1-S5.2); RCD: M-component reaction-cross-diffusion (S4.1-S4.3). */
+enum { SPDBA_MODEL_CH = 0, SPDBA_MODEL_NLS = 1, SPDBA_MODEL_RCD = 2 };
 enum { SPDBA_C64 = 0, SPDBA_C128 = 1 };
 /* spdba_apply(mode) of the paper (S2.1): 0 = Regular full update, 1 = sp-DBA */
 enum { SPDBA_MODE_REGULAR = 0, SPDBA_MODE_ADAPTIVE = 1 };
@@ -92,6 +94,15 @@ typedef struct spdba_options {
     double target_ratio;    /* 0 = control off (default)                                   */
     double control_eta;     /* relative deadband and step factor, default 0.05             */
     int32_t control_every;  /* control interval in steps, default 50                       */
+    /* RCD (S4.1-S4.2): du/dt = D lap u + R(u) with M components, D symmetric circulant
+       (D_ii = rcd_d_diag + 2 rcd_d_cross, -rcd_d_cross to the two periodic neighbour
+       components), R_i = u_i (rcd_r - rcd_a u_i - sum_{j != i} alpha_ij u_j) with
+       alpha_ij = rcd_beta + rcd_alpha for the neighbours and rcd_beta otherwise; per mode
+       u_hat <- V (I + dt k^2 Lambda)^{-1} V^T [u_hat + dt FFT(R)] with D = V Lambda V^T
+       (S4.3).  The activation measure is the component RMS amplitude
+       A(k) = sqrt(mean_m |u_hat_m(k)|^2); one state per block for all components. */
+    int32_t components;     /* M, 1..64, default 8                                          */
+    double rcd_d_diag, rcd_d_cross, rcd_alpha, rcd_beta, rcd_r, rcd_a;  /* 0.5 0.05 1 0.3 1 1 */
 } spdba_options;
 
 /* Per-run statistics, refreshed at each reassessment. */
@@ -134,6 +145,8 @@ void spdba_options_default(spdba_options* opt);
  *               (block b along an axis covers FFT indices [b*B, b*B + B - 1])
  *   threshold   see tau_rule; reassess  steps between block-state reassessments (>= 1)
  * The field starts at zero; set it with spdba_set_field.  *out receives the plan.
+ * RCD plans (model SPDBA_MODEL_RCD) are 2-D or 3-D with opt->components fields;
+ * their fields move in and out as components * prod(dims) reals, component-major.
  */
 spdba_status spdba_plan_create(spdba_plan** out, int32_t ndim, const int64_t* dims,
                                const int32_t* block, double threshold, int32_t reassess,

@@ -16,6 +16,7 @@
 
 #include "blocks.h"
 #include "nls.h"
+#include "rcd.h"
 
 namespace spdba {
 
@@ -139,6 +140,11 @@ template <typename T> struct Group {
     C* tw2 = nullptr;               // exp(-2 pi i a b / n) at a * 512 + b (long NLS signals)
     int B = 1, nblk = 1;
     NLSLaunch nl;                   // NLS launch shapes (fixed at creation)
+    // RCD: ncomp components per field, component-major in c_hat, work and real
+    long long ncomp = 1;
+    T* rcd_V = nullptr;             // eigenvectors of D, row-major V[i * M + j]
+    T* rcd_lam = nullptr;           // eigenvalues of D
+    FftEngine<T> rcd_fft;           // transforms of the ncomp fields (one batch)
     // predictor (3-D CH runs): last exact activity, prediction in force, scratch
     double* snap_maxsq = nullptr;
     double* snap_tau = nullptr;
@@ -163,6 +169,7 @@ template <typename T> struct Group {
         for (void* p : allocs) dev_free(p);
         allocs.clear();
         fft1.release();
+        rcd_fft.release();
     }
 };
 
@@ -171,9 +178,10 @@ template <typename T> struct Group {
 using namespace spdba;
 
 enum ProfKind { K_FFT_PASS = 0, K_FUSED_NL, K_UPDATE_DENSE, K_UPDATE_LIST, K_ASSESS, K_NLS_STEP, K_NLS_ROW, K_NLS_COL,
-                K_FFT_UPDATE, K_FFT_ZFWD, K_COUNT };
+                K_FFT_UPDATE, K_FFT_ZFWD, K_RCD_FFT, K_RCD_REACTION, K_COUNT };
 static const char* kProfName[K_COUNT] = {"fft_pass", "fft_fused_nl", "update_dense", "update_list", "assess",
-                                         "nls_step", "nls_row", "nls_col", "fft_update", "fft_z_forward"};
+                                         "nls_step", "nls_row", "nls_col", "fft_update", "fft_z_forward",
+                                         "rcd_fft", "rcd_reaction"};
 
 struct ProfRec {
     int kind;
@@ -186,8 +194,13 @@ struct RunRef {
     long long sub;
 };
 
+struct RcdParams {
+    double r, a, alpha, beta;
+};
+
 struct spdba_plan {
     spdba_options opt;
+    RcdParams rcd{1.0, 1.0, 1.0, 0.3};
     bool prof = false;
     int prof_every = 1;     // record the kernels of one step in `prof_every`
     bool prof_on = false;   // recording the current step
@@ -290,10 +303,10 @@ template <typename T> static spdba_status group_buffers(spdba_plan* p, Group<T>&
     cudaStream_t st = p->st;
     spdba_status s;
     const long long nb = r.g.blocks();
-    const long long tot = r.batch * r.n;
+    const long long tot = r.batch * r.n * r.ncomp;
     if ((s = r.alloc(&r.c_hat, sizeof(cx_t<T>) * tot)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.work, sizeof(cx_t<T>) * tot)) != SPDBA_OK) return s;
-    if ((s = r.alloc(&r.real, sizeof(T) * r.n)) != SPDBA_OK) return s;
+    if ((s = r.alloc(&r.real, sizeof(T) * r.n * r.ncomp)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.maxsq, sizeof(double) * nb)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.sumsq, sizeof(double) * nb)) != SPDBA_OK) return s;
     if ((s = r.alloc(&r.gmax, sizeof(double) * 2 * r.batch)) != SPDBA_OK) return s;
@@ -513,6 +526,76 @@ static spdba_status group_init_nls(spdba_plan* p, Group<T>& r, long long n, int 
     if ((s = upload(r, &r.H, H, st)) != SPDBA_OK) return s;
     if ((s = upload(r, &r.ntaper, taper_table<T>(r.B), st)) != SPDBA_OK) return s;
     return SPDBA_OK;
+}
+
+// Eigendecomposition D = V diag(lam) V^T of the symmetric circulant
+// cross-diffusion matrix (S4.1, S4.3), in FP64 from its closed form: the real
+// Fourier vectors diagonalise every symmetric circulant matrix, with
+// eigenvalue d + 2c - 2c cos(2 pi k / M) for frequency k (first row d + 2c,
+// -c, 0, ..., -c); for M = 2 the single off-diagonal entry -c gives d + c
+// (vector (1, 1)) and d + 3c (vector (1, -1)).  V[i * M + j] is component i
+// of eigenvector j.
+static void rcd_eigen_host(int M, double d, double c, std::vector<double>& V, std::vector<double>& lam) {
+    V.assign((size_t)M * M, 0.0);
+    lam.assign((size_t)M, 0.0);
+    if (M == 1) {
+        V[0] = 1.0;
+        lam[0] = d + 2.0 * c;
+        return;
+    }
+    if (M == 2) {
+        const double h = sqrt(0.5);
+        V[0] = h; V[1] = h; V[2] = h; V[3] = -h;
+        lam[0] = d + c;
+        lam[1] = d + 3.0 * c;
+        return;
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    const double s0 = 1.0 / sqrt((double)M), s1 = sqrt(2.0 / (double)M);
+    int col = 0;
+    for (int i = 0; i < M; ++i) V[(size_t)i * M + col] = s0;
+    lam[col++] = d;
+    for (int k = 1; 2 * k < M; ++k) {
+        const double l = d + 2.0 * c - 2.0 * c * cos(two_pi * (double)k / (double)M);
+        for (int i = 0; i < M; ++i) {
+            const double ang = two_pi * (double)((long long)k * i % M) / (double)M;   // reduced before the multiply
+            V[(size_t)i * M + col] = s1 * cos(ang);
+            V[(size_t)i * M + col + 1] = s1 * sin(ang);
+        }
+        lam[col] = l;
+        lam[col + 1] = l;
+        col += 2;
+    }
+    if (M % 2 == 0) {
+        for (int i = 0; i < M; ++i) V[(size_t)i * M + col] = (i % 2 ? -s0 : s0);
+        lam[col] = d + 4.0 * c;
+    }
+}
+
+template <typename T>
+static spdba_status group_init_rcd(spdba_plan* p, Group<T>& r, int ndim, const int64_t* dims, const int32_t* block) {
+    cudaStream_t st = p->st;
+    spdba_status s = make_geom(&r.g, ndim, dims, block);
+    if (s != SPDBA_OK) return s;
+    const int M = p->opt.components;
+    r.ndim = ndim;
+    r.batch = 1;
+    r.ncomp = M;
+    r.n = 1;
+    for (int a = 0; a < ndim; ++a) { r.dims[a] = dims[a]; r.n *= dims[a]; }
+    if ((s = group_buffers<T>(p, r)) != SPDBA_OK) return s;
+    const int a0 = 3 - ndim;
+    for (int ax = 0; ax < 3; ++ax) {
+        std::vector<T> k2 = ax < a0 ? std::vector<T>((size_t)r.g.n[ax], (T)0) : k2_table<T>(r.g.n[ax], p->opt.dx);
+        if ((s = upload(r, &r.k2ax[ax], k2, st)) != SPDBA_OK) return s;
+        if ((s = upload(r, &r.taper[ax], taper_table<T>(r.g.b[ax]), st)) != SPDBA_OK) return s;
+    }
+    if ((s = r.rcd_fft.init(ndim, dims, M, twc<T>(p), st)) != SPDBA_OK) return s;
+    std::vector<double> V, lam;
+    rcd_eigen_host(M, p->opt.rcd_d_diag, p->opt.rcd_d_cross, V, lam);
+    if ((s = upload(r, &r.rcd_V, std::vector<T>(V.begin(), V.end()), st)) != SPDBA_OK) return s;
+    if ((s = upload(r, &r.rcd_lam, std::vector<T>(lam.begin(), lam.end()), st)) != SPDBA_OK) return s;
+    return rcd_prepare<T>(M);
 }
 
 // State preparation (Methods): activity, threshold, states, list.
@@ -833,10 +916,73 @@ template <typename T> static spdba_status group_nls_steps(spdba_plan* p, Group<T
     return SPDBA_OK;
 }
 
+// One RCD step (S4.2): state preparation at reassessments (component RMS
+// amplitude), u = IFFT(u_hat) of the M components, R(u) in real space, its
+// FFT, then the per-mode coupled update on the listed blocks (or every block).
+template <typename T> static spdba_status group_rcd_step(spdba_plan* p, Group<T>& r) {
+    cudaStream_t st = p->st;
+    spdba_status s;
+    prof_select(p, r.step);
+    const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
+    const bool reassess = adaptive && (!r.assessed || r.step % p->reassess == 0);
+    const int M = (int)r.ncomp;
+    const double field_b = sizeof(cx_t<T>) * (double)(M * r.n);
+    if (control_step(p, r.step) && (s = group_control<T>(p, r)) != SPDBA_OK) return s;
+    if (reassess) {
+        ProfScope ps(p, K_ASSESS, field_b);
+        if ((s = launch_rcd_activity<T>(r.g, r.c_hat, M, r.maxsq, r.gmax, st)) != SPDBA_OK) return s;
+        if ((s = launch_classify_from_scan(r.g, r.maxsq, 1, r.gmax, p->threshold, p->opt.tau_rule, 1, p->opt.force_dc,
+                                           p->opt.transitions, r.tau, r.active, r.states, r.chi, r.list, r.count,
+                                           r.scratch, r.stats, st)) != SPDBA_OK)
+            return s;
+        p->launches += 4;
+        r.assessed = true;
+    }
+    const int dense = !adaptive || all_active_step(p, r.step);
+    {
+        ProfScope pr(p, K_RCD_FFT, 2.0 * r.ndim * field_b);
+        if ((s = r.rcd_fft.exec(r.c_hat, r.work, SPDBA_INVERSE, st)) != SPDBA_OK) return s;
+    }
+    {
+        ProfScope pr(p, K_RCD_REACTION, 2.0 * field_b);
+        const RcdParams& q = p->rcd;
+        if ((s = launch_rcd_reaction<T>(r.work, r.n, M, (T)q.r, (T)q.a, (T)q.alpha, (T)q.beta, st)) != SPDBA_OK)
+            return s;
+    }
+    {
+        ProfScope pr(p, K_RCD_FFT, 2.0 * r.ndim * field_b);
+        if ((s = r.rcd_fft.exec(r.work, r.work, SPDBA_FORWARD, st)) != SPDBA_OK) return s;
+    }
+    p->launches += 2 * r.ndim + 1;
+    RcdArgs<T> a;
+    a.u_hat = r.c_hat;
+    a.g_hat = r.work;
+    a.V = r.rcd_V;
+    a.lam = r.rcd_lam;
+    for (int ax = 0; ax < 3; ++ax) { a.k2ax[ax] = r.k2ax[ax]; a.taper[ax] = r.taper[ax]; }
+    a.states = r.states;
+    a.chi = r.chi;
+    a.list = r.list;
+    a.count = r.count;
+    a.dt = (T)p->opt.dt;
+    a.M = M;
+    a.n = r.n;
+    a.stats = r.stats;
+    {
+        // list-driven traffic is known only on the device; it is added at profile end
+        ProfScope pr(p, dense ? K_UPDATE_DENSE : K_UPDATE_LIST, dense ? 3.0 * field_b : 0.0);
+        if ((s = launch_rcd_update<T>(r.g, a, dense, st)) != SPDBA_OK) return s;
+        p->launches += 1;
+        if (!dense) p->list_updates += 1;
+    }
+    r.step += 1;
+    return SPDBA_OK;
+}
+
 template <typename T> static spdba_status group_steps(spdba_plan* p, Group<T>& g, int64_t n) {
     if (p->opt.model == SPDBA_MODEL_NLS) return group_nls_steps<T>(p, g, n);
     for (int64_t i = 0; i < n; ++i) {
-        spdba_status s = group_ch_step<T>(p, g);
+        spdba_status s = p->opt.model == SPDBA_MODEL_RCD ? group_rcd_step<T>(p, g) : group_ch_step<T>(p, g);
         if (s != SPDBA_OK) return s;
     }
     return SPDBA_OK;
@@ -891,7 +1037,7 @@ template <typename T> static spdba_status direct_steps(spdba_plan* p, int64_t n)
     }
     for (int64_t i = 0; i < n; ++i) {
         for (auto& g : gs) {
-            spdba_status s = group_ch_step<T>(p, *g);
+            spdba_status s = p->opt.model == SPDBA_MODEL_RCD ? group_rcd_step<T>(p, *g) : group_ch_step<T>(p, *g);
             if (s != SPDBA_OK) return s;
         }
     }
@@ -969,7 +1115,12 @@ static spdba_status run_set_field(spdba_plan* p, Group<T>& r, long long sub, con
     cx_t<T>* slot = r.c_hat + sub * r.n;
     cx_t<T>* wslot = r.work + sub * r.n;
     const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (p->opt.model == SPDBA_MODEL_CH) {
+    if (p->opt.model == SPDBA_MODEL_RCD) {
+        const long long tot = r.n * r.ncomp;
+        SPDBA_CUDA(cudaMemcpyAsync(r.real, src, sizeof(T) * tot, kind, st));
+        real_to_complex_kernel<T><<<grid_for(tot, 256), 256, 0, st>>>(r.real, r.work, tot);
+        if ((s = r.rcd_fft.exec(r.work, r.c_hat, SPDBA_FORWARD, st)) != SPDBA_OK) return s;
+    } else if (p->opt.model == SPDBA_MODEL_CH) {
         SPDBA_CUDA(cudaMemcpyAsync(r.real, src, sizeof(T) * r.n, kind, st));
         real_to_complex_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(r.real, wslot, r.n);
         if ((s = r.fft1.exec(wslot, slot, SPDBA_FORWARD, st)) != SPDBA_OK) return s;
@@ -1004,7 +1155,12 @@ static spdba_status run_get_field(spdba_plan* p, Group<T>& r, long long sub, voi
     cx_t<T>* slot = r.c_hat + sub * r.n;
     cx_t<T>* wslot = r.work + sub * r.n;
     const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (p->opt.model == SPDBA_MODEL_CH) {
+    if (p->opt.model == SPDBA_MODEL_RCD) {
+        const long long tot = r.n * r.ncomp;
+        if ((s = r.rcd_fft.exec(r.c_hat, r.work, SPDBA_INVERSE, st)) != SPDBA_OK) return s;
+        complex_real_part_kernel<T><<<grid_for(tot, 256), 256, 0, st>>>(r.work, r.real, tot);
+        SPDBA_CUDA(cudaMemcpyAsync(dst, r.real, sizeof(T) * tot, kind, st));
+    } else if (p->opt.model == SPDBA_MODEL_CH) {
         if ((s = r.fft1.exec(slot, wslot, SPDBA_INVERSE, st)) != SPDBA_OK) return s;
         complex_real_part_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(wslot, r.real, r.n);
         SPDBA_CUDA(cudaMemcpyAsync(dst, r.real, sizeof(T) * r.n, kind, st));
@@ -1029,7 +1185,7 @@ static spdba_status run_get_field(spdba_plan* p, Group<T>& r, long long sub, voi
 template <typename T>
 static spdba_status copy_spectrum(spdba_plan* p, Group<T>& r, long long sub, void* buf, int on_dev, bool get) {
     cudaStream_t st = p->st;
-    size_t bytes = sizeof(cx_t<T>) * (size_t)r.n;
+    size_t bytes = sizeof(cx_t<T>) * (size_t)(r.n * r.ncomp);
     cx_t<T>* slot = r.c_hat + sub * r.n;
     cx_t<T>* wslot = r.work + sub * r.n;
     spdba_status s;
@@ -1089,6 +1245,13 @@ extern "C" void spdba_options_default(spdba_options* o) {
     o->target_ratio = 0.0;
     o->control_eta = 0.05;
     o->control_every = 50;
+    o->components = 8;
+    o->rcd_d_diag = 0.5;
+    o->rcd_d_cross = 0.05;
+    o->rcd_alpha = 1.0;
+    o->rcd_beta = 0.3;
+    o->rcd_r = 1.0;
+    o->rcd_a = 1.0;
 }
 
 static spdba_status check_opts(const spdba_options* o, int ndim) {
@@ -1096,7 +1259,15 @@ static spdba_status check_opts(const spdba_options* o, int ndim) {
         return fail(SPDBA_ERR_ARG, "target_ratio must lie in [0, 1]");
     if (o->target_ratio > 0 && (!(o->control_eta > 0.0 && o->control_eta < 1.0) || o->control_every < 1))
         return fail(SPDBA_ERR_ARG, "threshold control needs 0 < control_eta < 1 and control_every >= 1");
-    if (o->model != SPDBA_MODEL_CH && o->model != SPDBA_MODEL_NLS) return fail(SPDBA_ERR_ARG, "bad model %d", o->model);
+    if (o->model != SPDBA_MODEL_CH && o->model != SPDBA_MODEL_NLS && o->model != SPDBA_MODEL_RCD)
+        return fail(SPDBA_ERR_ARG, "bad model %d", o->model);
+    if (o->model == SPDBA_MODEL_RCD) {
+        if (ndim < 2 || ndim > 3) return fail(SPDBA_ERR_UNSUPPORTED, "RCD plans are 2-D or 3-D");
+        if (o->components < 1 || o->components > kRcdMaxComponents)
+            return fail(SPDBA_ERR_UNSUPPORTED, "RCD with %d components (1..%d)", o->components, kRcdMaxComponents);
+        if (o->measure != SPDBA_MEASURE_MAXAMP)
+            return fail(SPDBA_ERR_ARG, "RCD activation uses the component RMS amplitude (SPDBA_MEASURE_MAXAMP)");
+    }
     if (o->precision != SPDBA_C64 && o->precision != SPDBA_C128)
         return fail(SPDBA_ERR_ARG, "bad precision %d", o->precision);
     if (o->mode != SPDBA_MODE_REGULAR && o->mode != SPDBA_MODE_ADAPTIVE) return fail(SPDBA_ERR_ARG, "bad mode %d", o->mode);
@@ -1136,7 +1307,10 @@ static spdba_status build_groups(spdba_plan* p, int nruns, int ndim, const int64
         long long batch = (long long)members[gi].size();
         gs.emplace_back(new Group<T>());
         spdba_status s;
-        if (p->opt.model == SPDBA_MODEL_NLS) {
+        if (p->opt.model == SPDBA_MODEL_RCD) {
+            if (nruns != 1) return fail(SPDBA_ERR_UNSUPPORTED, "an RCD plan holds one field of M components");
+            s = group_init_rcd<T>(p, *gs.back(), ndim, d, block);
+        } else if (p->opt.model == SPDBA_MODEL_NLS) {
             if (block[0] > 0 && d[0] % block[0] != 0)
                 return fail(SPDBA_ERR_UNSUPPORTED, "block edge %d does not divide %lld", block[0], (long long)d[0]);
             int nblk = block[0] <= 0 ? -block[0] : (int)(d[0] / block[0]);
@@ -1167,6 +1341,7 @@ extern "C" spdba_status spdba_batch_create(spdba_plan** out, int32_t nruns, int3
         }
     spdba_plan* p = new spdba_plan();
     p->opt = o;
+    p->rcd = RcdParams{o.rcd_r, o.rcd_a, o.rcd_alpha, o.rcd_beta};
     p->threshold = threshold;
     p->reassess = reassess;
     p->precision = o.precision;
@@ -1245,7 +1420,7 @@ struct GroupSnap {
 
 template <typename T> static spdba_status snap_take(spdba_plan* p, Group<T>& r, GroupSnap& sn) {
     const long long nb = r.g.blocks();
-    sn.bufs = {{r.c_hat, sizeof(cx_t<T>) * (size_t)(r.batch * r.n)},
+    sn.bufs = {{r.c_hat, sizeof(cx_t<T>) * (size_t)(r.batch * r.n * r.ncomp)},
                {r.stats, sizeof(DevStats) * (size_t)r.batch},
                {r.maxsq, sizeof(double) * (size_t)nb},
                {r.sumsq, sizeof(double) * (size_t)nb},

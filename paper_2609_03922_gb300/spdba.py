@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libspdba.so")
 
 SPDBA_OK, SPDBA_ERR_ARG, SPDBA_ERR_UNSUPPORTED, SPDBA_ERR_CUDA, SPDBA_ERR_OOM, SPDBA_ERR_TIMEOUT, SPDBA_ERR_STATE = range(7)
-SPDBA_MODEL_CH, SPDBA_MODEL_NLS = 0, 1
+SPDBA_MODEL_CH, SPDBA_MODEL_NLS, SPDBA_MODEL_RCD = 0, 1, 2
 SPDBA_C64, SPDBA_C128 = 0, 1
 SPDBA_MODE_REGULAR, SPDBA_MODE_ADAPTIVE = 0, 1
 SPDBA_MEASURE_MAXAMP, SPDBA_MEASURE_ENERGY = 0, 1
@@ -32,7 +32,9 @@ class spdba_options(ctypes.Structure):
                 ("beta2", ctypes.c_double), ("gamma", ctypes.c_double), ("h", ctypes.c_double),
                 ("dt_sample", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("target_ratio", ctypes.c_double), ("control_eta", ctypes.c_double),
-                ("control_every", ctypes.c_int32)]
+                ("control_every", ctypes.c_int32), ("components", ctypes.c_int32),
+                ("rcd_d_diag", ctypes.c_double), ("rcd_d_cross", ctypes.c_double), ("rcd_alpha", ctypes.c_double),
+                ("rcd_beta", ctypes.c_double), ("rcd_r", ctypes.c_double), ("rcd_a", ctypes.c_double)]
 
 
 class spdba_stats(ctypes.Structure):
@@ -224,18 +226,24 @@ class Plan:
         check(lib().spdba_sync(self._p))
 
     def field_dtype(self):
-        return self.real_dtype if self.opts.model == SPDBA_MODEL_CH else self.complex_dtype
+        return self.complex_dtype if self.opts.model == SPDBA_MODEL_NLS else self.real_dtype
+
+    def field_shape(self, run=0):
+        """Shape of a run's field: (components, *dims) for RCD plans, dims otherwise."""
+        if self.opts.model == SPDBA_MODEL_RCD:
+            return (int(self.opts.components),) + tuple(self.run_dims[run])
+        return tuple(self.run_dims[run])
 
     def get_field(self, out=None, run=0):
         if out is None:
-            out = np.empty(self.run_dims[run], dtype=self.field_dtype())
+            out = np.empty(self.field_shape(run), dtype=self.field_dtype())
         p, dev = _ptr(out)
         check(lib().spdba_get_field(self._p, run, p, dev))
         return out
 
     def get_spectrum(self, out=None, run=0):
         if out is None:
-            out = np.empty(self.run_dims[run], dtype=self.complex_dtype)
+            out = np.empty(self.field_shape(run), dtype=self.complex_dtype)
         p, dev = _ptr(out)
         check(lib().spdba_get_spectrum(self._p, run, p, dev))
         return out
