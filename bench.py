@@ -19,11 +19,11 @@ DRAM), a cuFFT comparator, the end-to-end figure through host buffers, and
 the FP64 oracle (CPU baseline and parity) run in a process of its own.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                      [--workload ch3d256|ch2d128|nls512|ensemble64|ch3d384pred]
+                      [--workload ch3d256|ch2d128|nls512|ensemble64|ch3d384pred|rcd128]
 The default workload is the headline line; the others print one line each for
 the remaining configurations (2-D 128^2 FP64; 512 NLS signals; the uneven
 64-run ensemble, grouped vs one plan per run; 3-D 384^3 with the learned
-predictor).
+predictor) and the M-component reaction-cross-diffusion workload (128^3).
 Under torchrun (N > 1) every rank runs an independent replica (the 256^3 run
 does not shard); value = N*K / max-over-ranks time.
 """
@@ -846,6 +846,15 @@ NLS_ORACLE_SUBSET = 7        # the first signal of each length 2^12..2^18
 ENSEMBLE_ORACLE_RUNS = 8     # the first runs of side <= 256
 PRED_SMALL = (64, 64, 64)    # the predictor configuration at a size the oracle finishes
 NLS_CONTROL_THRESHOLD0 = 1e-4  # initial threshold of the DBP runs under control (S5.3)
+RCD_DIMS = (128, 128, 128)     # S4.2: 128^3 with B = 4
+RCD_BLOCK = (4, 4, 4)
+RCD_COMPONENTS = (8, 24, 48)   # S4.2 varies M from 2 to 64; Fig. 3d quotes 24, 48, 64
+RCD_TARGETS = (0.03, 0.1, 0.2)  # S4.2: target ratios 3-20 %, adjustment factor 0.1, interval 50
+RCD_THRESHOLD0 = 1e-4
+RCD_WARM = 1000                # untimed steps before the timed window (control settles)
+RCD_STEPS = 100                # timed steps per repetition
+RCD_SMALL = (32, 32, 32)       # oracle parity size (same parameters)
+RCD_SMALL_STEPS = 100
 
 
 def _nls_oracle_pick():
@@ -888,6 +897,13 @@ def workload_oracle_job(workload, threads):
             ch, _ = O.run_ch(c0, O.CHConfig((sd, sd), (16, 16), threshold=1e-6, reassess=10), 1000)
             out[r] = O.ch_real_field(ch)
             units += 1000
+    elif workload == "rcd128":
+        for M in RCD_COMPONENTS:
+            u0 = W.rcd_initial_condition(RCD_SMALL, M, W.rcd_lv_homogeneous(M), 0.1, seed=W.BASE_SEED + M)
+            cfg = O.RCDConfig(RCD_SMALL, RCD_BLOCK, M, threshold=RCD_THRESHOLD0, reassess=10)
+            uh, _ = O.run_rcd(u0.astype(np.float32).astype(np.float64), cfg, RCD_SMALL_STEPS)
+            out["M%d" % M] = O.rcd_real_field(uh)
+            units += RCD_SMALL_STEPS
     elif workload == "ch3d384pred":
         c0 = W.ch_initial_condition(PRED_SMALL, mean=0.1, seed=W.BASE_SEED).astype(np.float32).astype(np.float64)
         ch, _ = O.run_ch(c0, O.CHConfig(PRED_SMALL, (8, 8, 8), threshold=1e-6, reassess=10), 5000)
@@ -896,7 +912,7 @@ def workload_oracle_job(workload, threads):
     return {"fields": out, "seconds": time.perf_counter() - t0, "steps": units, "cores": O.num_threads()}
 
 
-ORACLE_JOBS = ("ch2d128", "nls512", "ensemble64", "ch3d384pred")
+ORACLE_JOBS = ("ch2d128", "nls512", "ensemble64", "ch3d384pred", "rcd128")
 
 
 def start_workload_oracle(workload):
@@ -920,6 +936,96 @@ def _oracle_leg(fut, gpu_fields, sample):
             "rel_l2_vs_oracle_max": max(rel.values()) if rel else None}
 
 
+def run_rcd128(args, oracle_fut=None):
+    """Reaction-cross-diffusion 128^3 (S4.2: dx = 0.5, dt = 0.01, D_diag = 0.5, D_cross =
+    0.05, alpha = 1, beta = 0.3, B = 4), complex64, M components: Regular against sp-DBA,
+    both with the diagonalized update (S4.3), sp-DBA under dynamic threshold control at
+    the targets of S4.2.  Each plan runs RCD_WARM steps untimed from the seeded start,
+    then RCD_STEPS steps are timed from that state (repeated to 1 s, median); the
+    update stage is the coupled update plus the state preparation (the paper's
+    update-stage metric), from a profiled repetition of the same window."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    import workloads as W
+    torch.cuda.set_stream(torch.cuda.Stream())
+    st = torch.cuda.current_stream()
+    out = {}
+    small = {}
+    for M in RCD_COMPONENTS:
+        u0 = W.rcd_initial_condition(RCD_DIMS, M, W.rcd_lv_homogeneous(M), 0.1, seed=W.BASE_SEED + M)
+        u0 = torch.from_numpy(u0.astype(np.float32)).cuda()
+        res = {}
+        fields = {}
+        for name, mode, kw in ([("regular", 0, {})] +
+                               [("control_%g" % t, 1, {"target_ratio": t, "control_every": 50, "control_eta": 0.1})
+                                for t in RCD_TARGETS]):
+            pl = spdba.Plan(RCD_DIMS, RCD_BLOCK, threshold=RCD_THRESHOLD0, reassess=10, precision=spdba.SPDBA_C64,
+                            model=spdba.SPDBA_MODEL_RCD, components=M, dx=0.5, mode=mode, **kw)
+            pl.set_field(u0)
+            pl.step(RCD_WARM)
+            snap = torch.empty((M,) + RCD_DIMS, dtype=torch.complex64, device="cuda")
+            pl.get_spectrum(snap)
+            s0 = pl.get_stats()
+            pl.step(RCD_STEPS)
+            s1 = pl.get_stats()
+            ratio = (s1["active_ratio_sum"] - s0["active_ratio_sum"]) / RCD_STEPS
+            ms = []
+            while True:
+                pl.set_spectrum(snap)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                pl.step(RCD_STEPS)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                if sum(ms) >= 1e3 * MIN_TIMED_S and len(ms) >= 3:
+                    break
+            f = torch.empty((M,) + RCD_DIMS, dtype=torch.float32, device="cuda")
+            pl.get_field(f)
+            fields[name] = f
+            pl.set_spectrum(snap)
+            pl.profile_begin(1)
+            pl.step(RCD_STEPS)
+            prof = pl.profile_end()
+            kinds = _kind_summary(prof)
+            upd = sum(prof[0].get(k, {"total_ms": 0.0})["total_ms"] for k in ("update_list", "update_dense", "assess"))
+            res[name] = {"steps_per_s": RCD_STEPS / (_median(ms) / 1e3), "nonfrozen_ratio": ratio,
+                         "update_stage_ms_per_step": upd / RCD_STEPS, "threshold": s1["threshold"],
+                         "kernels": kinds}
+            pl.close()
+            del snap
+        reg = fields["regular"].double()
+        for name in res:
+            if name != "regular":
+                res[name]["rel_l2_vs_regular_window"] = float(((fields[name].double() - reg).norm() / reg.norm()).item())
+                res[name]["over_regular"] = res[name]["steps_per_s"] / res["regular"]["steps_per_s"]
+                res[name]["update_stage_speedup"] = (res["regular"]["update_stage_ms_per_step"] /
+                                                     max(1e-9, res[name]["update_stage_ms_per_step"]))
+        out["M%d" % M] = res
+        del fields, reg
+        # the oracle parity run (small size, same parameters, free-running adaptive at the fixed threshold)
+        with spdba.Plan(RCD_SMALL, RCD_BLOCK, threshold=RCD_THRESHOLD0, reassess=10, precision=spdba.SPDBA_C64,
+                        model=spdba.SPDBA_MODEL_RCD, components=M, dx=0.5) as sp:
+            us = W.rcd_initial_condition(RCD_SMALL, M, W.rcd_lv_homogeneous(M), 0.1, seed=W.BASE_SEED + M)
+            sp.set_field(us.astype(np.float32))
+            sp.step(RCD_SMALL_STEPS)
+            small["M%d" % M] = sp.get_field()
+        torch.cuda.empty_cache()
+    head = out["M%d" % RCD_COMPONENTS[-1]]["control_0.03"]
+    extra = {"dtype": "c64", "components": list(RCD_COMPONENTS), "results": out,
+             "note": "window of %d steps after %d untimed steps; control: factor 0.1, interval 50; the update is "
+                     "the diagonalized form in both modes (the paper's direct dense solve exists only in the oracle)"
+                     % (RCD_STEPS, RCD_WARM)}
+    extra.update(_oracle_leg(oracle_fut, small, "32^3 (4^3 blocks), %d adaptive steps at the fixed threshold %g, "
+                                                "M = %s (FP64 oracle, own scans)" % (RCD_SMALL_STEPS, RCD_THRESHOLD0,
+                                                                                    list(RCD_COMPONENTS))))
+    return _line("RCD spectral steps/s, sp-DBA (3 %% target) vs Regular, M = %d, 128^3" % RCD_COMPONENTS[-1],
+                 head["steps_per_s"], "steps/s", RCD_STEPS, RCD_WARM, 1e3 * RCD_STEPS / head["steps_per_s"],
+                 {"workload": "rcd-128^3-B4-c64-dx0.5", "dims": list(RCD_DIMS)}, extra)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -928,7 +1034,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="ch3d256",
-                    choices=["ch3d256", "ch2d128", "nls512", "ensemble64", "ch3d384pred"])
+                    choices=["ch3d256", "ch2d128", "nls512", "ensemble64", "ch3d384pred", "rcd128"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -941,7 +1047,7 @@ def main():
         B.build()
         torch.cuda.set_device(0)
         fn = {"ch2d128": run_ch2d128, "nls512": run_nls512, "ensemble64": run_ensemble64,
-              "ch3d384pred": run_ch3d384pred}[args.workload]
+              "ch3d384pred": run_ch3d384pred, "rcd128": run_rcd128}[args.workload]
         print(json.dumps(fn(args, oracle_fut)), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))

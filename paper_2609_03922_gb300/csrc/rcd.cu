@@ -62,10 +62,50 @@ spdba_status launch_rcd_reaction(cx_t<T>* work, long long n, int M, T r, T a, T 
 }
 
 // ------------------------------------------------------------------ activity
-// One warp per block.  A(k)^2 = (1/M) sum_m (re*re + im*im), every product and
-// sum rounded separately in FP64, components in order; the block's maximum is
-// exact in FP64.  Non-negative doubles order like their bit patterns, so the
-// global maxima are integer atomicMax on the bits.
+// One warp per block.  A(k)^2 = (1/M) sum_m (re^2 + im^2).  GB300's FP64 rate
+// is a small fraction of its FP32 rate, so the sum runs in double-float: each
+// square is split exactly into p + e with an FMA (Dekker's two-product), the
+// large parts are added with Knuth's two-sum into (hi, lo), and hi + lo is
+// converted to FP64 once per mode.  The result carries about 2^-44 relative
+// error (squares of |x| < 2^-63 fall below FP32's range and count as zero:
+// such values lie far below any threshold in use), so the block maximum and
+// the global maxima are FP64-accurate.  Non-negative doubles order like their
+// bit patterns: the global maxima are integer atomicMax on the bits.
+__device__ __forceinline__ void rcd_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void rcd_acc_sq(float x, float& hi, float& lo) {
+    const float p = __fmul_rn(x, x);
+    const float pe = __fmaf_rn(x, x, -p);   // x^2 = p + pe exactly
+    float s, e;
+    rcd_two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+template <typename C> __device__ __forceinline__ double rcd_mode_sq(const C* __restrict__ q, long long n, long long e,
+                                                                    int M);
+template <> __device__ __forceinline__ double rcd_mode_sq<float2>(const float2* __restrict__ q, long long n,
+                                                                   long long e, int M) {
+    float hi = 0.f, lo = 0.f;
+    for (int m = 0; m < M; ++m) {
+        const float2 v = q[(long long)m * n + e];
+        rcd_acc_sq(v.x, hi, lo);
+        rcd_acc_sq(v.y, hi, lo);
+    }
+    return __ddiv_rn(__dadd_rn((double)hi, (double)lo), (double)M);
+}
+template <> __device__ __forceinline__ double rcd_mode_sq<double2>(const double2* __restrict__ q, long long n,
+                                                                    long long e, int M) {
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double2 v = q[(long long)m * n + e];
+        s = __dadd_rn(s, __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)));
+    }
+    return __ddiv_rn(s, (double)M);
+}
+
 template <typename T>
 __global__ void rcd_activity_kernel(Geom g, const cx_t<T>* __restrict__ q, int M, long long n, double* maxsq,
                                     double* gmax) {
@@ -83,13 +123,7 @@ __global__ void rcd_activity_kernel(Geom g, const cx_t<T>* __restrict__ q, int M
             const long long rr = o / B2;
             const int d1 = (int)(rr % B1), d0 = (int)(rr / B1);
             const long long e = ((b0 * B0 + d0) * g.n[1] + (b1 * B1 + d1)) * g.n[2] + (b2 * B2 + d2);
-            double s = 0.0;
-            for (int m = 0; m < M; ++m) {
-                const cx_t<T> v = q[(long long)m * n + e];
-                const double re = (double)v.x, im = (double)v.y;
-                s = __dadd_rn(s, __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)));
-            }
-            const double a2 = __ddiv_rn(s, (double)M);
+            const double a2 = rcd_mode_sq(q, n, e, M);
             bmax = fmax(bmax, a2);
             gall = fmax(gall, a2);
             if (e != 0) gnz = fmax(gnz, a2);

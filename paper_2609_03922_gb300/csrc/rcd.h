@@ -31,7 +31,9 @@ template <typename T>
 spdba_status launch_rcd_reaction(cx_t<T>* work, long long n, int M, T r, T a, T alpha, T beta, cudaStream_t st);
 
 // Per block: maxsq[b] = max_{k in B} A(k)^2 with A(k)^2 = (1/M) sum_m |u_m(k)|^2
-// (FP64); gmax[0] = max over all k, gmax[1] = max over k != 0 (max-reduced: zero before).
+// (FP64-accurate: a double-float sum of exact squares for complex64, FP64 for
+// complex128); gmax[0] = max over all k, gmax[1] = max over k != 0 (max-reduced:
+// zero before).
 template <typename T>
 spdba_status launch_rcd_activity(const Geom& g, const cx_t<T>* u_hat, int M, double* maxsq, double* gmax,
                                  cudaStream_t st);
