@@ -103,6 +103,9 @@ typedef struct spdba_options {
        A(k) = sqrt(mean_m |u_hat_m(k)|^2); one state per block for all components. */
     int32_t components;     /* M, 1..64, default 8                                          */
     double rcd_d_diag, rcd_d_cross, rcd_alpha, rcd_beta, rcd_r, rcd_a;  /* 0.5 0.05 1 0.3 1 1 */
+    int32_t tma_update;     /* 1: the staged CH update of 3-D complex64 plans with 8^3 blocks
+                               moves whole blocks as TMA boxes (same values bit for bit);
+                               0 (default): per-warp loads.  spdba_plan_autotune may change it. */
 } spdba_options;
 
 /* Per-run statistics, refreshed at each reassessment. */
@@ -214,7 +217,8 @@ typedef struct spdba_kernel_time {
  * Autotuner (no counterpart in the paper).  Times `steps` steps of the plan
  * for every candidate launch configuration -- the CH update fused into the
  * last forward FFT pass or staged as its own kernel (when the plan was created
- * with fuse_update = 1), the 3-D transforms on the Hermitian half spectrum or
+ * with fuse_update = 1), the staged update's block loads by warps or by TMA
+ * boxes (3-D complex64 plans with 8^3 blocks), the 3-D transforms on the Hermitian half spectrum or
  * on the full one (when created with half_spectrum = 1 and the shape has half-
  * spectrum kernels), and reassessment segments replayed as a CUDA graph or
  * launched directly (graphs only on a non-legacy stream) -- each from the same
@@ -226,12 +230,14 @@ typedef struct spdba_kernel_time {
  * of the plan's state in device memory for the duration of the call; not with
  * an attached predictor (SPDBA_ERR_STATE).  report may be NULL.  Synchronizes.
  */
-#define SPDBA_TUNE_MAX 8
+#define SPDBA_TUNE_MAX 16
 typedef struct spdba_tune_report {
     int32_t n_candidates;
     int32_t fuse_update[SPDBA_TUNE_MAX];
     int32_t use_graph[SPDBA_TUNE_MAX];
     int32_t half_spectrum[SPDBA_TUNE_MAX];
+    int32_t tma_update[SPDBA_TUNE_MAX];  /* staged list update moved by TMA boxes (3-D complex64,
+                                            8^3 blocks) instead of per-warp loads */
     double ms_per_step[SPDBA_TUNE_MAX];
     int32_t chosen;          /* index of the configuration in force afterwards */
 } spdba_tune_report;

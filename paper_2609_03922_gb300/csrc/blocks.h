@@ -46,6 +46,15 @@ template <typename T> struct CHUpdateArgs {
 };
 template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdateArgs<T>& a, int dense, cudaStream_t st);
 
+// TMA form of the list-driven update (3-D complex64, 8^3 blocks, one run):
+// tensor-map descriptors (128 bytes, 64-byte aligned) of c_hat and g_hat made
+// once at plan creation; launch shape from tma_update_prepare.
+bool tma_update_fits(const Geom& g);
+spdba_status make_box_map(void* map_out, const void* base, const Geom& g);
+spdba_status tma_update_prepare(int* per_sm, int* nsm);
+spdba_status launch_ch_update_tma(const void* map_c, const void* map_g, const Geom& g, const CHUpdateArgs<float>& a,
+                                  long long grid, cudaStream_t st);
+
 // Per-axis |k|^2 table and taper table, computed in FP64 on the host.
 template <typename T> std::vector<T> k2_table(long long n, double dx);
 template <typename T> std::vector<T> taper_table(int B);

@@ -135,6 +135,10 @@ template <typename T> struct PassParams {
     // paired z forward with block states: its live tiles (any order) and their count
     const int* live_tiles = nullptr;
     const int* live_count = nullptr;
+    // plain passes whose tiles are P consecutive columns i of the pencil grid: a
+    // tile is skipped when none of its columns is marked (the outputs of
+    // unmarked columns are never read), or null to transform every tile
+    const uint8_t* col_live = nullptr;
 };
 
 // Address of element (p, j) of the tile starting at pencil q0.
@@ -857,8 +861,16 @@ __device__ __forceinline__ UpdTile upd_tile(const PassParams<T>& a, int q0) {
 // evaluates this independently (no block-wide synchronisation needed).
 template <typename T, int P, int MODE>
 __device__ __forceinline__ bool tile_live(const PassParams<T>& a, long long q0) {
-    if constexpr (!is_update_mode(MODE)) return true;
-    else {
+    if constexpr (MODE == PASS_PLAIN) {
+        if (a.col_live == nullptr) return true;
+        const long long i0 = q0 - (long long)a.fd_I.div((uint32_t)q0) * a.I;
+        bool live = false;
+#pragma unroll
+        for (int p = 0; p < P; ++p) live |= a.col_live[i0 + p] != 0;
+        return live;
+    } else if constexpr (!is_update_mode(MODE)) {
+        return true;
+    } else {
         if (a.fu.dense) return true;
         const UpdTile u = upd_tile<T, P>(a, (int)q0);
         if (u.rows) return true;

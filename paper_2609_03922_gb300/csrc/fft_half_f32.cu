@@ -115,3 +115,37 @@ spdba_status launch_pair_live_list(const Pass<float>& ps, int* list, int* count,
 }
 
 }  // namespace spdba
+
+namespace spdba {
+// x frequencies 0 .. NHP-1 of the half array whose columns some paired z
+// forward tile reads: column kx (kx <= N2/2) serves half pencils (ky, kx) for
+// x frequencies kx and N2 - kx, so it is live when any block of block column
+// kx / B2 or (N2 - kx) / B2 (over all kz, ky) is non-frozen; padding columns
+// are never read.
+__global__ void __launch_bounds__(1024) half_col_live_kernel(const uint8_t* __restrict__ states, int nrows, int nb2,
+                                                             int B2, int N2, int NHP, uint8_t* __restrict__ col_live) {
+    __shared__ uint8_t s_col[64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int bx = warp; bx < nb2; bx += 32) {
+        bool live = false;
+        for (int r = lane; r < nrows && !live; r += 32) live = states[(long long)r * nb2 + bx] != 0;
+        const unsigned any = __ballot_sync(0xffffffffu, live);
+        if (lane == 0) s_col[bx] = any != 0;
+    }
+    __syncthreads();
+    for (int kx = threadIdx.x; kx < NHP; kx += blockDim.x) {
+        uint8_t v = 0;
+        if (kx <= N2 / 2) v = s_col[kx / B2] | (kx > 0 ? s_col[(N2 - kx) / B2] : (uint8_t)0);
+        col_live[kx] = v;
+    }
+}
+
+spdba_status launch_half_col_live(const Geom& g, const uint8_t* states, int N2, int NHP, uint8_t* col_live,
+                                  cudaStream_t st) {
+    if (g.nb[2] > 64) return fail(SPDBA_ERR_UNSUPPORTED, "more than 64 block columns");
+    half_col_live_kernel<<<1, 1024, 0, st>>>(states, (int)(g.nb[0] * g.nb[1]), (int)g.nb[2], g.b[2], N2, NHP,
+                                             col_live);
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
+}
+}  // namespace spdba

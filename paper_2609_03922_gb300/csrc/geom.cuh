@@ -43,6 +43,7 @@ struct DevStats {
     unsigned long long ctl_nf;      // non-frozen blocks summed over the control interval's adaptive steps
     unsigned long long ctl_steps;   // adaptive steps in the control interval
     unsigned long long controls;    // control decisions made
+    unsigned long long timeouts;    // bounded device waits that ran out (SPDBA_ERR_TIMEOUT)
 };
 
 }  // namespace spdba

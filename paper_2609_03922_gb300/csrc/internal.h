@@ -76,6 +76,11 @@ spdba_status make_half_pass(Pass<float>* out, int mode, const HalfGeo& hg, Twidd
 // List the live tiles of a paired z forward pass (one with block states) into
 // list[] (at most its tile count) and their number into *count.
 spdba_status launch_pair_live_list(const Pass<float>& ps, int* list, int* count, cudaStream_t st);
+// Live x-frequency columns of the half array for the paired z forward (one
+// byte per column, NHP of them) from a single 3-D run's block states.
+
+spdba_status launch_half_col_live(const Geom& g, const uint8_t* states, int N2, int NHP, uint8_t* col_live,
+                                  cudaStream_t st);
 // Tiles of a paired z forward pass.
 long long pair_tile_count(const Pass<float>& ps);
 // Pencils per tile of the pass kernels of length L (0 if none).

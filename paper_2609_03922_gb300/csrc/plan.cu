@@ -125,6 +125,7 @@ template <typename T> struct Group {
     long long half_n = 0;           // elements of the half array
     Pass<T> h_inv_z, h_inv_y, h_nl, h_fwd_y, h_mirror, h_upd;
     int* pair_list = nullptr;       // live tiles of the paired z forward (with block states)
+    uint8_t* col_live = nullptr;    // live x-frequency columns of the half array (the y forward skips the rest)
     int* pair_count = nullptr;
     long long pair_list_n = 0;      // capacity of pair_list
     bool fused_update = false;      // the last forward pass carries the update (upd_pass)
@@ -145,6 +146,12 @@ template <typename T> struct Group {
     T* rcd_V = nullptr;             // eigenvectors of D, row-major V[i * M + j]
     T* rcd_lam = nullptr;           // eigenvalues of D
     FftEngine<T> rcd_fft;           // transforms of the ncomp fields (one batch)
+    // TMA form of the list-driven update (3-D complex64, 8^3 blocks): tensor maps of c_hat and work
+    alignas(64) unsigned char tma_map_c[128] = {};
+    alignas(64) unsigned char tma_map_g[128] = {};
+    bool tma_ok = false;            // the TMA kernel exists for this group
+    bool use_tma = false;           // ... and is in use (the autotuner's choice)
+    long long tma_grid = 0;
     // predictor (3-D CH runs): last exact activity, prediction in force, scratch
     double* snap_maxsq = nullptr;
     double* snap_tau = nullptr;
@@ -178,10 +185,10 @@ template <typename T> struct Group {
 using namespace spdba;
 
 enum ProfKind { K_FFT_PASS = 0, K_FUSED_NL, K_UPDATE_DENSE, K_UPDATE_LIST, K_ASSESS, K_NLS_STEP, K_NLS_ROW, K_NLS_COL,
-                K_FFT_UPDATE, K_FFT_ZFWD, K_RCD_FFT, K_RCD_REACTION, K_COUNT };
+                K_FFT_UPDATE, K_FFT_ZFWD, K_RCD_FFT, K_RCD_REACTION, K_FFT_YFWD, K_COUNT };
 static const char* kProfName[K_COUNT] = {"fft_pass", "fft_fused_nl", "update_dense", "update_list", "assess",
                                          "nls_step", "nls_row", "nls_col", "fft_update", "fft_z_forward",
-                                         "rcd_fft", "rcd_reaction"};
+                                         "rcd_fft", "rcd_reaction", "fft_y_forward_pruned"};
 
 struct ProfRec {
     int kind;
@@ -385,6 +392,10 @@ static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* di
         SPDBA_CUDA(cudaMemsetAsync(r.pair_count, 0, sizeof(int), st));
         hmir.p.live_tiles = r.pair_list;
         hmir.p.live_count = r.pair_count;
+        if (r.g.nb[2] <= 64) {
+            if ((s = r.alloc(&r.col_live, (size_t)NHP)) != SPDBA_OK) return s;
+            SPDBA_CUDA(cudaMemsetAsync(r.col_live, 1, (size_t)NHP, st));
+        }
     }
     const int64_t dh[3] = {N0, N1, NHP};
     if ((s = make_axis_pass<float>(&hy_inv, 3, dh, 1, 1, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
@@ -469,6 +480,16 @@ static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const in
         if (ndim == 3 && batch == 1 && p->opt.half_spectrum) {
             s = setup_half(p, r, dims);
             if (s != SPDBA_OK && s != SPDBA_ERR_UNSUPPORTED) return s;
+        }
+        if (tma_update_fits(r.g)) {
+            // the list-driven update moves whole 8^3 blocks as TMA boxes
+            int per_sm = 0, nsm = 0;
+            if ((s = make_box_map(r.tma_map_c, r.c_hat, r.g)) != SPDBA_OK) return s;
+            if ((s = make_box_map(r.tma_map_g, r.work, r.g)) != SPDBA_OK) return s;
+            if ((s = tma_update_prepare(&per_sm, &nsm)) != SPDBA_OK) return s;
+            r.tma_grid = (long long)per_sm * nsm;
+            r.tma_ok = true;
+            r.use_tma = p->opt.tma_update != 0;
         }
     }
     return SPDBA_OK;
@@ -707,6 +728,12 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
                 if ((s = launch_pair_live_list(r.h_mirror, r.pair_list, r.pair_count, st)) != SPDBA_OK) return s;
                 p->launches += 1;
             }
+            if (r.col_live) {
+                if ((s = launch_half_col_live(r.g, r.states, (int)r.g.n[2], (int)r.h_fwd_y.p.I, r.col_live, st)) !=
+                    SPDBA_OK)
+                    return s;
+                p->launches += 1;
+            }
         }
     }
     const int dense = !adaptive || all_active_step(p, r.step);
@@ -735,8 +762,13 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
             if ((s = launch_pass<T>(nl, r.half, r.half, st)) != SPDBA_OK) return s;
         }
         {
-            ProfScope pr(p, K_FFT_PASS, 2.0 * half_b);
-            if ((s = launch_pass<T>(r.h_fwd_y, r.half, r.half, st)) != SPDBA_OK) return s;
+            // the staged form's y forward skips the x-frequency columns that no
+            // live z-forward tile reads (their outputs are never used)
+            Pass<T> yf = r.h_fwd_y;
+            const bool prune = !r.fused_update && !dense && r.col_live != nullptr;
+            if (prune) yf.p.col_live = r.col_live;
+            ProfScope pr(p, prune ? K_FFT_YFWD : K_FFT_PASS, 2.0 * half_b);
+            if ((s = launch_pass<T>(yf, r.half, r.half, st)) != SPDBA_OK) return s;
         }
         p->launches += 4;
         if (r.fused_update) {
@@ -817,7 +849,14 @@ template <typename T> static spdba_status ch_staged_update(spdba_plan* p, Group<
         // list-update traffic is known only on the device; it is added at profile end
         ProfScope pr(p, dense ? K_UPDATE_DENSE : K_UPDATE_LIST,
                      dense ? 3.0 * sizeof(cx_t<T>) * (double)(r.batch * r.n) : 0.0);
-        if ((s = launch_ch_update<T>(r.g, a, dense, st)) != SPDBA_OK) return s;
+        bool tma = false;
+        if constexpr (std::is_same<T, float>::value) tma = r.use_tma && !dense;
+        if (tma) {
+            if constexpr (std::is_same<T, float>::value)
+                if ((s = launch_ch_update_tma(r.tma_map_c, r.tma_map_g, r.g, a, r.tma_grid, st)) != SPDBA_OK) return s;
+        } else if ((s = launch_ch_update<T>(r.g, a, dense, st)) != SPDBA_OK) {
+            return s;
+        }
         p->launches += 1;
         if (!dense) p->list_updates += 1;
     }
@@ -1455,10 +1494,11 @@ template <typename T> static spdba_status snap_restore(spdba_plan* p, Group<T>& 
     return SPDBA_OK;
 }
 
-template <typename T> static void apply_config(spdba_plan* p, int fuse, int graph, int half) {
+template <typename T> static void apply_config(spdba_plan* p, int fuse, int graph, int half, int tma) {
     for (auto& g : groups<T>(p)) {
         g->fused_update = fuse && g->has_fused;
         g->use_half = half && g->has_half;
+        g->use_tma = tma && g->tma_ok;
     }
     p->opt.use_graph = graph;
     if (p->seg_exec) {
@@ -1472,12 +1512,13 @@ template <typename T> static void apply_config(spdba_plan* p, int fuse, int grap
 // keeps the fastest and restores the state.
 template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t steps, spdba_tune_report* rep) {
     auto& gs = groups<T>(p);
-    bool any_fused = false, any_half = false;
+    bool any_fused = false, any_half = false, any_tma = false;
     for (auto& g : gs) {
         any_fused |= g->has_fused;
         any_half |= g->has_half;
+        any_tma |= g->tma_ok;
     }
-    struct Cand { int fuse, graph, half; };
+    struct Cand { int fuse, graph, half, tma; };
     std::vector<Cand> cand;
     for (int hf : {1, 0}) {
         if (hf && !any_half) continue;
@@ -1485,7 +1526,11 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
             if (f && !any_fused) continue;
             for (int gr : {1, 0}) {
                 if (gr && p->st == 0) continue;   // graphs need a non-legacy stream
-                cand.push_back({f, gr, hf});
+                // the staged form's list-driven update: warp kernel or TMA kernel
+                for (int tm : {0, 1}) {
+                    if (tm && (f || !any_tma)) continue;
+                    cand.push_back({f, gr, hf, tm});
+                }
             }
         }
     }
@@ -1500,7 +1545,7 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
     if (s == SPDBA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         s = fail(SPDBA_ERR_CUDA, "autotune: cudaEventCreate failed");
     for (size_t c = 0; c < cand.size() && s == SPDBA_OK; ++c) {
-        apply_config<T>(p, cand[c].fuse, cand[c].graph, cand[c].half);
+        apply_config<T>(p, cand[c].fuse, cand[c].graph, cand[c].half, cand[c].tma);
         if ((s = plan_step<T>(p, R)) != SPDBA_OK) break;   // warm-up (graph capture)
         for (size_t i = 0; i < gs.size() && s == SPDBA_OK; ++i) s = snap_restore<T>(p, *gs[i], snaps[i]);
         if (s != SPDBA_OK) break;
@@ -1517,7 +1562,8 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
     size_t best = 0;
     for (size_t c = 1; c < cand.size(); ++c)
         if (ms[c] < ms[best]) best = c;
-    if (s == SPDBA_OK && !cand.empty()) apply_config<T>(p, cand[best].fuse, cand[best].graph, cand[best].half);
+    if (s == SPDBA_OK && !cand.empty())
+        apply_config<T>(p, cand[best].fuse, cand[best].graph, cand[best].half, cand[best].tma);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaError_t e = cudaStreamSynchronize(p->st);
@@ -1532,6 +1578,7 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
             rep->fuse_update[c] = cand[c].fuse;
             rep->use_graph[c] = cand[c].graph;
             rep->half_spectrum[c] = cand[c].half;
+            rep->tma_update[c] = cand[c].tma;
             rep->ms_per_step[c] = ms[c];
         }
         rep->chosen = (int32_t)best;
@@ -1598,6 +1645,7 @@ template <typename T> static spdba_status get_stats_t(spdba_plan* p, Group<T>& r
     out->missed_blocks = (int64_t)d.missed;
     out->threshold = d.eps;
     out->controls = (int64_t)d.controls;
+    if (d.timeouts) return fail(SPDBA_ERR_TIMEOUT, "a bounded device wait ran out (%llu times)", d.timeouts);
     return SPDBA_OK;
 }
 

@@ -1,0 +1,64 @@
+"""Run one plan configuration for a fixed number of steps, for kernel profilers.
+
+Kernel profilers (ncu) select launches by kernel name and launch index; this
+runs the 3-D Cahn-Hilliard workload from its seeded initial field for
+`--warm` steps (so that the captured steps see the run's steady block states),
+then `--steps` more, with direct kernel launches (no graph replay) on a
+non-default stream, and prints the plan's statistics.  Every step runs in the
+library's kernels; this module only drives the plan.
+
+Example (256^3, complex64, the staged half-spectrum form, steps 500..509):
+    python -m paper_2609_03922_gb300.profile_step --dims 256 256 256 --warm 500 --steps 10
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs=3, default=[256, 256, 256])
+    ap.add_argument("--block", type=int, nargs=3, default=[8, 8, 8])
+    ap.add_argument("--threshold", type=float, default=1e-6)
+    ap.add_argument("--reassess", type=int, default=10)
+    ap.add_argument("--mode", choices=["adaptive", "regular"], default="adaptive")
+    ap.add_argument("--fuse", type=int, default=0, help="1: update fused into the last forward pass")
+    ap.add_argument("--half", type=int, default=1, help="1: Hermitian half-spectrum transforms")
+    ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--mean", type=float, default=0.1)
+    ap.add_argument("--warm", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=10)
+    args = ap.parse_args(argv)
+
+    import torch
+    from paper_2609_03922_gb300 import build as B
+    B.build()
+    from paper_2609_03922_gb300 import spdba
+    import workloads as W
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    prec = spdba.SPDBA_C64 if args.precision == "c64" else spdba.SPDBA_C128
+    rdt = np.float32 if prec == spdba.SPDBA_C64 else np.float64
+    dims = tuple(args.dims)
+    c0 = W.ch_initial_condition(dims, mean=args.mean, seed=W.BASE_SEED).astype(rdt)
+    with spdba.Plan(dims, tuple(args.block), threshold=args.threshold, reassess=args.reassess, precision=prec,
+                    mode=spdba.SPDBA_MODE_ADAPTIVE if args.mode == "adaptive" else spdba.SPDBA_MODE_REGULAR,
+                    fuse_update=args.fuse, half_spectrum=args.half, use_graph=0) as plan:
+        plan.set_field(c0)
+        plan.step(args.warm)
+        plan.step(args.steps)
+        plan.sync()
+        st = plan.get_stats()
+    print(json.dumps({"dims": dims, "steps": st["step"], "n_active": st["n_active"],
+                      "n_transition": st["n_transition"], "nblocks": st["nblocks"]}))
+
+
+if __name__ == "__main__":
+    main()

@@ -34,7 +34,8 @@ class spdba_options(ctypes.Structure):
                 ("target_ratio", ctypes.c_double), ("control_eta", ctypes.c_double),
                 ("control_every", ctypes.c_int32), ("components", ctypes.c_int32),
                 ("rcd_d_diag", ctypes.c_double), ("rcd_d_cross", ctypes.c_double), ("rcd_alpha", ctypes.c_double),
-                ("rcd_beta", ctypes.c_double), ("rcd_r", ctypes.c_double), ("rcd_a", ctypes.c_double)]
+                ("rcd_beta", ctypes.c_double), ("rcd_r", ctypes.c_double), ("rcd_a", ctypes.c_double),
+                ("tma_update", ctypes.c_int32)]
 
 
 class spdba_stats(ctypes.Structure):
@@ -45,10 +46,14 @@ class spdba_stats(ctypes.Structure):
                 ("threshold", ctypes.c_double), ("controls", ctypes.c_int64)]
 
 
+TUNE_MAX = 16
+
+
 class spdba_tune_report(ctypes.Structure):
-    _fields_ = [("n_candidates", ctypes.c_int32), ("fuse_update", ctypes.c_int32 * 8),
-                ("use_graph", ctypes.c_int32 * 8), ("half_spectrum", ctypes.c_int32 * 8),
-                ("ms_per_step", ctypes.c_double * 8), ("chosen", ctypes.c_int32)]
+    _fields_ = [("n_candidates", ctypes.c_int32), ("fuse_update", ctypes.c_int32 * TUNE_MAX),
+                ("use_graph", ctypes.c_int32 * TUNE_MAX), ("half_spectrum", ctypes.c_int32 * TUNE_MAX),
+                ("tma_update", ctypes.c_int32 * TUNE_MAX),
+                ("ms_per_step", ctypes.c_double * TUNE_MAX), ("chosen", ctypes.c_int32)]
 
 
 class spdba_kernel_time(ctypes.Structure):
@@ -269,7 +274,8 @@ class Plan:
         rep = spdba_tune_report()
         check(lib().spdba_plan_autotune(self._p, int(steps), ctypes.byref(rep)))
         cands = [{"fuse_update": int(rep.fuse_update[i]), "use_graph": int(rep.use_graph[i]),
-                  "half_spectrum": int(rep.half_spectrum[i]), "ms_per_step": float(rep.ms_per_step[i])}
+                  "half_spectrum": int(rep.half_spectrum[i]), "tma_update": int(rep.tma_update[i]),
+                  "ms_per_step": float(rep.ms_per_step[i])}
                  for i in range(rep.n_candidates)]
         return {"candidates": cands, "chosen": int(rep.chosen)}
 

@@ -293,3 +293,22 @@ def test_autotune_restores_state_and_keeps_results():
         assert np.array_equal(ma, mb)
         assert ta["step"] == tb["step"] == 23 and ta["assessments"] == tb["assessments"]
         assert ta["active_ratio_sum"] == tb["active_ratio_sum"]
+
+
+def test_tma_list_update_equals_warp_list_update():
+    """The staged update moved by TMA boxes (3-D complex64, 8^3 blocks) gives the
+    values of the per-warp list kernel bit for bit, through several state settings."""
+    from paper_2609_03922_gb300 import spdba
+    dims = (64, 64, 64)
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 44).astype(np.float32)
+    outs = []
+    for tma in (0, 1):
+        with spdba.Plan(dims, (8, 8, 8), threshold=1e-3, reassess=4, precision=0, fuse_update=0,
+                        tma_update=tma) as plan:
+            plan.set_field(c0)
+            plan.step(23)
+            outs.append((plan.get_spectrum(), plan.get_mask(), plan.get_stats()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.any(outs[0][1] == 0)
+    assert outs[1][2]["active_ratio_sum"] == outs[0][2]["active_ratio_sum"]
