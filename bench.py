@@ -9,10 +9,12 @@ c0 = 0.1 + U[-0.05, 0.05] (seed 1234).  A "step" is one solver step of the
 whole hot path (inverse FFT, nonlinearity, forward FFT, state preparation
 every 10 steps, blockwise update).
 
-The plans run from c0 to step 500 (untimed; blocks have frozen by then) and
-autotune there; `value` is K steps from that state, timed with CUDA events
-and repeated from the same state until the timed steps add up to 1 s
-(median).  The line also carries the configuration's own comparison (the
+The plans autotune at step 500 of the run (untimed; from c0 every block is
+active, later blocks freeze).  `value` is K steps timed with CUDA events from
+each of 8 states spread evenly over the configuration's 2000-step run (steps
+0, 250, ..., 1750; for K >= 250 from c0 alone, so that the timed steps are
+the run itself), the mean per window, the set repeated until the timed steps
+add up to 1 s (median).  The line also carries the configuration's own comparison (the
 whole 2000-step run from c0, adaptive vs dense), the staged form's
 update-stage speedup, per-kernel GB/s (algorithmic, dense-equivalent, ncu
 DRAM), a cuFFT comparator, the end-to-end figure through host buffers, and
@@ -62,31 +64,40 @@ def prof_every(k):
 
 
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels
-# on the 256^3 field (cold L2 at the start of each launch), by kernel kind:
+# on the 256^3 field, one launch each at step 505 of the staged half-spectrum
+# run (cold L2 at the start of each launch; profiles/ch3d256_step_kernels.md):
 TOUCHED_BYTES = {
-    # z forward + fused update of the half-spectrum form: 250.95 MB read, 87.26 MB written
+    # z forward + fused update of the half-spectrum form (an early, mostly active step): 250.95 MB read, 87.26 MB written
     "fft_update": 250.95e6 + 87.26e6,
-    # paired z forward of the staged form with block states: 79.77 MB read, 38.01 MB written
-    "fft_z_forward": 79.77e6 + 38.01e6,
-    # x pass (two real rows per transform): 75.54 MB read, 15.38 MB written
-    "fft_fused_nl": 75.54e6 + 15.38e6,
-    # list-driven update: 173.46 MB read, 44.28 MB written
-    "update_list": 173.46e6 + 44.28e6,
-    # z inverse 144.23 + 37.44, y inverse 75.55 + 15.15, y forward 75.55 + 15.43 MB, averaged
-    "fft_pass": (144.23e6 + 37.44e6 + 75.55e6 + 15.15e6 + 75.55e6 + 15.43e6) / 3,
+    # paired z forward of the staged form with block states: 52.03 MB read, 6.57 MB written
+    "fft_z_forward": 52.03e6 + 6.57e6,
+    # x pass (two real rows per transform): 75.53 MB read, 14.72 MB written
+    "fft_fused_nl": 75.53e6 + 14.72e6,
+    # list-driven update (per-warp loads): 82.58 MB read, 4.32 MB written
+    "update_list": 82.58e6 + 4.32e6,
+    # y forward pruned to the live x-frequency columns: 58.78 MB read, 4.07 MB written
+    "fft_y_forward_pruned": 58.78e6 + 4.07e6,
+    # z inverse 144.16 + 37.32 and y inverse 75.55 + 14.80 MB, averaged (the staged form's plain passes)
+    "fft_pass": (144.16e6 + 37.32e6 + 75.55e6 + 14.80e6) / 2,
+    # activity scan (rows kernel): 134.26 MB read, 3.11 MB written
+    "assess": 134.26e6 + 3.11e6,
 }
 TOUCHED_NOTE = {
     "fft_update": "ncu DRAM read + write of one launch (an early, mostly active step)",
-    "fft_z_forward": "ncu DRAM read + write of one launch (autotuner's staged candidates at step 50); part of the "
-                     "output is still in L2 when the launch ends",
-    "fft_fused_nl": "ncu DRAM read + write of one launch (cold L2)",
-    "update_list": "ncu DRAM read + write of one launch (autotuner's staged candidates at step 50)",
-    "fft_pass": "ncu DRAM read + write per launch, averaged over the z inverse and the two y passes (cold L2)",
+    "fft_z_forward": "ncu DRAM read + write of one launch at step 505 (cold L2; part of the output is still in L2 "
+                     "when the launch ends)",
+    "fft_fused_nl": "ncu DRAM read + write of one launch at step 505 (cold L2)",
+    "update_list": "ncu DRAM read + write of one launch at step 505",
+    "fft_y_forward_pruned": "ncu DRAM read + write of one launch at step 505",
+    "fft_pass": "ncu DRAM read + write per launch, averaged over the z inverse and the y inverse (cold L2)",
+    "assess": "ncu DRAM read + write of one scan at step 510 (the scan launch only; the classification's three "
+              "small launches are in the same kind)",
 }
 CONTROL_TARGETS = (0.05, 0.1, 0.2)   # dynamic threshold control targets (S1.3: 5-20 %)
 CONTROL_EVERY = 50                   # control interval (S3.2, S4.2, S5.3)
 CONTROL_ETA = 0.05                   # adjustment factor (S3.2, S5.3)
-TUNE_AT = 500          # step of the run where the plans are tuned and the timed window starts
+TUNE_AT = 500          # step of the run where the plans are tuned
+NSNAP = 8              # timed windows start at NSNAP states spread over the run
 FULL_RUN = 2000        # the configuration's whole run
 MIN_TIMED_S = 1.0      # the timed region is repeated until it adds up to this (clock samples)
 MAX_REPS = 5000
@@ -164,6 +175,15 @@ def _median(xs):
     return float(np.median(np.asarray(xs, dtype=np.float64)))
 
 
+def snapshot_steps(k):
+    """Starts of the timed windows: NSNAP states spread evenly over the
+    configuration's run when K steps fit between them, else the run's start."""
+    gap = FULL_RUN // NSNAP
+    if k >= gap:
+        return [0]
+    return [gap * i for i in range(NSNAP)]
+
+
 def cufft_comparator(dev, reps=20):
     """cuFFT (through torch.fft) on the 256^3 complex64 field: the C2C forward +
     inverse pair and the R2C + C2R pair the step's transforms correspond to.
@@ -227,23 +247,34 @@ def run_ours(args, rank, world, local_rank, parity=None):
 
     def prepare(plan):
         """From c0 to step TUNE_AT (blocks have frozen there), where the plan's
-        autotuner picks its launch configuration; returns the report and the
-        plan's c_hat at that step (device)."""
+        autotuner picks its launch configuration; then the run again from c0,
+        keeping c_hat at the window starts: steps 0, FULL_RUN/NSNAP, ...
+        (NSNAP states spread over the configuration's run) when K is shorter
+        than that spacing, else step 0 alone (the timed steps are then the run
+        itself).  Returns the tuner's report and the states (device)."""
         plan.set_field(c0_dev)
         plan.step(TUNE_AT)
         tune = plan.autotune(2 * REASSESS)
         tune["at_step"] = TUNE_AT
-        snap = torch.empty(DIMS, dtype=torch.complex64, device=dev)
-        plan.get_spectrum(snap)
-        return tune, snap
+        starts = snapshot_steps(K)
+        plan.set_field(c0_dev)
+        snaps, at = [], 0
+        for s in starts:
+            plan.step(s - at)
+            at = s
+            snap = torch.empty(DIMS, dtype=torch.complex64, device=dev)
+            plan.get_spectrum(snap)
+            snaps.append(snap)
+        return tune, snaps
 
-    def window(plan, snap, sampler_on=False, profile=False, reps=None):
-        """W warm-up steps from the step-TUNE_AT state, then K timed steps from
-        that state, repeated (same state each time) until the timed steps add
-        up to MIN_TIMED_S (at least 3 times).  Returns (median ms of K steps
-        -- max over ranks --, repetitions, wall interval, profile)."""
+    def window(plan, snaps, profile=False, reps=None):
+        """W warm-up steps, then K timed steps from each of the states in `snaps`
+        (CUDA events around each K-step stretch), the set repeated until the timed
+        steps add up to MIN_TIMED_S (at least 3 times).  Returns (median over the
+        repetitions of the mean ms per K steps -- max over ranks --, repetitions,
+        wall interval, profile)."""
         st = torch.cuda.current_stream()
-        plan.set_spectrum(snap)
+        plan.set_spectrum(snaps[0])
         plan.step(Wm)
         torch.cuda.synchronize()
         ms_list = []
@@ -253,21 +284,24 @@ def run_ours(args, rank, world, local_rank, parity=None):
         t0 = time.time()
         n = 0
         while True:
-            plan.set_spectrum(snap)
-            torch.cuda.synchronize()
-            barrier()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            plan.step(K)
-            e1.record(st)
-            torch.cuda.synchronize()
-            ms_list.append(e0.elapsed_time(e1))
+            tot = 0.0
+            for snap in snaps:
+                plan.set_spectrum(snap)
+                torch.cuda.synchronize()
+                barrier()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                plan.step(K)
+                e1.record(st)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms_list.append(tot / len(snaps))
             n += 1
             if reps is None and n == 1:
                 # every rank runs the same number of repetitions
-                reps = int(max_over_ranks(float(max(3, math.ceil(1e3 * MIN_TIMED_S / max(ms_list[0], 1e-3))))))
+                reps = int(max_over_ranks(float(max(3, math.ceil(1e3 * MIN_TIMED_S / max(tot, 1e-3))))))
                 reps = min(reps, MAX_REPS)
             if n >= reps:
                 break
@@ -297,27 +331,33 @@ def run_ours(args, rank, world, local_rank, parity=None):
 
     sampler = ClockSampler(local_rank) if rank == 0 else None
 
-    # ---- the adaptive plan: tuned at step TUNE_AT, timed on K steps from there
+    # ---- the adaptive plan: tuned at step TUNE_AT, timed on K steps from states
+    # spread over the configuration's run
     ada = make(spdba.SPDBA_MODE_ADAPTIVE, 1)
     tune, snap_ada = prepare(ada)
+    starts = snapshot_steps(K)
     time.sleep(0.3 if sampler else 0)
     ms_ada, reps_ada, (t0, t1), _ = window(ada, snap_ada)
     clocks = sampler.stop(t0, t1) if sampler else None
-    # kernel events of every step, on separate repetitions of the same window
-    prof_reps = max(3, -(-PROFILE_STEPS // K))
+    # kernel events of every step, on separate repetitions of the same windows
+    prof_reps = max(1, -(-PROFILE_STEPS // (K * len(snap_ada))))
     _, _, _, prof = window(ada, snap_ada, profile=True, reps=prof_reps)
-    # the window's mean non-frozen share, from the run statistics around one more pass
-    ada.set_spectrum(snap_ada)
-    s0 = ada.get_stats()
-    ada.step(K)
-    s1 = ada.get_stats()
-    ratio_win = (s1["active_ratio_sum"] - s0["active_ratio_sum"]) / max(1, s1["step"] - s0["step"])
+    # the windows' mean non-frozen share, from the run statistics around one more pass
+    nf_sum, nf_steps = 0.0, 0
+    for snap in snap_ada:
+        ada.set_spectrum(snap)
+        s0 = ada.get_stats()
+        ada.step(K)
+        s1 = ada.get_stats()
+        nf_sum += s1["active_ratio_sum"] - s0["active_ratio_sum"]
+        nf_steps += s1["step"] - s0["step"]
+    ratio_win = nf_sum / max(1, nf_steps)
 
-    # ---- the dense plan (Regular) on the same window of its own run
+    # ---- the dense plan (Regular) on the same windows of its own run
     dense = make(spdba.SPDBA_MODE_REGULAR, 1)
     tune_dense, snap_dense = prepare(dense)
     ms_dense, _, _, _ = window(dense, snap_dense)
-    _, _, _, prof_dense = window(dense, snap_dense, profile=True, reps=max(3, -(-PROFILE_STEPS // K)))
+    _, _, _, prof_dense = window(dense, snap_dense, profile=True, reps=prof_reps)
 
     # ---- the configuration's own comparison: the whole 2000-step run from c0, each
     # plan in the configuration its autotuner chose at step TUNE_AT
@@ -338,8 +378,8 @@ def run_ours(args, rank, world, local_rank, parity=None):
     for target in CONTROL_TARGETS:
         pl = make(spdba.SPDBA_MODE_ADAPTIVE, 1, target_ratio=target, control_every=CONTROL_EVERY,
                   control_eta=CONTROL_ETA)
-        tune_c, snap = prepare(pl)
-        del snap
+        tune_c, snaps_c = prepare(pl)
+        del snaps_c
         ms_c, _ = full_run(pl)
         st_c = pl.get_stats()
         f_c = torch.empty(DIMS, dtype=torch.float32, device=dev)
@@ -360,35 +400,41 @@ def run_ours(args, rank, world, local_rank, parity=None):
         pl = make(mode, 0)
         _, snap = prepare(pl)
         ms, _, _, _ = window(pl, snap)
-        _, _, _, pr = window(pl, snap, profile=True, reps=max(3, -(-PROFILE_STEPS // K)))
+        _, _, _, pr = window(pl, snap, profile=True, reps=prof_reps)
         nsteps = max(1, pr[0]["fft_fused_nl"]["launches"])
         upd = sum(pr[0].get(k, {"total_ms": 0.0})["total_ms"] for k in ("update_list", "update_dense", "assess"))
         staged[name] = {"steps_per_s": world * K / (ms / 1e3), "update_stage_ms_per_step": upd / nsteps}
         pl.close()
         del snap
 
-    # ---- end to end through the C ABI with host buffers: the step-TUNE_AT field
-    # uploaded from pinned host memory, K steps, the field read back to pinned host
-    # memory (median of repetitions, like the device-timed window)
-    ada.set_spectrum(snap_ada)
-    f_tune = torch.empty(DIMS, dtype=torch.float32, device=dev)
-    ada.get_field(f_tune)
-    in_pin = f_tune.cpu().pin_memory()
+    # ---- end to end through the C ABI with host buffers: each window's starting
+    # field uploaded from pinned host memory, K steps, the field read back to
+    # pinned host memory (median over repetitions of the mean per window)
+    in_pins = []
+    for snap in snap_ada:
+        ada.set_spectrum(snap)
+        f_s = torch.empty(DIMS, dtype=torch.float32, device=dev)
+        ada.get_field(f_s)
+        in_pins.append(f_s.cpu().pin_memory())
+        del f_s
     out_pin = torch.empty(DIMS, dtype=torch.float32).pin_memory()
-    del f_tune
-    ada.set_field(in_pin)
+    ada.set_field(in_pins[0])
     ada.step(Wm)
     ada.get_field(out_pin)
     e2e_ms = []
     for _ in range(reps_ada):
-        barrier()
-        torch.cuda.synchronize()
-        te0 = time.perf_counter()
-        ada.set_field(in_pin)
-        ada.step(K)
-        ada.get_field(out_pin)          # synchronizes the plan's stream
-        e2e_ms.append((time.perf_counter() - te0) * 1e3)
+        tot = 0.0
+        for in_pin in in_pins:
+            barrier()
+            torch.cuda.synchronize()
+            te0 = time.perf_counter()
+            ada.set_field(in_pin)
+            ada.step(K)
+            ada.get_field(out_pin)          # synchronizes the plan's stream
+            tot += (time.perf_counter() - te0) * 1e3
+        e2e_ms.append(tot / len(in_pins))
     e2e = max_over_ranks(_median(e2e_ms))
+    del in_pins
 
     # ---- parity legs (GPU side): the adaptive run's field after the oracle's
     # sample of steps at full size, and a whole run at 64^3 (same parameters)
@@ -498,9 +544,8 @@ def run_ours(args, rank, world, local_rank, parity=None):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(DIMS), "block": list(BLOCK), "threshold_rel": THRESHOLD,
                    "reassess": REASSESS, "dt": DT, "kappa": KAPPA, "ic": "0.1+U[-0.05,0.05] seed 1234",
-                   "timed": ("%d steps from the run's state at step %d (c0 advanced %d steps, untimed, then "
-                             "autotuned); the K-step region repeated %d times from that state, median"
-                             % (K, TUNE_AT, TUNE_AT, reps_ada)),
+                   "timed": ("%d steps from each of the run's states at steps %s (plans autotuned at step %d); "
+                             "mean per window, the set repeated %d times, median" % (K, starts, TUNE_AT, reps_ada)),
                    "l2": "working set larger than L2 (c_hat 134 MB + half-spectrum workspace 75 MB per replica)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "dense_steps_per_s": dense_value,
@@ -538,8 +583,8 @@ def run_ours(args, rank, world, local_rank, parity=None):
                                       "forward or z forward + update) from the profiled window"),
         "e2e": {"value": world * K / (e2e / 1e3), "unit": "steps/s",
                 "h2d_bytes_per_step": 4.0 * n / K, "d2h_bytes_per_step": 4.0 * n / K,
-                "note": ("set_field of the step-%d field from pinned host + %d steps + get_field to pinned "
-                         "host, median of %d" % (TUNE_AT, K, reps_ada))},
+                "note": ("set_field of each window's starting field (steps %s) from pinned host + %d steps + "
+                         "get_field to pinned host; mean per window, median of %d" % (starts, K, reps_ada))},
         "gpu_launches": int(round(prof[1] / prof_reps)),
         "clocks": clocks,
     }

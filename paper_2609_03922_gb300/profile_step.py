@@ -9,6 +9,8 @@ library's kernels; this module only drives the plan.
 
 Example (256^3, complex64, the staged half-spectrum form, steps 500..509):
     python -m paper_2609_03922_gb300.profile_step --dims 256 256 256 --warm 500 --steps 10
+RCD (M components; dx = 0.5):
+    python -m paper_2609_03922_gb300.profile_step --model rcd --components 48 --dims 128 128 128 --block 4 4 4
 """
 import argparse
 import json
@@ -31,10 +33,13 @@ def main(argv=None):
     ap.add_argument("--mode", choices=["adaptive", "regular"], default="adaptive")
     ap.add_argument("--fuse", type=int, default=0, help="1: update fused into the last forward pass")
     ap.add_argument("--half", type=int, default=1, help="1: Hermitian half-spectrum transforms")
+    ap.add_argument("--tma", type=int, default=0, help="1: staged update moved by TMA boxes")
     ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
     ap.add_argument("--mean", type=float, default=0.1)
     ap.add_argument("--warm", type=int, default=500)
     ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--model", choices=["ch", "rcd"], default="ch")
+    ap.add_argument("--components", type=int, default=48, help="RCD: components M")
     args = ap.parse_args(argv)
 
     import torch
@@ -47,10 +52,16 @@ def main(argv=None):
     prec = spdba.SPDBA_C64 if args.precision == "c64" else spdba.SPDBA_C128
     rdt = np.float32 if prec == spdba.SPDBA_C64 else np.float64
     dims = tuple(args.dims)
-    c0 = W.ch_initial_condition(dims, mean=args.mean, seed=W.BASE_SEED).astype(rdt)
+    kw = {}
+    if args.model == "rcd":
+        M = args.components
+        c0 = W.rcd_initial_condition(dims, M, W.rcd_lv_homogeneous(M), 0.1, seed=W.BASE_SEED + M).astype(rdt)
+        kw = dict(model=spdba.SPDBA_MODEL_RCD, components=M, dx=0.5)
+    else:
+        c0 = W.ch_initial_condition(dims, mean=args.mean, seed=W.BASE_SEED).astype(rdt)
     with spdba.Plan(dims, tuple(args.block), threshold=args.threshold, reassess=args.reassess, precision=prec,
                     mode=spdba.SPDBA_MODE_ADAPTIVE if args.mode == "adaptive" else spdba.SPDBA_MODE_REGULAR,
-                    fuse_update=args.fuse, half_spectrum=args.half, use_graph=0) as plan:
+                    fuse_update=args.fuse, half_spectrum=args.half, use_graph=0, tma_update=args.tma, **kw) as plan:
         plan.set_field(c0)
         plan.step(args.warm)
         plan.step(args.steps)
