@@ -89,7 +89,19 @@ template <typename C> __device__ __forceinline__ double rcd_mode_sq(const C* __r
 template <> __device__ __forceinline__ double rcd_mode_sq<float2>(const float2* __restrict__ q, long long n,
                                                                    long long e, int M) {
     float hi = 0.f, lo = 0.f;
-    for (int m = 0; m < M; ++m) {
+    // the component loads of a group of 8 are issued before any is used
+    int m = 0;
+    for (; m + 8 <= M; m += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = q[(long long)(m + k) * n + e];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            rcd_acc_sq(v[k].x, hi, lo);
+            rcd_acc_sq(v[k].y, hi, lo);
+        }
+    }
+    for (; m < M; ++m) {
         const float2 v = q[(long long)m * n + e];
         rcd_acc_sq(v.x, hi, lo);
         rcd_acc_sq(v.y, hi, lo);
@@ -161,18 +173,19 @@ constexpr int RCD_RG = RCD_NT / RCD_COLS;
 template <int MM> __host__ __device__ constexpr int rcd_smem_elems() { return 2 * MM * MM + 2 * MM * RCD_COLS; }
 
 // acc += dot(row[0 .. MM), col[0 .. MM)) with 16-byte row reads
+// (two partial sums: half the dependent FMA chain)
 template <int MM>
 __device__ __forceinline__ float rcd_dot(const float* __restrict__ row, const float (&col)[MM]) {
-    float acc = 0.f;
+    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
     for (int i = 0; i < MM; i += 4) {
         const float4 v = *reinterpret_cast<const float4*>(row + i);
-        acc = fmaf(v.x, col[i], acc);
-        acc = fmaf(v.y, col[i + 1], acc);
-        acc = fmaf(v.z, col[i + 2], acc);
-        acc = fmaf(v.w, col[i + 3], acc);
+        a0 = fmaf(v.x, col[i], a0);
+        a1 = fmaf(v.y, col[i + 1], a1);
+        a0 = fmaf(v.z, col[i + 2], a0);
+        a1 = fmaf(v.w, col[i + 3], a1);
     }
-    return acc;
+    return a0 + a1;
 }
 template <int MM>
 __device__ __forceinline__ double rcd_dot(const double* __restrict__ row, const double (&col)[MM]) {
@@ -186,8 +199,14 @@ __device__ __forceinline__ double rcd_dot(const double* __restrict__ row, const 
     return acc;
 }
 
+// CTAs per SM the update kernel is compiled for: three for complex64 up to 48
+// components (shared memory 67.6 KB at 48), else as registers allow
+template <typename T, int MM> struct RcdOcc {
+    static constexpr int value = sizeof(T) == 4 ? (MM <= 48 ? 3 : 2) : 1;
+};
+
 template <typename T, int MM>
-__global__ void __launch_bounds__(RCD_NT) rcd_update_kernel(Geom g, RcdArgs<T> a, int dense) {
+__global__ void __launch_bounds__(RCD_NT, RcdOcc<T, MM>::value) rcd_update_kernel(Geom g, RcdArgs<T> a, int dense) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sVt = reinterpret_cast<T*>(smem_raw);   // sVt[j * MM + i] = V[i][j] (zero padded)
     T* sV = sVt + MM * MM;                     // sV[i * MM + j] = V[i][j]
@@ -229,21 +248,40 @@ __global__ void __launch_bounds__(RCD_NT) rcd_update_kernel(Geom g, RcdArgs<T> a
         const int ti = (int)(w % tpb);
         const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
         __syncthreads();   // the previous tile's stores have read sY
-        // load u_hat and b = u_hat + dt g_hat of the tile's modes
-        for (int e = threadIdx.x; e < MM * RCD_TM; e += RCD_NT) {
-            const int m = e / RCD_TM, t = e - (e / RCD_TM) * RCD_TM;
-            const int o = ti * RCD_TM + t;
-            cx_t<T> u = mk<cx_t<T>>((T)0, (T)0), gg = u;
-            if (m < M && o < bm) {
-                const int d2 = o % B2, d1 = (o / B2) % B1, d0 = o / (B2 * B1);
-                const long long idx = ((b0 * B0 + d0) * g.n[1] + (b1 * B1 + d1)) * g.n[2] + (b2 * B2 + d2);
-                u = a.u_hat[(long long)m * n + idx];
-                gg = a.g_hat[(long long)m * n + idx];
+        // load u_hat and b = u_hat + dt g_hat of the tile's modes: thread e handles
+        // mode t = e % RCD_TM of components m = e / RCD_TM, e / RCD_TM + RCD_NT / RCD_TM, ...
+        constexpr int LSTEP = RCD_NT / RCD_TM;   // components per pass of the CTA
+        constexpr int LPER = (MM + LSTEP - 1) / LSTEP;
+        const int lt = threadIdx.x % RCD_TM, lm0 = threadIdx.x / RCD_TM;
+        const int lo = ti * RCD_TM + lt;
+        const bool lvalid = lo < bm;
+        long long lidx = 0;
+        if (lvalid) {
+            const int d2 = lo % B2, d1 = (lo / B2) % B1, d0 = lo / (B2 * B1);
+            lidx = ((b0 * B0 + d0) * g.n[1] + (b1 * B1 + d1)) * g.n[2] + (b2 * B2 + d2);
+        }
+        {
+            cx_t<T> u[LPER], gg[LPER];
+#pragma unroll
+            for (int k = 0; k < LPER; ++k) {
+                const int m = lm0 + LSTEP * k;
+                u[k] = mk<cx_t<T>>((T)0, (T)0);
+                gg[k] = u[k];
+                if (m < M && lvalid) {
+                    u[k] = a.u_hat[(long long)m * n + lidx];
+                    gg[k] = a.g_hat[(long long)m * n + lidx];
+                }
             }
-            sU[m * RCD_COLS + 2 * t] = u.x;
-            sU[m * RCD_COLS + 2 * t + 1] = u.y;
-            sY[m * RCD_COLS + 2 * t] = u.x + a.dt * gg.x;
-            sY[m * RCD_COLS + 2 * t + 1] = u.y + a.dt * gg.y;
+#pragma unroll
+            for (int k = 0; k < LPER; ++k) {
+                const int m = lm0 + LSTEP * k;
+                if (m < MM) {
+                    sU[m * RCD_COLS + 2 * lt] = u[k].x;
+                    sU[m * RCD_COLS + 2 * lt + 1] = u[k].y;
+                    sY[m * RCD_COLS + 2 * lt] = u[k].x + a.dt * gg[k].x;
+                    sY[m * RCD_COLS + 2 * lt + 1] = u[k].y + a.dt * gg[k].y;
+                }
+            }
         }
         __syncthreads();
         // this column's mode: |k|^2 and (transition blocks) the taper weight
@@ -285,13 +323,13 @@ __global__ void __launch_bounds__(RCD_NT) rcd_update_kernel(Geom g, RcdArgs<T> a
             sY[i * RCD_COLS + c] = st == SPDBA_ACTIVE ? xi : ui + sg * (xi - ui);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < M * RCD_TM; e += RCD_NT) {
-            const int m = e / RCD_TM, t = e - (e / RCD_TM) * RCD_TM;
-            const int oo = ti * RCD_TM + t;
-            if (oo < bm) {
-                const int e2 = oo % B2, e1 = (oo / B2) % B1, e0 = oo / (B2 * B1);
-                const long long idx = ((b0 * B0 + e0) * g.n[1] + (b1 * B1 + e1)) * g.n[2] + (b2 * B2 + e2);
-                a.u_hat[(long long)m * n + idx] = mk<cx_t<T>>(sY[m * RCD_COLS + 2 * t], sY[m * RCD_COLS + 2 * t + 1]);
+        if (lvalid) {
+#pragma unroll
+            for (int k = 0; k < LPER; ++k) {
+                const int m = lm0 + LSTEP * k;
+                if (m < M)
+                    a.u_hat[(long long)m * n + lidx] =
+                        mk<cx_t<T>>(sY[m * RCD_COLS + 2 * lt], sY[m * RCD_COLS + 2 * lt + 1]);
             }
         }
     }
