@@ -267,6 +267,14 @@ def run_ours(args, rank, world, local_rank, parity=None):
             snaps.append(snap)
         return tune, snaps
 
+    def align(plan):
+        """Untimed steps until the plan's step count is a multiple of the
+        reassessment interval, so that every window starts where the run's
+        reassessments fall (each window then has the run's share of scans)."""
+        r = (-int(plan.get_stats()["step"])) % REASSESS
+        if r:
+            plan.step(r)
+
     def window(plan, snaps, profile=False, reps=None):
         """W warm-up steps, then K timed steps from each of the states in `snaps`
         (CUDA events around each K-step stretch), the set repeated until the timed
@@ -286,6 +294,7 @@ def run_ours(args, rank, world, local_rank, parity=None):
         while True:
             tot = 0.0
             for snap in snaps:
+                align(plan)
                 plan.set_spectrum(snap)
                 torch.cuda.synchronize()
                 barrier()
@@ -345,6 +354,7 @@ def run_ours(args, rank, world, local_rank, parity=None):
     # the windows' mean non-frozen share, from the run statistics around one more pass
     nf_sum, nf_steps = 0.0, 0
     for snap in snap_ada:
+        align(ada)
         ada.set_spectrum(snap)
         s0 = ada.get_stats()
         ada.step(K)

@@ -80,3 +80,32 @@ def test_metrics_closed_form():
     assert math.isclose(O.nmse_db(1.1 * x, x), 10 * math.log10(0.01), rel_tol=1e-12)
     assert math.isclose(O.field_corr(2j * x, x), 1.0, rel_tol=1e-15)
     assert math.isclose(O.rel_l2(1.5 * x, x), 0.5, rel_tol=1e-15)
+
+
+def test_masked_half_step_transition_weights_by_hand():
+    """One linear half-step on a 1-D map of 4 blocks of B = 4 bins with states
+    (ACTIVE, TRANSITION, FROZEN, FROZEN): the ACTIVE block takes E H, the FROZEN
+    blocks keep E, and the TRANSITION block (its lower neighbour ACTIVE, its upper
+    neighbour FROZEN) takes E + w(B-1-i) (E H - E) with the taper
+    w = (1 - cos(pi i / 3)) / 2 = (0, 1/4, 3/4, 1), so w(3 - i) = (1, 3/4, 1/4, 0)
+    (S1.1, Eq. S.1-S.3)."""
+    n, B = 16, 4
+    E = (np.arange(n) + 1.0) * (1.0 + 0.5j)
+    H = np.exp(1j * 0.1 * np.arange(n))
+    states = np.array([O.STATE_ACTIVE, O.STATE_TRANSITION, O.STATE_FROZEN, O.STATE_FROZEN], dtype=np.uint8)
+    out = O.nls_masked_half(E, states, (B,), H)
+    new = E * H
+    assert np.array_equal(out[0:4], new[0:4])
+    assert np.array_equal(out[8:16], E[8:16])
+    expect = [1.0, 0.75, 0.25, 0.0]
+    for i in range(4):
+        k = 4 + i
+        assert abs(out[k] - (E[k] + expect[i] * (new[k] - E[k]))) <= 1e-15 * abs(E[k])
+    # the mode touching the frozen face keeps its value exactly (w(0) = 0)
+    assert out[7] == E[7]
+    # periodic wrap: a TRANSITION block at the start whose lower neighbour (the last
+    # block) is FROZEN takes w(i) = (0, 1/4, 3/4, 1) when its upper neighbour is ACTIVE
+    states = np.array([O.STATE_TRANSITION, O.STATE_ACTIVE, O.STATE_FROZEN, O.STATE_FROZEN], dtype=np.uint8)
+    out = O.nls_masked_half(E, states, (B,), H)
+    for i, w in enumerate([0.0, 0.25, 0.75, 1.0]):
+        assert abs(out[i] - (E[i] + w * (new[i] - E[i]))) <= 1e-15 * abs(E[i])
