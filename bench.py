@@ -595,7 +595,7 @@ def run_ours(args, rank, world, local_rank, parity=None):
                 "h2d_bytes_per_step": 4.0 * n / K, "d2h_bytes_per_step": 4.0 * n / K,
                 "note": ("set_field of each window's starting field (steps %s) from pinned host + %d steps + "
                          "get_field to pinned host; mean per window, median of %d" % (starts, K, reps_ada))},
-        "gpu_launches": int(round(prof[1] / prof_reps)),
+        "gpu_launches": int(round(prof[1] / (prof_reps * len(snap_ada)))),   # per K-step window
         "clocks": clocks,
     }
     return line, gpu_par
