@@ -185,10 +185,10 @@ template <typename T> struct Group {
 using namespace spdba;
 
 enum ProfKind { K_FFT_PASS = 0, K_FUSED_NL, K_UPDATE_DENSE, K_UPDATE_LIST, K_ASSESS, K_NLS_STEP, K_NLS_ROW, K_NLS_COL,
-                K_FFT_UPDATE, K_FFT_ZFWD, K_RCD_FFT, K_RCD_REACTION, K_FFT_YFWD, K_COUNT };
+                K_FFT_UPDATE, K_FFT_ZFWD, K_RCD_FFT, K_RCD_REACTION, K_FFT_YFWD, K_PREDICT, K_COUNT };
 static const char* kProfName[K_COUNT] = {"fft_pass", "fft_fused_nl", "update_dense", "update_list", "assess",
                                          "nls_step", "nls_row", "nls_col", "fft_update", "fft_z_forward",
-                                         "rcd_fft", "rcd_reaction", "fft_y_forward_pruned"};
+                                         "rcd_fft", "rcd_reaction", "fft_y_forward_pruned", "predict"};
 
 struct ProfRec {
     int kind;
@@ -669,7 +669,7 @@ template <typename T> static spdba_status group_assess_predicted(spdba_plan* p, 
         r.has_pred = false;
         return SPDBA_OK;
     }
-    ProfScope ps(p, K_ASSESS, 0.0);
+    ProfScope ps(p, K_PREDICT, 0.0);
     if ((s = spdba_predictor_states_internal(p->pred, r.snap_maxsq, r.snap_tau, r.states, 1, r.px, r.pmeasure, st)) !=
         SPDBA_OK)
         return s;
