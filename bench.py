@@ -787,21 +787,39 @@ def run_nls512(args, oracle_fut=None):
 
 def run_ensemble64(args, oracle_fut=None):
     """64 CH runs, sides uniform in {128,192,256,384,512}, means U[-0.2,0.2], c64, 16^2 blocks,
-    1000 steps: one grouped plan with graph replay vs one plan per run."""
+    1000 steps from c0.  Launch forms of the one batched plan: one launch per group and pass
+    phase with the groups on concurrent streams, and one persistent launch per pass phase over
+    every group's tiles (tile tables of 4096 and 2048 elements); the autotuner's choice at step
+    500 is the line's value.  Also one plan per run, for reference."""
     import torch
     from paper_2609_03922_gb300 import spdba
     import workloads as W
     members = W.ensemble_members(64)
     steps = 1000
     c0s = [W.ch_initial_condition((sd, sd), mean=m, seed=seed).astype(np.float32) for sd, m, seed in members]
+    bd = [(sd, sd) for sd, _, _ in members]
     side = torch.cuda.Stream()
+    forms = {}
     with torch.cuda.stream(side):
-        pl = spdba.Plan(None, (16, 16), threshold=1e-6, reassess=10, batch_dims=[(sd, sd) for sd, _, _ in members],
-                        precision=spdba.SPDBA_C64)
+        def setin_for(pl):
+            def setin():
+                for r, x in enumerate(c0s):
+                    pl.set_field(x, run=r)
+            return setin
 
-        def setin():
-            for r, x in enumerate(c0s):
-                pl.set_field(x, run=r)
+        for name, mp in (("per_group_streams", 0), ("multi_4096", 1), ("multi_2048", 2)):
+            pl = spdba.Plan(None, (16, 16), threshold=1e-6, reassess=10, batch_dims=bd, precision=spdba.SPDBA_C64,
+                            multi_pass=mp)
+            assert pl.get_config()["multi_pass"] == mp
+            _timed_steps(pl, 20, setin_for(pl), side)
+            forms[name] = steps / (_timed_steps(pl, steps, setin_for(pl), side) / 1e3)
+            pl.close()
+        pl = spdba.Plan(None, (16, 16), threshold=1e-6, reassess=10, batch_dims=bd, precision=spdba.SPDBA_C64)
+        setin = setin_for(pl)
+        setin()
+        pl.step(TUNE_AT)
+        tune = pl.autotune(2 * REASSESS)
+        chosen = tune["candidates"][tune["chosen"]]
         _timed_steps(pl, 20, setin, side)
         ms_g = _timed_steps(pl, steps, setin, side)
         ratio = float(np.mean([pl.get_stats(run=r)["active_ratio_sum"] / steps for r in range(64)]))
@@ -829,12 +847,15 @@ def run_ensemble64(args, oracle_fut=None):
         for p_ in plans:
             p_.close()
     pts = sum(sd * sd for sd, _, _ in members)
-    extra = {"dtype": "c64", "per_run_plans_steps_per_s": steps / (ms_p / 1e3),
+    extra = {"dtype": "c64", "steps_per_s_by_launch_form": forms, "autotune": tune,
+             "autotune_chosen": chosen, "per_run_plans_steps_per_s": steps / (ms_p / 1e3),
              "grouped_over_per_run": ms_p / ms_g, "mean_nonfrozen_ratio": ratio}
     extra.update(_oracle_leg(oracle_fut, fields, "runs %s (the first of side <= 256), all 1000 steps (FP64 "
                                                  "oracle, own scans)" % pick))
     return _line("ensemble steps/s (64 uneven CH runs, all advance one step)", steps / (ms_g / 1e3), "steps/s", steps,
-                 20, ms_g, {"workload": "ch2d-ensemble-64-runs-128..512-c64-B16", "points": pts}, extra)
+                 20, ms_g, {"workload": "ch2d-ensemble-64-runs-128..512-c64-B16", "points": pts,
+                            "launch_form": "multi_pass=%d, use_graph=%d (autotuned at step %d)"
+                                           % (chosen["multi_pass"], chosen["use_graph"], TUNE_AT)}, extra)
 
 
 def run_ch3d384pred(args, oracle_fut=None):

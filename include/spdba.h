@@ -106,6 +106,17 @@ typedef struct spdba_options {
     int32_t tma_update;     /* 1: the staged CH update of 3-D complex64 plans with 8^3 blocks
                                moves whole blocks as TMA boxes (same values bit for bit);
                                0 (default): per-warp loads.  spdba_plan_autotune may change it. */
+    int32_t multi_pass;     /* batched 2-D complex64 CH plans of several run sizes (2..8 groups of
+                               equal-size runs, sides of 64, 128, 192, 256, 384 or 512 points, the
+                               update fused into the last forward pass):
+                               1 or 2 = each pass phase of a step is ONE persistent launch over
+                               every group's tiles (one queue, group after group, walked by the
+                               launch's CTAs in a fixed stride; tiles of 4096 or 2048 elements
+                               respectively), 0 (default) = one launch
+                               per group and phase, groups on concurrent streams.  All forms give
+                               bit-identical fields and block states (the FP64 mass statistic
+                               differs in rounding).  Ignored (0 in force) where the plan does
+                               not qualify; spdba_plan_autotune may change it. */
 } spdba_options;
 
 /* Per-run statistics, refreshed at each reassessment. */
@@ -220,7 +231,9 @@ typedef struct spdba_kernel_time {
  * with fuse_update = 1), the staged update's block loads by warps or by TMA
  * boxes (3-D complex64 plans with 8^3 blocks), the 3-D transforms on the Hermitian half spectrum or
  * on the full one (when created with half_spectrum = 1 and the shape has half-
- * spectrum kernels), and reassessment segments replayed as a CUDA graph or
+ * spectrum kernels), one launch per pass phase over all groups of a batched
+ * 2-D complex64 plan with tiles of 4096 or 2048 elements (multi_pass, with the
+ * fused update) or one per group, and reassessment segments replayed as a CUDA graph or
  * launched directly (graphs only on a non-legacy stream) -- each from the same
  * state after one warm-up segment, keeps the fastest for later spdba_step
  * calls, and restores the plan's fields, block states, statistics and step
@@ -240,8 +253,31 @@ typedef struct spdba_tune_report {
                                             8^3 blocks) instead of per-warp loads */
     double ms_per_step[SPDBA_TUNE_MAX];
     int32_t chosen;          /* index of the configuration in force afterwards */
+    int32_t multi_pass[SPDBA_TUNE_MAX];  /* the candidate's multi_pass (see spdba_options) */
+    int32_t cached;          /* 1: spdba_plan_autotune_cached applied a stored choice (no
+                                timing; n_candidates = 1, ms_per_step[0] = the stored time) */
 } spdba_tune_report;
 spdba_status spdba_plan_autotune(spdba_plan* plan, int32_t steps, spdba_tune_report* report);
+/*
+ * Tuning cache (process-wide).  Every spdba_plan_autotune call stores its
+ * choice under the plan's signature: precision, model, mode, dimensionality,
+ * block edges, the run extents and run counts of its groups, the options that
+ * enable candidates (fuse_update, half_spectrum) and the plan's stream kind
+ * (graphs need a non-legacy stream).  spdba_plan_autotune_cached applies the
+ * stored choice to a plan of the same signature without timing anything
+ * (report->cached = 1), else it is spdba_plan_autotune.  The state a plan was
+ * tuned in (its share of frozen blocks) is not part of the signature.  Not
+ * for concurrent use from several threads.  spdba_tune_cache_clear empties it.
+ */
+spdba_status spdba_plan_autotune_cached(spdba_plan* plan, int32_t steps, spdba_tune_report* report);
+void spdba_tune_cache_clear(void);
+/*
+ * The options in force (those the plan was created with, with the launch
+ * configuration the autotuner chose): fuse_update, half_spectrum and
+ * tma_update are 1 where some group uses that form, multi_pass is the form in
+ * force (0, 1 or 2), use_graph as set.  Not a synchronizing call.
+ */
+spdba_status spdba_plan_get_config(const spdba_plan* plan, spdba_options* out);
 
 spdba_status spdba_profile_begin(spdba_plan* plan);
 /* As spdba_profile_begin, but records the kernels of one step in `every`

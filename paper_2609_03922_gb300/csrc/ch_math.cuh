@@ -35,7 +35,7 @@ __device__ __forceinline__ cx_t<T> ch_blend(cx_t<T> c, cx_t<T> nw, const T* cons
         if (lo) sg *= taper[ax][l[ax]];
         if (hi) sg *= taper[ax][g.b[ax] - 1 - l[ax]];
     }
-    return mk<cx_t<T>>(c.x + sg * (nw.x - c.x), c.y + sg * (nw.y - c.y));
+    return mk<cx_t<T>>(fma_rn(sg, nw.x - c.x, c.x), fma_rn(sg, nw.y - c.y, c.y));
 }
 
 }  // namespace spdba

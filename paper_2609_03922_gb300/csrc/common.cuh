@@ -16,10 +16,21 @@ template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+// Rounded multiply and fused multiply-add with the rounding pinned: every
+// transform kernel evaluates a product the same way, whatever the compiler
+// would contract in its context, so the launch forms of a pass (one group per
+// launch or many; any tile width) give bit-identical values.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
-    return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return mk<C>(fma_rn(a.x, b.x, -mul_rn(a.y, b.y)), fma_rn(a.x, b.y, mul_rn(a.y, b.x)));
 }
-template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) {
+    return mk<C>(mul_rn(a.x, s), mul_rn(a.y, s));
+}
 // multiply by s*i for s = +-1
 template <int S, typename C> __device__ __forceinline__ C cmul_si(C a) {
     return S > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
@@ -49,7 +60,7 @@ template <int M, int SIGN, typename C> __device__ __forceinline__ C twiddle16(C 
     else {
         constexpr T c = (T)cos16(m);
         constexpr T s = (T)(SIGN * sin16(m));
-        return mk<C>(x.x * c - x.y * s, x.x * s + x.y * c);
+        return mk<C>(fma_rn(x.x, c, -mul_rn(x.y, s)), fma_rn(x.x, s, mul_rn(x.y, c)));
     }
 }
 
@@ -68,9 +79,9 @@ template <int SIGN, typename C> struct Dft<3, SIGN, C> {
         const T h = (T)0.5;
         const T r3 = (T)(SIGN * 0.86602540378443865);   // SIGN * sqrt(3)/2
         C t1 = cadd(v[1], v[2]);
-        C t2 = mk<C>(v[0].x - h * t1.x, v[0].y - h * t1.y);
+        C t2 = mk<C>(fma_rn(-h, t1.x, v[0].x), fma_rn(-h, t1.y, v[0].y));
         C d = csub(v[1], v[2]);
-        C t3 = mk<C>(-r3 * d.y, r3 * d.x);   // i * r3 * (v1 - v2)
+        C t3 = mk<C>(mul_rn(-r3, d.y), mul_rn(r3, d.x));   // i * r3 * (v1 - v2)
         v[0] = cadd(v[0], t1);
         v[1] = cadd(t2, t3);
         v[2] = csub(t2, t3);

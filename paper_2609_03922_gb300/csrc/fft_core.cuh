@@ -536,9 +536,9 @@ template <typename T, int L, class LY, class MID> struct MidOut {
 template <typename T> struct ChNlMid {
     T scale, msum;
     __device__ __forceinline__ cx_t<T> operator()(int, int, cx_t<T> x) {
-        const T c = x.x * scale;
+        const T c = mul_rn(x.x, scale);
         msum += c;
-        return mk<cx_t<T>>(c * c * c - c, (T)0);
+        return mk<cx_t<T>>(fma_rn(mul_rn(c, c), c, -c), (T)0);
     }
 };
 
@@ -882,16 +882,17 @@ __device__ __forceinline__ bool tile_live(const PassParams<T>& a, long long q0) 
     }
 }
 
-// Per-run share of non-frozen blocks for this step (CTA 0, once per launch).
-template <typename T, int NT> __device__ __forceinline__ void ch_update_stats(const CHFuse<T>& f) {
+// Per-run share of non-frozen blocks for this step (CTA 0, once per launch);
+// dense: every block is updated this step.
+template <typename T, int NT> __device__ __forceinline__ void ch_update_stats(const CHFuse<T>& f, int dense) {
     const Geom& g = f.g;
     if (blockIdx.x != 0 || !f.stats) return;
     const double inv = 1.0 / (double)g.bpr();
     const long long bm = g.block_modes();
     for (long long r = threadIdx.x; r < g.runs(); r += NT) {
-        double nf = f.dense ? (double)g.bpr() : (double)(f.stats[r].n_active + f.stats[r].n_transition);
+        double nf = dense ? (double)g.bpr() : (double)(f.stats[r].n_active + f.stats[r].n_transition);
         f.stats[r].ratio_sum += nf * inv;
-        if (!f.dense) {
+        if (!dense) {
             f.stats[r].list_modes += nf * (double)bm;
             f.stats[r].ctl_nf += f.stats[r].n_active + f.stats[r].n_transition;   // control interval
             f.stats[r].ctl_steps += 1;
@@ -1094,9 +1095,9 @@ __device__ __forceinline__ void tile_body(cx_t<T>* sm, const PassParams<T>& a, l
             if constexpr (LY::PMAP) { p = e % P; j = e / P; }
             else { p = e / L; j = e % L; }
             C v = sm[LY::idx(p, j)];
-            T c = v.x * a.nl_scale;
+            T c = mul_rn(v.x, a.nl_scale);
             msum += c;
-            sm[LY::idx(p, j)] = mk<C>(c * c * c - c, (T)0);
+            sm[LY::idx(p, j)] = mk<C>(fma_rn(mul_rn(c, c), c, -c), (T)0);
         }
         if (a.mass != nullptr) {
             double ms = (double)msum;
@@ -1139,10 +1140,87 @@ template <typename T, int L, int MODE, bool PFAST> struct PipeOcc {
                                                                : 3;
 };
 
+// Shared-memory layout of the pipelined kernels' tiles.
+template <int L, int P, bool PFAST>
+using PipeLayout = typename std::conditional<PFAST, LayoutB<L, P>, LayoutA<L, P, true>>::type;
+
+// Start the asynchronous load of the tile at pencil q0 (one cp.async group is
+// committed by the caller).
+template <typename T, int L, int P, int NT, int MODE, bool PFAST>
+__device__ __forceinline__ void pipe_issue(cx_t<T>* sm, const PassParams<T>& a, long long q0) {
+    using LY = PipeLayout<L, P, PFAST>;
+    if constexpr (reads_half(MODE)) issue_tile_half<T, L, P, NT, LY>(sm, a, q0);
+    else issue_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
+}
+
+// Transform the tile at pencil q0, resident in `sm`, and store it (or apply
+// the update).  chat: the tile-sized buffer that receives staged c_hat rows
+// (update passes that stage them); tab: the per-tile state table (update
+// passes); kp: |k|^2 of the pass axis; tw: the length-L twiddle table.  Ends
+// with the tile's results issued; the caller synchronises before reusing
+// shared memory.
+template <typename T, int L, int P, int NT, int SIGN, int MODE, bool PFAST>
+__device__ __forceinline__ void pipe_tile(cx_t<T>* sm, cx_t<T>* chat, const PassParams<T>& a, long long q0,
+                                          uint8_t* tab, const T* kp, const cx_t<T>* tw) {
+    using C = cx_t<T>;
+    using LY = PipeLayout<L, P, PFAST>;
+    // direct stores from the last stage stay coalesced when a warp's lanes
+    // cover at least 32 contiguous bytes of each output row
+    // (the radix-3 tails of 192 and 384 hold too many registers to emit directly)
+    constexpr bool DIRECT = (LY::PMAP || (L / Radices_last<L>::value) * (int)sizeof(C) >= 32) &&
+                            Radices_last<L>::value != 3;
+    if constexpr (MODE == PASS_MIRROR) {
+        MirrorPlainOut<T, L, P> out(a, q0);
+        run_stages_out<T, L, P, NT, SIGN, LY>(sm, tw, out);
+    } else if constexpr (!is_update_mode(MODE) && !DIRECT) {
+        // short pencil-major pencils: the staged store keeps 16-byte coalesced writes
+        tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
+        store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
+    } else if constexpr (MODE == PASS_PLAIN) {
+        if (a.tw4 != nullptr) {
+            // first pass of a four-step transform: twiddle in shared memory
+            tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
+            store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
+        } else {
+            PlainOut<T, L> out(a, q0);
+            run_stages_out<T, L, P, NT, SIGN, LY>(sm, tw, out);
+        }
+    } else if constexpr (MODE == PASS_CH_NL) {
+        // inverse transform, the nonlinearity, forward transform (last stage storing)
+        ChNlMid<T> mid{a.nl_scale, (T)0};
+        PlainOut<T, L> out(a, q0);
+        transform_pair<T, L, P, NT, +1, -1, LY>(sm, tw, mid, out);
+        const T msum = mid.msum;
+        if (a.mass != nullptr) {
+            double ms = warp_sum((double)msum);
+            if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);
+        }
+    } else {
+        const UpdTile u = upd_tile<T, P>(a, (int)q0);
+        if (u.rows) {
+            // the tile spans several rows of a small grid
+            run_stages<T, L, P, NT, -1, LY>(sm, tw);
+            ch_update_tile_rows<T, L, P, NT, LY>(sm, a, q0);
+        } else if constexpr (upd_stages_chat<T, L>()) {
+            // c_hat of the tile's non-frozen rows streams in during the transform
+            ch_update_table<T, L, P, NT>(tab, a, u);
+            __syncthreads();
+            issue_chat<T, L, P, NT, LY>(chat, a, u, tab);
+            UpdOut<T, L, P, NT, Radices_last<L>::value, true, LY, MODE == PASS_UPD_HALF> out(a, u, tab, kp, chat);
+            run_stages_out<T, L, P, NT, -1, LY>(sm, tw, out);
+        } else {
+            ch_update_table<T, L, P, NT>(tab, a, u);
+            run_stages<T, L, P, NT, -1, LY>(sm, tw);
+            UpdOut<T, L, P, NT, 4, false, LY, MODE == PASS_UPD_HALF> out(a, u, tab, kp, nullptr);
+            drain_tile<T, L, P, NT, 4, LY>(sm, out);
+        }
+    }
+}
+
 template <typename T, int L, int P, int NT, int SIGN, int MODE, bool PFAST>
 __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pass_pipe_kernel(PassParams<T> a) {
     using C = cx_t<T>;
-    using LY = typename std::conditional<PFAST, LayoutB<L, P>, LayoutA<L, P, true>>::type;
+    using LY = PipeLayout<L, P, PFAST>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm0 = reinterpret_cast<C*>(smem_raw);
     C* sm1 = sm0 + LY::SIZE;
@@ -1158,81 +1236,21 @@ __global__ void __launch_bounds__(NT, PipeOcc<T, L, MODE, PFAST>::value) fft_pas
     if constexpr (STW)
         for (int j = threadIdx.x; j < L; j += NT) s_tw[j] = a.tw[j];   // visible after the loop's first barrier
     const C* const tw = STW ? s_tw : a.tw;
-    // direct stores from the last stage stay coalesced when a warp's lanes
-    // cover at least 32 contiguous bytes of each output row
-    // (the radix-3 tails of 192 and 384 hold too many registers to emit directly)
-    constexpr bool DIRECT = (LY::PMAP || (L / Radices_last<L>::value) * (int)sizeof(C) >= 32) &&
-                            Radices_last<L>::value != 3;
     const long long ntiles = (a.O * a.I) / P;
-    if constexpr (is_update_mode(MODE)) ch_update_stats<T, NT>(a.fu);
+    if constexpr (is_update_mode(MODE)) ch_update_stats<T, NT>(a.fu, a.fu.dense);
     long long t = blockIdx.x;
     while (t < ntiles && !tile_live<T, P, MODE>(a, t * P)) t += gridDim.x;
-    if (t < ntiles) {
-        if constexpr (reads_half(MODE)) issue_tile_half<T, L, P, NT, LY>(sm0, a, t * P);
-        else issue_tile<T, L, P, NT, PFAST, LY>(sm0, a, t * P);
-    }
+    if (t < ntiles) pipe_issue<T, L, P, NT, MODE, PFAST>(sm0, a, t * P);
     cp_async_commit();
     int buf = 0;
     while (t < ntiles) {
         long long tn = t + gridDim.x;
         while (tn < ntiles && !tile_live<T, P, MODE>(a, tn * P)) tn += gridDim.x;
-        if (tn < ntiles) {
-            if constexpr (reads_half(MODE)) issue_tile_half<T, L, P, NT, LY>(buf ? sm0 : sm1, a, tn * P);
-            else issue_tile<T, L, P, NT, PFAST, LY>(buf ? sm0 : sm1, a, tn * P);
-        }
+        if (tn < ntiles) pipe_issue<T, L, P, NT, MODE, PFAST>(buf ? sm0 : sm1, a, tn * P);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        C* sm = buf ? sm1 : sm0;
-        const long long q0 = t * P;
-        if constexpr (MODE == PASS_MIRROR) {
-            MirrorPlainOut<T, L, P> out(a, q0);
-            run_stages_out<T, L, P, NT, SIGN, LY>(sm, tw, out);
-        } else if constexpr (!is_update_mode(MODE) && !DIRECT) {
-            // short pencil-major pencils: the staged store keeps 16-byte coalesced writes
-            tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
-            store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
-        } else if constexpr (MODE == PASS_PLAIN) {
-            if (a.tw4 != nullptr) {
-                // first pass of a four-step transform: twiddle in shared memory
-                tile_body<T, L, P, NT, SIGN, MODE, LY>(sm, a, q0);
-                store_tile<T, L, P, NT, PFAST, LY>(sm, a, q0);
-            } else {
-                PlainOut<T, L> out(a, q0);
-                run_stages_out<T, L, P, NT, SIGN, LY>(sm, tw, out);
-            }
-        } else if constexpr (MODE == PASS_CH_NL) {
-            // inverse transform, the nonlinearity, forward transform (last stage storing)
-            ChNlMid<T> mid{a.nl_scale, (T)0};
-            PlainOut<T, L> out(a, q0);
-            transform_pair<T, L, P, NT, +1, -1, LY>(sm, tw, mid, out);
-            const T msum = mid.msum;
-            if (a.mass != nullptr) {
-                double ms = warp_sum((double)msum);
-                if ((threadIdx.x & 31) == 0) atomicAdd(a.mass + (q0 / a.mass_ppr) * a.mass_stride, ms);
-            }
-        } else {
-            const UpdTile u = upd_tile<T, P>(a, (int)q0);
-            if (u.rows) {
-                // the tile spans several rows of a small grid
-                run_stages<T, L, P, NT, -1, LY>(sm, tw);
-                ch_update_tile_rows<T, L, P, NT, LY>(sm, a, q0);
-            } else if constexpr (upd_stages_chat<T, L>()) {
-                // c_hat of the tile's non-frozen rows streams in during the transform
-                ch_update_table<T, L, P, NT>(s_tab, a, u);
-                __syncthreads();
-                C* smc = sm0 + 2 * LY::SIZE;
-                issue_chat<T, L, P, NT, LY>(smc, a, u, s_tab);
-                UpdOut<T, L, P, NT, Radices_last<L>::value, true, LY, MODE == PASS_UPD_HALF> out(a, u, s_tab, s_kp,
-                                                                                               smc);
-                run_stages_out<T, L, P, NT, -1, LY>(sm, tw, out);
-            } else {
-                ch_update_table<T, L, P, NT>(s_tab, a, u);
-                run_stages<T, L, P, NT, -1, LY>(sm, tw);
-                UpdOut<T, L, P, NT, 4, false, LY, MODE == PASS_UPD_HALF> out(a, u, s_tab, s_kp, nullptr);
-                drain_tile<T, L, P, NT, 4, LY>(sm, out);
-            }
-        }
+        pipe_tile<T, L, P, NT, SIGN, MODE, PFAST>(buf ? sm1 : sm0, sm0 + 2 * LY::SIZE, a, t * P, s_tab, s_kp, tw);
         __syncthreads();
         buf ^= 1;
         t = tn;

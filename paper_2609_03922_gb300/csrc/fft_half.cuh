@@ -170,9 +170,9 @@ __global__ void __launch_bounds__(NT, 2) fft_herm_inv_kernel(PassParams<T> a) {
 template <typename T> struct ChNlPairMid {
     T scale, msum;
     __device__ __forceinline__ cx_t<T> operator()(int, int, cx_t<T> x) {
-        const T c0 = x.x * scale, c1 = x.y * scale;
+        const T c0 = mul_rn(x.x, scale), c1 = mul_rn(x.y, scale);
         msum += c0 + c1;
-        return mk<cx_t<T>>(c0 * c0 * c0 - c0, c1 * c1 * c1 - c1);
+        return mk<cx_t<T>>(fma_rn(mul_rn(c0, c0), c0, -c0), fma_rn(mul_rn(c1, c1), c1, -c1));
     }
 };
 

@@ -86,6 +86,31 @@ long long pair_tile_count(const Pass<float>& ps);
 // Pencils per tile of the pass kernels of length L (0 if none).
 template <typename T> int pass_tile_pencils(int64_t L);
 
+// ------------------------------------------------------------------ multi-size passes
+// One launch of a pass phase over every group of a batched complex64 plan: the
+// groups' tiles form one queue (group after group) that the persistent CTAs of
+// the launch walk in a fixed stride.
+constexpr int kMultiMaxGroups = 8;
+constexpr int kMultiNT = 256;
+template <typename T> struct MultiGroup {
+    PassParams<T> a;   // the group's pass with its input and output set (fu.dense 0, mass set)
+    int L, P;          // pencil length, pencils per tile
+    unsigned t0, nt;   // first tile in the queue's numbering, tile count
+};
+// Pencils per tile of length L in the multi-size table of `tile` elements per
+// tile (4096 or 2048); 0 if the length has no multi-size kernel.
+int multi_tile_pencils(int tile, int64_t L);
+// Kernel, dynamic shared memory and resident CTAs (occupancy x SMs) of a
+// multi-size pass: pfast = row-major tiles (PASS_PLAIN, PASS_CH_UPDATE), else
+// pencil-major tiles (PASS_CH_NL).  Sets the kernel's shared-memory limit.
+spdba_status multi_kernel(int tile, int sign, int mode, bool pfast, const void** func, int* smem,
+                          long long* resident);
+// One launch over `ng` groups (device array) and `total` queue positions.
+// Bit g of dense_mask: group g updates every block this step; of mass_mask:
+// group g accumulates its runs' mass (the nonlinearity pass).
+spdba_status launch_multi(const void* func, int smem, long long grid, const MultiGroup<float>* groups, int ng,
+                          unsigned total, unsigned dense_mask, unsigned mass_mask, cudaStream_t st);
+
 // Pass along axis `axis` of `batch` contiguous arrays of shape dims (in place).
 template <typename T>
 spdba_status make_axis_pass(Pass<T>* out, int ndim, const int64_t* dims, int64_t batch, int axis, int sign,

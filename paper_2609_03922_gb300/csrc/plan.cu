@@ -205,8 +205,26 @@ struct RcdParams {
     double r, a, alpha, beta;
 };
 
+// One pass phase of the multi-size form: a single launch over every group's tiles.
+struct MultiPhase {
+    const void* func = nullptr;
+    int smem = 0;
+    long long grid = 0;
+    spdba::MultiGroup<float>* groups = nullptr;   // device array, ng entries
+    int ng = 0;
+    unsigned total = 0;                           // tiles of all groups
+};
+// The multi-size form of a batched 2-D complex64 CH plan (one per tile table).
+struct MultiForm {
+    bool ok = false;
+    MultiPhase inv, nl, upd;   // inverse along axis 0; nonlinearity along axis 1; forward + update along axis 0
+};
+
 struct spdba_plan {
     spdba_options opt;
+    MultiForm multi[2];     // tile tables of 4096 and 2048 elements
+    int multi_sel = 0;      // form in force: 0 = per group, 1 / 2 = multi[0] / multi[1]
+    std::vector<void*> multi_bufs;   // device buffers of the multi-size forms
     RcdParams rcd{1.0, 1.0, 1.0, 0.3};
     bool prof = false;
     int prof_every = 1;     // record the kernels of one step in `prof_every`
@@ -1018,6 +1036,120 @@ template <typename T> static spdba_status group_rcd_step(spdba_plan* p, Group<T>
     return SPDBA_OK;
 }
 
+// ------------------------------------------------------------------ multi-size form
+// Builds the multi-size form of a batched 2-D complex64 CH plan for one tile
+// table (mf.ok stays false where some group does not qualify).
+static spdba_status build_multi(spdba_plan* p, int tile, MultiForm& mf) {
+    auto& gs = groups<float>(p);
+    mf.ok = false;
+    if (p->opt.model != SPDBA_MODEL_CH || gs.size() < 2 || gs.size() > (size_t)kMultiMaxGroups) return SPDBA_OK;
+    std::vector<MultiGroup<float>> hv[3];
+    unsigned tot[3] = {0, 0, 0};
+    // the phase's pass of one group: length L along the pass axis, in -> out
+    auto add = [&](int ph, const Pass<float>& ps, int64_t L, const void* in, void* out) {
+        const int P = multi_tile_pencils(tile, L);
+        const long long np = ps.p.O * ps.p.I;
+        if (P == 0 || ps.p.generic || ps.p.I % P != 0 || np / P + tot[ph] >= 0x7fffffffLL) return false;
+        MultiGroup<float> m;
+        m.a = ps.p;
+        m.a.in = reinterpret_cast<const cx_t<float>*>(in);
+        m.a.out = reinterpret_cast<cx_t<float>*>(out);
+        m.L = (int)L;
+        m.P = P;
+        m.t0 = tot[ph];
+        m.nt = (unsigned)(np / P);
+        tot[ph] += m.nt;
+        hv[ph].push_back(m);
+        return true;
+    };
+    for (auto& gp : gs) {
+        Group<float>& r = *gp;
+        if (r.ndim != 2 || r.pre_inv.size() != 1 || r.pre_fwd.size() != 1 || !r.has_fused) return SPDBA_OK;
+        // the update's per-tile state table must fit with this table's tile width
+        const int P0 = multi_tile_pencils(tile, r.dims[0]);
+        if (P0 == 0 || (r.dims[0] / r.g.b[1]) * (int64_t)upd_table_cols(P0, r.g.b[2]) > kUpdTable) return SPDBA_OK;
+        if (!add(0, r.pre_inv[0], r.dims[0], r.c_hat, r.work)) return SPDBA_OK;
+        Pass<float> nl = r.fused;
+        nl.p.mass = &r.stats[0].mass;   // the kernel clears it on steps without a reassessment
+        if (!add(1, nl, r.dims[1], r.work, r.work)) return SPDBA_OK;
+        Pass<float> up = r.upd_pass;
+        up.p.fu.dense = 0;              // set per launch
+        if (!add(2, up, r.dims[0], r.work, r.work)) return SPDBA_OK;
+    }
+    MultiPhase* ph[3] = {&mf.inv, &mf.nl, &mf.upd};
+    const int sign[3] = {+1, -1, -1};
+    const int mode[3] = {PASS_PLAIN, PASS_CH_NL, PASS_CH_UPDATE};
+    const bool pfast[3] = {true, false, true};
+    cudaStream_t st = p->st;
+    for (int k = 0; k < 3; ++k) {
+        MultiPhase& m = *ph[k];
+        long long resident = 0;
+        spdba_status s = multi_kernel(tile, sign[k], mode[k], pfast[k], &m.func, &m.smem, &resident);
+        if (s != SPDBA_OK) return s;
+        void* g = nullptr;
+        cudaError_t e = dev_alloc(&g, sizeof(MultiGroup<float>) * hv[k].size());
+        if (e != cudaSuccess) return cuda_fail(e, "device allocation (multi-size groups)");
+        p->multi_bufs.push_back(g);
+        SPDBA_CUDA(cudaMemcpyAsync(g, hv[k].data(), sizeof(MultiGroup<float>) * hv[k].size(), cudaMemcpyHostToDevice, st));
+        m.groups = reinterpret_cast<MultiGroup<float>*>(g);
+        m.ng = (int)hv[k].size();
+        m.total = tot[k];
+        m.grid = resident < (long long)tot[k] ? resident : (long long)tot[k];
+    }
+    SPDBA_CUDA(cudaStreamSynchronize(st));   // the host arrays are temporaries
+    mf.ok = true;
+    return SPDBA_OK;
+}
+
+// One step of every group in the multi-size form: per group the control
+// check and the reassessment (when due), then three launches over all groups.
+static spdba_status multi_ch_step(spdba_plan* p, const MultiForm& mf) {
+    auto& gs = groups<float>(p);
+    cudaStream_t st = p->st;
+    spdba_status s;
+    const bool adaptive = p->opt.mode == SPDBA_MODE_ADAPTIVE;
+    unsigned dense_mask = 0, mass_mask = 0;
+    double pass_bytes = 0, upd_bytes = 0;
+    prof_select(p, gs[0]->step);
+    for (size_t i = 0; i < gs.size(); ++i) {
+        Group<float>& r = *gs[i];
+        const bool reassess = adaptive && (!r.assessed || r.step % p->reassess == 0);
+        if (control_step(p, r.step) && (s = group_control<float>(p, r)) != SPDBA_OK) return s;
+        if (reassess) {
+            if ((s = group_assess<float>(p, r)) != SPDBA_OK) return s;
+            zero_strided_kernel<<<1, 256, 0, st>>>(&r.stats[0].mass, r.batch, r.fused.p.mass_stride);
+            p->launches += 1;
+            mass_mask |= 1u << i;
+        }
+        if (!adaptive || all_active_step(p, r.step)) dense_mask |= 1u << i;
+        const double b = sizeof(cx_t<float>) * (double)(r.batch * r.n);
+        pass_bytes += 2.0 * b;
+        upd_bytes += 3.0 * b;
+    }
+    {
+        ProfScope pr(p, K_FFT_PASS, pass_bytes);
+        if ((s = launch_multi(mf.inv.func, mf.inv.smem, mf.inv.grid, mf.inv.groups, mf.inv.ng, mf.inv.total, 0u, 0u,
+                              st)) != SPDBA_OK)
+            return s;
+    }
+    {
+        ProfScope pr(p, K_FUSED_NL, pass_bytes);
+        if ((s = launch_multi(mf.nl.func, mf.nl.smem, mf.nl.grid, mf.nl.groups, mf.nl.ng, mf.nl.total, 0u,
+                              mass_mask, st)) != SPDBA_OK)
+            return s;
+    }
+    {
+        // forward transform + update; traffic depends on the states (dense-equivalent bytes)
+        ProfScope pr(p, K_FFT_UPDATE, upd_bytes);
+        if ((s = launch_multi(mf.upd.func, mf.upd.smem, mf.upd.grid, mf.upd.groups, mf.upd.ng, mf.upd.total,
+                              dense_mask, 0u, st)) != SPDBA_OK)
+            return s;
+    }
+    p->launches += 3;
+    for (auto& g : gs) g->step += 1;
+    return SPDBA_OK;
+}
+
 template <typename T> static spdba_status group_steps(spdba_plan* p, Group<T>& g, int64_t n) {
     if (p->opt.model == SPDBA_MODEL_NLS) return group_nls_steps<T>(p, g, n);
     for (int64_t i = 0; i < n; ++i) {
@@ -1044,6 +1176,16 @@ static spdba_status ensure_group_streams(spdba_plan* p, size_t ngroups) {
 
 template <typename T> static spdba_status direct_steps(spdba_plan* p, int64_t n) {
     auto& gs = groups<T>(p);
+    if constexpr (std::is_same<T, float>::value) {
+        if (p->multi_sel > 0 && p->opt.model == SPDBA_MODEL_CH) {
+            const MultiForm& mf = p->multi[p->multi_sel - 1];
+            for (int64_t i = 0; i < n; ++i) {
+                spdba_status s = multi_ch_step(p, mf);
+                if (s != SPDBA_OK) return s;
+            }
+            return SPDBA_OK;
+        }
+    }
     if (gs.size() > 1 && !p->prof) {
         // groups share nothing during steps: each runs its n steps on its own
         // stream, forked from the plan's stream and joined back to it (inside a
@@ -1313,6 +1455,7 @@ static spdba_status check_opts(const spdba_options* o, int ndim) {
     if (o->measure != SPDBA_MEASURE_MAXAMP && o->measure != SPDBA_MEASURE_ENERGY) return fail(SPDBA_ERR_ARG, "bad measure");
     if (o->tau_rule != SPDBA_TAU_REL_MAX && o->tau_rule != SPDBA_TAU_ABS) return fail(SPDBA_ERR_ARG, "bad tau rule");
     if (o->refresh_every < 0 || o->warmup_steps < 0) return fail(SPDBA_ERR_ARG, "negative refresh/warm-up");
+    if (o->multi_pass < 0 || o->multi_pass > 2) return fail(SPDBA_ERR_ARG, "multi_pass must be 0, 1 or 2");
     if (o->model == SPDBA_MODEL_CH && (ndim < 2 || ndim > 3)) return fail(SPDBA_ERR_UNSUPPORTED, "CH plans are 2-D or 3-D");
     if (o->model == SPDBA_MODEL_NLS && ndim != 1) return fail(SPDBA_ERR_UNSUPPORTED, "NLS plans are 1-D");
     return SPDBA_OK;
@@ -1387,6 +1530,13 @@ extern "C" spdba_status spdba_batch_create(spdba_plan** out, int32_t nruns, int3
     p->st = (cudaStream_t)o.stream;
     s = p->precision == SPDBA_C64 ? build_groups<float>(p, nruns, ndim, dims, block)
                                   : build_groups<double>(p, nruns, ndim, dims, block);
+    if (s == SPDBA_OK && p->precision == SPDBA_C64 && ndim == 2) {
+        // multi-size forms (tile tables of 4096 and 2048 elements)
+        for (int k = 0; k < 2 && s == SPDBA_OK; ++k) s = build_multi(p, k == 0 ? 4096 : 2048, p->multi[k]);
+        if (s == SPDBA_OK && o.multi_pass > 0 && o.fuse_update && p->multi[o.multi_pass - 1].ok)
+            p->multi_sel = o.multi_pass;
+    }
+    p->opt.multi_pass = p->multi_sel;
     if (s == SPDBA_OK) {
         cudaError_t e = cudaStreamSynchronize(p->st);
         if (e != cudaSuccess) s = cuda_fail(e, "plan setup");
@@ -1419,6 +1569,7 @@ extern "C" void spdba_plan_destroy(spdba_plan* p) {
     }
     for (cudaEvent_t e : p->gevents) cudaEventDestroy(e);
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    for (void* b : p->multi_bufs) dev_free(b);
     delete p;
 }
 
@@ -1494,17 +1645,50 @@ template <typename T> static spdba_status snap_restore(spdba_plan* p, Group<T>& 
     return SPDBA_OK;
 }
 
-template <typename T> static void apply_config(spdba_plan* p, int fuse, int graph, int half, int tma) {
+template <typename T> static void apply_config(spdba_plan* p, int fuse, int graph, int half, int tma, int multi) {
     for (auto& g : groups<T>(p)) {
         g->fused_update = fuse && g->has_fused;
         g->use_half = half && g->has_half;
         g->use_tma = tma && g->tma_ok;
     }
+    p->multi_sel = (multi > 0 && fuse && p->multi[multi - 1].ok) ? multi : 0;
+    p->opt.multi_pass = p->multi_sel;
     p->opt.use_graph = graph;
     if (p->seg_exec) {
         cudaGraphExecDestroy(p->seg_exec);
         p->seg_exec = nullptr;
     }
+}
+
+// ------------------------------------------------------------------ tuning cache
+struct TunedConfig {
+    int fuse, graph, half, tma, multi;
+    double ms;
+};
+static std::map<std::string, TunedConfig>& tune_cache() {
+    static std::map<std::string, TunedConfig> m;
+    return m;
+}
+// What the candidate set and their timings depend on: precision, model, mode,
+// dimensionality, block edges, each group's run extents and run count, the
+// options that enable candidates and whether graphs are possible.
+static std::string plan_signature(spdba_plan* p) {
+    std::string k;
+    char buf[96];
+    snprintf(buf, sizeof buf, "p%d m%d md%d f%d h%d s%d|", p->precision, p->opt.model, p->opt.mode,
+             p->opt.fuse_update, p->opt.half_spectrum, p->st == 0 ? 0 : 1);
+    k += buf;
+    auto add_groups = [&](auto& gs) {
+        for (auto& g : gs) {
+            snprintf(buf, sizeof buf, "d%d:%lld,%lld,%lld b%d,%d,%d x%lld;", g->ndim, (long long)g->dims[0],
+                     (long long)g->dims[1], (long long)g->dims[2], g->g.b[0], g->g.b[1], g->g.b[2],
+                     (long long)g->batch);
+            k += buf;
+        }
+    };
+    add_groups(p->g32);
+    add_groups(p->g64);
+    return k;
 }
 
 // Times `steps` steps (after a warm-up segment that also captures a graph)
@@ -1518,7 +1702,7 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
         any_half |= g->has_half;
         any_tma |= g->tma_ok;
     }
-    struct Cand { int fuse, graph, half, tma; };
+    struct Cand { int fuse, graph, half, tma, multi; };
     std::vector<Cand> cand;
     for (int hf : {1, 0}) {
         if (hf && !any_half) continue;
@@ -1529,8 +1713,11 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
                 // the staged form's list-driven update: warp kernel or TMA kernel
                 for (int tm : {0, 1}) {
                     if (tm && (f || !any_tma)) continue;
-                    cand.push_back({f, gr, hf, tm});
+                    cand.push_back({f, gr, hf, tm, 0});
                 }
+                // the fused form of a batched 2-D plan: one launch per phase over all groups
+                for (int mu : {1, 2})
+                    if (f && !hf && p->multi[mu - 1].ok) cand.push_back({f, gr, hf, 0, mu});
             }
         }
     }
@@ -1545,7 +1732,7 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
     if (s == SPDBA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         s = fail(SPDBA_ERR_CUDA, "autotune: cudaEventCreate failed");
     for (size_t c = 0; c < cand.size() && s == SPDBA_OK; ++c) {
-        apply_config<T>(p, cand[c].fuse, cand[c].graph, cand[c].half, cand[c].tma);
+        apply_config<T>(p, cand[c].fuse, cand[c].graph, cand[c].half, cand[c].tma, cand[c].multi);
         if ((s = plan_step<T>(p, R)) != SPDBA_OK) break;   // warm-up (graph capture)
         for (size_t i = 0; i < gs.size() && s == SPDBA_OK; ++i) s = snap_restore<T>(p, *gs[i], snaps[i]);
         if (s != SPDBA_OK) break;
@@ -1563,7 +1750,7 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
     for (size_t c = 1; c < cand.size(); ++c)
         if (ms[c] < ms[best]) best = c;
     if (s == SPDBA_OK && !cand.empty())
-        apply_config<T>(p, cand[best].fuse, cand[best].graph, cand[best].half, cand[best].tma);
+        apply_config<T>(p, cand[best].fuse, cand[best].graph, cand[best].half, cand[best].tma, cand[best].multi);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaError_t e = cudaStreamSynchronize(p->st);
@@ -1579,9 +1766,14 @@ template <typename T> static spdba_status autotune_t(spdba_plan* p, int32_t step
             rep->use_graph[c] = cand[c].graph;
             rep->half_spectrum[c] = cand[c].half;
             rep->tma_update[c] = cand[c].tma;
+            rep->multi_pass[c] = cand[c].multi;
             rep->ms_per_step[c] = ms[c];
         }
         rep->chosen = (int32_t)best;
+    }
+    if (!cand.empty()) {
+        const Cand& b = cand[best];
+        tune_cache()[plan_signature(p)] = TunedConfig{b.fuse, b.graph, b.half, b.tma, b.multi, ms[best]};
     }
     return SPDBA_OK;
 }
@@ -1593,6 +1785,53 @@ extern "C" spdba_status spdba_plan_autotune(spdba_plan* p, int32_t steps, spdba_
     if (p->prof) return fail(SPDBA_ERR_STATE, "spdba_plan_autotune: a profile is open");
     spdba_status s = p->precision == SPDBA_C64 ? autotune_t<float>(p, steps, report) : autotune_t<double>(p, steps, report);
     return latch(p, s);
+}
+
+extern "C" spdba_status spdba_plan_autotune_cached(spdba_plan* p, int32_t steps, spdba_tune_report* report) {
+    PLAN_CHECK(p);
+    if (steps < 1) return fail(SPDBA_ERR_ARG, "spdba_plan_autotune_cached: steps must be >= 1");
+    if (p->pred) return fail(SPDBA_ERR_STATE, "spdba_plan_autotune_cached: detach the predictor first");
+    if (p->prof) return fail(SPDBA_ERR_STATE, "spdba_plan_autotune_cached: a profile is open");
+    auto it = tune_cache().find(plan_signature(p));
+    if (it == tune_cache().end()) return spdba_plan_autotune(p, steps, report);
+    const TunedConfig& c = it->second;
+    if (p->precision == SPDBA_C64) apply_config<float>(p, c.fuse, c.graph, c.half, c.tma, c.multi);
+    else apply_config<double>(p, c.fuse, c.graph, c.half, c.tma, c.multi);
+    if (report) {
+        memset(report, 0, sizeof *report);
+        report->n_candidates = 1;
+        report->fuse_update[0] = c.fuse;
+        report->use_graph[0] = c.graph;
+        report->half_spectrum[0] = c.half;
+        report->tma_update[0] = c.tma;
+        report->multi_pass[0] = c.multi;
+        report->ms_per_step[0] = c.ms;
+        report->chosen = 0;
+        report->cached = 1;
+    }
+    return SPDBA_OK;
+}
+
+extern "C" void spdba_tune_cache_clear(void) { tune_cache().clear(); }
+
+extern "C" spdba_status spdba_plan_get_config(const spdba_plan* p, spdba_options* out) {
+    if (!p || !out) return fail(SPDBA_ERR_ARG, "spdba_plan_get_config: bad arguments");
+    *out = p->opt;
+    int fuse = 0, half = 0, tma = 0;
+    auto scan = [&](auto& gs) {
+        for (auto& g : gs) {
+            fuse |= g->fused_update ? 1 : 0;
+            half |= g->use_half ? 1 : 0;
+            tma |= g->use_tma ? 1 : 0;
+        }
+    };
+    scan(p->g32);
+    scan(p->g64);
+    out->fuse_update = fuse;
+    out->half_spectrum = half;
+    out->tma_update = tma;
+    out->multi_pass = p->multi_sel;
+    return SPDBA_OK;
 }
 
 extern "C" spdba_status spdba_get_field(spdba_plan* p, int32_t run, void* dst, int32_t on_dev) {

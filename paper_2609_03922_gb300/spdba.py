@@ -35,7 +35,7 @@ class spdba_options(ctypes.Structure):
                 ("control_every", ctypes.c_int32), ("components", ctypes.c_int32),
                 ("rcd_d_diag", ctypes.c_double), ("rcd_d_cross", ctypes.c_double), ("rcd_alpha", ctypes.c_double),
                 ("rcd_beta", ctypes.c_double), ("rcd_r", ctypes.c_double), ("rcd_a", ctypes.c_double),
-                ("tma_update", ctypes.c_int32)]
+                ("tma_update", ctypes.c_int32), ("multi_pass", ctypes.c_int32)]
 
 
 class spdba_stats(ctypes.Structure):
@@ -53,7 +53,8 @@ class spdba_tune_report(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int32), ("fuse_update", ctypes.c_int32 * TUNE_MAX),
                 ("use_graph", ctypes.c_int32 * TUNE_MAX), ("half_spectrum", ctypes.c_int32 * TUNE_MAX),
                 ("tma_update", ctypes.c_int32 * TUNE_MAX),
-                ("ms_per_step", ctypes.c_double * TUNE_MAX), ("chosen", ctypes.c_int32)]
+                ("ms_per_step", ctypes.c_double * TUNE_MAX), ("chosen", ctypes.c_int32),
+                ("multi_pass", ctypes.c_int32 * TUNE_MAX), ("cached", ctypes.c_int32)]
 
 
 class spdba_kernel_time(ctypes.Structure):
@@ -84,6 +85,9 @@ SIGNATURES = {
     "spdba_get_activity": (_S, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "spdba_plan_attach_predictor": (_S, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
     "spdba_plan_autotune": (_S, [_P, ctypes.c_int32, ctypes.POINTER(spdba_tune_report)]),
+    "spdba_plan_autotune_cached": (_S, [_P, ctypes.c_int32, ctypes.POINTER(spdba_tune_report)]),
+    "spdba_tune_cache_clear": (None, []),
+    "spdba_plan_get_config": (_S, [_P, ctypes.POINTER(spdba_options)]),
     "spdba_profile_begin": (_S, [_P]),
     "spdba_profile_begin_sampled": (_S, [_P, ctypes.c_int32]),
     "spdba_profile_end": (_S, [_P, ctypes.POINTER(spdba_kernel_time), ctypes.c_int32, _I32P,
@@ -268,16 +272,24 @@ class Plan:
         check(lib().spdba_get_mask(self._p, run, out.ctypes.data, out.size))
         return out
 
-    def autotune(self, steps=20):
-        """Pick the fastest launch configuration (spdba_plan_autotune); returns the
-        candidates with their ms per step and the chosen index."""
+    def autotune(self, steps=20, cached=False):
+        """Pick the fastest launch configuration (spdba_plan_autotune, or with
+        cached=True spdba_plan_autotune_cached); returns the candidates with their
+        ms per step, the chosen index and whether a stored choice was applied."""
         rep = spdba_tune_report()
-        check(lib().spdba_plan_autotune(self._p, int(steps), ctypes.byref(rep)))
+        fn = lib().spdba_plan_autotune_cached if cached else lib().spdba_plan_autotune
+        check(fn(self._p, int(steps), ctypes.byref(rep)))
         cands = [{"fuse_update": int(rep.fuse_update[i]), "use_graph": int(rep.use_graph[i]),
                   "half_spectrum": int(rep.half_spectrum[i]), "tma_update": int(rep.tma_update[i]),
-                  "ms_per_step": float(rep.ms_per_step[i])}
+                  "multi_pass": int(rep.multi_pass[i]), "ms_per_step": float(rep.ms_per_step[i])}
                  for i in range(rep.n_candidates)]
-        return {"candidates": cands, "chosen": int(rep.chosen)}
+        return {"candidates": cands, "chosen": int(rep.chosen), "cached": int(rep.cached)}
+
+    def get_config(self):
+        """The options in force (spdba_plan_get_config) as a dict."""
+        o = spdba_options()
+        check(lib().spdba_plan_get_config(self._p, ctypes.byref(o)))
+        return {f: getattr(o, f) for f, _ in spdba_options._fields_ if f != "stream"}
 
     def profile_begin(self, every=1):
         """Record kernel events of every step, or of one step in `every`."""
@@ -339,6 +351,11 @@ class FFTPlan:
             self.close()
         except Exception:
             pass
+
+
+def tune_cache_clear():
+    """Forget every stored autotuner choice (spdba_tune_cache_clear)."""
+    lib().spdba_tune_cache_clear()
 
 
 def block_activity(q, block, maxsq, sumsq, gmax, precision=SPDBA_C64, stream=None):
