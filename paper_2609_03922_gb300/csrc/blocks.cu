@@ -36,13 +36,13 @@ spdba_status make_geom_batched(Geom* g, int ndim, const int64_t* dims, const int
 }
 
 // ------------------------------------------------------------------ activity
-// One warp per block.  The block max of |q|^2 is exact in FP64: FP32 screens
-// (screen_sq, screen_abs below) select the few modes that can hold the max, and
-// only those are evaluated exactly (re*re + im*im in FP64, the oracle's
-// formula), so a mode that is skipped cannot be the max.  Non-negative doubles order like
-// their bit patterns, so the warp max is two 32-bit integer reductions
-// (high word, then low word among the lanes holding the high maximum) and
-// costs no FP64 instruction.  The ENERGY sum is accumulated per lane in FP64.
+// One warp per block.  The block max of |q|^2 is exact in FP64: an FP32 screen
+// selects the few modes that can hold the max, and only those are evaluated
+// exactly (re*re + im*im in FP64, the oracle's formula), so a mode that is
+// skipped cannot be the max.  Non-negative doubles order like their bit
+// patterns, so the warp max is two 32-bit integer reductions (high word, then
+// low word among the lanes holding the high maximum) and costs no FP64
+// instruction.  The ENERGY sum is accumulated per lane in FP64.
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
     unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
     unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
@@ -52,44 +52,23 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
-// Screens of a mode.  p32 = fma(re, re, im * im) is within 2^-22 of |q|^2 when
-// |q|^2 is a normal FP32 number, so below a screen max pm >= 2^-100 a mode
-// under (1 - 2^-20) pm cannot hold the block's largest |q|^2 (any mode whose
-// |q|^2 is below the normal range lies far under pm too).  When pm < 2^-100 the
-// exact s = max(|re|, |im|) decides instead: |q|^2 lies in [s^2, 2 s^2], so a
-// mode below s_max / sqrt(2) (the cut 0.7071067 leaves room for the product's
-// rounding) cannot hold the max, and s_max = 0 means the modes are exactly 0.
+// The screen.  Any partition of a block's modes gives the block's exact max
+// when every part yields its own exact max; a part is one lane's modes.  The
+// lane keeps the running max S of p = fma(re, re, im * im) over its modes and
+// evaluates exactly only the modes with p >= (1 - 2^-20) S, S taken after each
+// chunk of modes has been folded in.  Below the FP32 overflow threshold,
+// |p - |q|^2| <= 2^-23 |q|^2 + 2^-148, so the part's largest |q|^2 has
+// p >= (1 - 2^-20) S whenever S >= 2^-99 (S bounds every p of the part, taken
+// before or after it); below 2^-99 every nonzero mode is evaluated, and
+// exactly-zero modes never need it.  The running max rises in few chunks, so
+// about one mode in a chunk reaches the slow FP64 pipe; the rest costs two
+// FP32 operations and a compare, and nothing crosses lanes until the end.  The
+// field's k = 0 mode is kept out of the screen and taken apart, so that the
+// max over k != 0 is exact as well.
 __device__ __forceinline__ float screen_sq(float2 q) { return fmaf(q.x, q.x, q.y * q.y); }
-__device__ __forceinline__ float screen_abs(float2 q) { return fmaxf(fabsf(q.x), fabsf(q.y)); }
-constexpr float kScreenTiny = 7.8886090522101181e-31f;   // 2^-100
-__device__ __forceinline__ float screen_cut_sq(float pm) {
-    return pm >= kScreenTiny ? pm * (1.0f - 9.5367431640625e-07f) : __int_as_float(0x7f800000);
-}
-__device__ __forceinline__ float screen_cut_abs(float pm, float sm) {
-    return (pm < kScreenTiny && sm > 0.f) ? sm * 0.7071067f : __int_as_float(0x7f800000);
-}
-
-// exact FP64 |q|^2 for the modes of `mask` (a data-dependent loop, so the FP64
-// work is not speculated for every mode)
-template <int K>
-__device__ __forceinline__ void exact_candidates(const float2 (&v)[K], unsigned mask, unsigned dcmask, double& mx,
-                                                 double& mxnd) {
-    while (mask) {
-        int i = __ffs(mask) - 1;
-        mask &= mask - 1;
-        // select v[i] by compares (a dynamic index would move v to local memory)
-        float2 c = v[0];
-#pragma unroll
-        for (int k = 1; k < K; ++k)
-            if (i == k) c = v[k];
-        double e = mode_sq(c);
-        mx = fmax(mx, e);
-        if (!((dcmask >> i) & 1u)) mxnd = fmax(mxnd, e);
-    }
-}
-
-__device__ __forceinline__ float warp_max_nonneg_f(float x) {
-    return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(x)));
+constexpr float kScreen99 = 1.5777218104420236e-30f;   // 2^-99
+__device__ __forceinline__ bool nonzero_mode(float2 v) {
+    return ((__float_as_uint(v.x) | __float_as_uint(v.y)) << 1) != 0u;
 }
 
 template <typename T, bool ENERGY>
@@ -108,62 +87,65 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
     if constexpr (sizeof(cx_t<T>) == 8) {
         // chunks of up to 16 modes per lane, as 8 16-byte loads of mode pairs along
         // the fast axis (B2 is even for every supported block), all issued before
-        // use; FP32 screen; warp max; exact FP64 for the candidates only
+        // use; the per-lane running screen of block_activity_rows_kernel (each
+        // lane's modes are one part of the block), exact FP64 for its candidates
         const int H = B2 >> 1;
         const int npair = B0 * B1 * H;
         constexpr int K2 = 8;
+        float S = 0.f;
+        double Ddc = 0.0;   // |q(k = 0)|^2: pair 0 of the block holding it (lane 0)
+        if (lane == 0 && base == dc) Ddc = mode_sq(q[dc]);
         for (int m0 = 0; m0 < npair; m0 += 32 * K2) {
             float4 w[K2];
-            long long first[K2];
+            bool isdc[K2];
 #pragma unroll
             for (int k = 0; k < K2; ++k) {
                 const int m = m0 + k * 32 + lane;
                 w[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                first[k] = -1;
+                isdc[k] = false;
                 if (m < npair) {
                     const int row = m / H, l2 = (m - row * H) * 2;
                     const int l1 = row % B1, l0 = row / B1;
                     const long long idx = base + ((long long)l0 * g.n[1] + l1) * g.n[2] + l2;
-                    first[k] = idx;
+                    isdc[k] = idx == dc;
                     w[k] = *reinterpret_cast<const float4*>(q + idx);
                 }
             }
             float2 v[2 * K2];
-            unsigned dcmask = 0;
-            float lmax = 0.f, lmaxnd = 0.f, smax = 0.f, smaxnd = 0.f;
-            float p32[2 * K2], s32[2 * K2];
+            float p32[2 * K2];
 #pragma unroll
             for (int k = 0; k < K2; ++k) {
                 v[2 * k] = make_float2(w[k].x, w[k].y);
                 v[2 * k + 1] = make_float2(w[k].z, w[k].w);
-                if (first[k] == dc) dcmask |= 1u << (2 * k);
-                if (first[k] >= 0 && first[k] + 1 == dc) dcmask |= 1u << (2 * k + 1);
+                if (ENERGY) {
+                    sm += mode_sq(v[2 * k]);
+                    sm += mode_sq(v[2 * k + 1]);
+                }
+                if (isdc[k]) v[2 * k] = make_float2(0.f, 0.f);   // k = 0: out of the screen
             }
+            float cm = S;
 #pragma unroll
             for (int k = 0; k < 2 * K2; ++k) {
                 p32[k] = screen_sq(v[k]);
-                s32[k] = screen_abs(v[k]);
-                lmax = fmaxf(lmax, p32[k]);
-                smax = fmaxf(smax, s32[k]);
-                if (!((dcmask >> k) & 1u)) {
-                    lmaxnd = fmaxf(lmaxnd, p32[k]);
-                    smaxnd = fmaxf(smaxnd, s32[k]);
-                }
-                if (ENERGY) sm += mode_sq(v[k]);
+                cm = fmaxf(cm, p32[k]);
             }
-            const float pm = warp_max_nonneg_f(lmax), pmnd = warp_max_nonneg_f(lmaxnd);
-            const float cut = screen_cut_sq(pm), cutnd = screen_cut_sq(pmnd);
-            const float cuts = screen_cut_abs(pm, warp_max_nonneg_f(smax));
-            const float cutsnd = screen_cut_abs(pmnd, warp_max_nonneg_f(smaxnd));
+            S = cm;
+            const float cut = S >= kScreen99 ? S * (1.0f - 9.5367431640625e-07f) : 0.f;
             unsigned mask = 0;
 #pragma unroll
-            for (int k = 0; k < 2 * K2; ++k) {
-                const bool isdc = (dcmask >> k) & 1u;
-                if (p32[k] >= cut || s32[k] >= cuts || (!isdc && (p32[k] >= cutnd || s32[k] >= cutsnd)))
-                    mask |= 1u << k;
+            for (int k = 0; k < 2 * K2; ++k)
+                if (p32[k] >= cut) mask |= 1u << k;
+            while (mask) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1;
+                float2 c = v[0];
+#pragma unroll
+                for (int k = 1; k < 2 * K2; ++k)
+                    if (i == k) c = v[k];
+                if (nonzero_mode(c)) mxnd = fmax(mxnd, mode_sq(c));
             }
-            exact_candidates<2 * K2>(v, mask, dcmask, mx, mxnd);
         }
+        mx = fmax(mxnd, Ddc);
     } else {
         const int nmodes = B0 * B1 * B2;
         for (int m = lane; m < nmodes; m += 32) {
@@ -190,12 +172,9 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
 // complex64 fields whose rows are short (n2 / 2 <= 256 mode pairs): one CTA
 // per row of blocks (b0, b1), reading its B0 * B1 whole rows of n2 modes in
 // order (full-row 16-byte loads, the layout HBM streams best).  A thread keeps
-// one mode pair column 2u, so it stays in one block bx = 2u / B2 throughout,
-// shared with the G = B2 / 2 neighbouring lanes of its row.  Per chunk of 16
-// modes a lane forms the FP32 screens, the G lanes agree (shuffles) on the
-// running screen maxima of their block, and only modes that pass the cuts are
-// evaluated in FP64 -- about one per block and chunk, so the slow FP64 pipe
-// stays idle.  The row groups combine through shared memory at the end.
+// one mode pair column 2u, so it stays in one block bx = 2u / B2 throughout;
+// its modes are one part of the block for the screen above.  The G = B2 / 2
+// lanes of a block and the row groups combine at the end.
 constexpr int ROWACT_NT = 256;
 __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, const float2* __restrict__ q,
                                                                          double* __restrict__ maxsq,
@@ -207,76 +186,66 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
     const int b0 = blockIdx.x / (int)g.nb[1], b1 = blockIdx.x - b0 * (int)g.nb[1];
     const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
     const int G = B2 >> 1;                                 // lanes per block (a power of two <= 32)
-    const int lane = threadIdx.x & 31;
-    const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
     const int rows = B0 * B1;
     const long long bpr = g.bpr();
     const long long blk0 = ((long long)b0 * g.nb[1] + b1) * g.nb[2];   // block id of bx = 0
     const long long run = blk0 / bpr;
     const long long dc = run * g.fmodes();
     const long long rowbase = ((long long)b0 * B0 * g.n[1] + (long long)b1 * B1) * n2 + 2 * u;
-    float pm = 0.f, pmnd = 0.f, psm = 0.f, psmnd = 0.f;   // the block's running screen maxima
-    double mx = 0.0, mxnd = 0.0;
+    float S = 0.f;        // running screen max of this lane's modes (k = 0 left out)
+    double D = 0.0;       // exact max of this lane's k != 0 modes
+    double Ddc = 0.0;     // |q(k = 0)|^2, in the lane that holds it (row 0, pair 0)
+    if (rho == 0 && rowbase == dc) Ddc = mode_sq(q[dc]);
     constexpr int U = 8;
     for (int r0 = rho; rho < rpi && r0 < rows; r0 += U * rpi) {
         float4 w[U];
-        long long idx[U];
+        bool isdc[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const int r = r0 + k * rpi;
-            idx[k] = -1;
             w[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            isdc[k] = false;
             if (r < rows) {
                 const int l0 = r / B1, l1 = r - l0 * B1;
-                idx[k] = rowbase + ((long long)l0 * g.n[1] + l1) * n2;
-                w[k] = *reinterpret_cast<const float4*>(q + idx[k]);
+                const long long idx = rowbase + ((long long)l0 * g.n[1] + l1) * n2;
+                isdc[k] = idx == dc;
+                w[k] = *reinterpret_cast<const float4*>(q + idx);
             }
         }
         float2 v[2 * U];
-        float p32[2 * U], s32[2 * U];
-        unsigned dcmask = 0;
-        float lmax = 0.f, lmaxnd = 0.f, lsmax = 0.f, lsmaxnd = 0.f;
+        float p[2 * U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
-            v[2 * k] = make_float2(w[k].x, w[k].y);
+            // the first mode of a pair may be k = 0: out of the screen (no FP64 here,
+            // so none is evaluated speculatively)
+            v[2 * k] = isdc[k] ? make_float2(0.f, 0.f) : make_float2(w[k].x, w[k].y);
             v[2 * k + 1] = make_float2(w[k].z, w[k].w);
-            if (idx[k] == dc) dcmask |= 1u << (2 * k);
-            if (idx[k] >= 0 && idx[k] + 1 == dc) dcmask |= 1u << (2 * k + 1);
         }
+        float cm = S;
 #pragma unroll
         for (int k = 0; k < 2 * U; ++k) {
-            p32[k] = screen_sq(v[k]);
-            s32[k] = screen_abs(v[k]);
-            lmax = fmaxf(lmax, p32[k]);
-            lsmax = fmaxf(lsmax, s32[k]);
-            if (!((dcmask >> k) & 1u)) {
-                lmaxnd = fmaxf(lmaxnd, p32[k]);
-                lsmaxnd = fmaxf(lsmaxnd, s32[k]);
-            }
+            p[k] = screen_sq(v[k]);
+            cm = fmaxf(cm, p[k]);
         }
-        for (int o = G >> 1; o > 0; o >>= 1) {
-            lmax = fmaxf(lmax, __shfl_xor_sync(gmask, lmax, o));
-            lmaxnd = fmaxf(lmaxnd, __shfl_xor_sync(gmask, lmaxnd, o));
-            lsmax = fmaxf(lsmax, __shfl_xor_sync(gmask, lsmax, o));
-            lsmaxnd = fmaxf(lsmaxnd, __shfl_xor_sync(gmask, lsmaxnd, o));
-        }
-        pm = fmaxf(pm, lmax);
-        pmnd = fmaxf(pmnd, lmaxnd);
-        psm = fmaxf(psm, lsmax);
-        psmnd = fmaxf(psmnd, lsmaxnd);
-        const float cut = screen_cut_sq(pm), cutnd = screen_cut_sq(pmnd);
-        const float cuts = screen_cut_abs(pm, psm), cutsnd = screen_cut_abs(pmnd, psmnd);
+        S = cm;
+        const float cut = S >= kScreen99 ? S * (1.0f - 9.5367431640625e-07f) : 0.f;
         unsigned mask = 0;
 #pragma unroll
-        for (int k = 0; k < 2 * U; ++k) {
-            const bool isdc = (dcmask >> k) & 1u;
-            if (p32[k] >= cut || s32[k] >= cuts || (!isdc && (p32[k] >= cutnd || s32[k] >= cutsnd)))
-                mask |= 1u << k;
+        for (int k = 0; k < 2 * U; ++k)
+            if (p[k] >= cut) mask |= 1u << k;
+        while (mask) {
+            const int i = __ffs(mask) - 1;
+            mask &= mask - 1;
+            // select v[i] by compares (a dynamic index would move v to local memory)
+            float2 c = v[0];
+#pragma unroll
+            for (int k = 1; k < 2 * U; ++k)
+                if (i == k) c = v[k];
+            if (nonzero_mode(c)) D = fmax(D, mode_sq(c));
         }
-        exact_candidates<2 * U>(v, mask, dcmask, mx, mxnd);
     }
     // combine the G lanes of one block (aligned lane groups), then the row groups
-    unsigned long long bm = dbits(mx), bmnd = dbits(mxnd);
+    unsigned long long bm = dbits(fmax(D, Ddc)), bmnd = dbits(D);
     for (int o = G >> 1; o > 0; o >>= 1) {
         const unsigned long long om = __shfl_xor_sync(0xffffffffu, bm, o);
         const unsigned long long omnd = __shfl_xor_sync(0xffffffffu, bmnd, o);

@@ -71,6 +71,66 @@ def test_block_max_only_matches_oracle(shape, block):
     assert g[1] == O.global_max_sq(q64, exclude_dc=True)
 
 
+def _screen_field(shape, block, seed):
+    """A complex64 field whose blocks each hold one hard case for the FP32 screen
+    of the activity scan: exact zeros, one subnormal mode, all modes below the
+    screen floor 2^-99 (in |q|^2), modes straddling it, near-ties within 2^-22
+    of each other, exact ties, a dominant k = 0 mode, huge dynamic range, and
+    plain random blocks."""
+    r = np.random.default_rng(seed)
+    nb = tuple(s // b for s, b in zip(shape, block))
+    bm = int(np.prod(block))
+    q = np.zeros(shape, dtype=np.complex64)
+    view = q.reshape(nb[0], block[0], nb[1], block[1], nb[2], block[2])
+    for b0 in range(nb[0]):
+        for b1 in range(nb[1]):
+            for b2 in range(nb[2]):
+                kind = r.integers(0, 9)
+                v = np.zeros(bm, dtype=np.complex64)
+                if kind == 1:
+                    v[r.integers(0, bm)] = np.float32(1e-40) * (1 + 1j)
+                elif kind == 2:
+                    v = ((r.standard_normal(bm) + 1j * r.standard_normal(bm)) * 1e-20).astype(np.complex64)
+                elif kind == 3:
+                    v = ((r.standard_normal(bm) + 1j * r.standard_normal(bm)) * 2.0 ** -50).astype(np.complex64)
+                elif kind == 4:
+                    ang = r.random(bm) * 2 * np.pi
+                    mag = 1.0 + r.integers(-4, 5, size=bm) * 2.0 ** -24
+                    v = (mag * np.exp(1j * ang)).astype(np.complex64)
+                elif kind == 5:
+                    v = (r.integers(-3, 4, size=bm) + 1j * r.integers(-3, 4, size=bm)).astype(np.complex64)
+                elif kind == 6:
+                    v = ((r.standard_normal(bm) + 1j * r.standard_normal(bm)) * 10.0 ** r.uniform(-30, 15, bm)
+                         ).astype(np.complex64)
+                elif kind >= 7:
+                    v = (r.standard_normal(bm) + 1j * r.standard_normal(bm)).astype(np.complex64)
+                view[b0, :, b1, :, b2, :] = v.reshape(block)
+    q[(0,) * len(shape)] = np.complex64(3e9 + 1e9j)   # dominant k = 0
+    return q
+
+
+@pytest.mark.parametrize("shape,block", [((256, 256, 64), (8, 8, 8)), ((64, 64, 64), (8, 8, 8)),
+                                         ((128, 256, 32), (4, 4, 8))])
+def test_block_max_screen_hard_cases(shape, block):
+    """Both scan kernels (rows of blocks, warp per block) on blocks built to
+    defeat an FP32 screen: the FP64 maxima stay bit-exact, and the maximum over
+    k != 0 ignores the dominant k = 0 mode."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    q = _screen_field(shape, block, 11)
+    nb = tuple(s // b for s, b in zip(shape, block))
+    maxsq = torch.empty(nb, dtype=torch.float64, device="cuda")
+    gmax = torch.zeros(2, dtype=torch.float64, device="cuda")
+    spdba.block_activity(torch.from_numpy(q).cuda(), block, maxsq, None, gmax, precision=0)
+    torch.cuda.synchronize()
+    q64 = q.astype(np.complex128)
+    mx, _ = O.block_measures(q64, block)
+    assert np.array_equal(maxsq.cpu().numpy(), mx)
+    g = gmax.cpu().numpy()
+    assert g[0] == O.global_max_sq(q64, exclude_dc=False)
+    assert g[1] == O.global_max_sq(q64, exclude_dc=True)
+
+
 def _expected_chi(states):
     d = states.ndim
     chi = np.zeros(states.shape, dtype=np.uint8)
