@@ -117,6 +117,11 @@ typedef struct spdba_options {
                                bit-identical fields and block states (the FP64 mass statistic
                                differs in rounding).  Ignored (0 in force) where the plan does
                                not qualify; spdba_plan_autotune may change it. */
+    int32_t tma_passes;     /* 1 (default): the z inverse of the half-spectrum form (3-D complex64)
+                               loads its direct and mirror tiles as TMA tensor boxes where its x rows
+                               are a whole number of tiles; 0: per-thread cp.async copies.  Same
+                               values bit for bit.  A bounded wait that runs out makes
+                               spdba_get_stats return SPDBA_ERR_TIMEOUT. */
 } spdba_options;
 
 /* Per-run statistics, refreshed at each reassessment. */
@@ -273,9 +278,9 @@ spdba_status spdba_plan_autotune_cached(spdba_plan* plan, int32_t steps, spdba_t
 void spdba_tune_cache_clear(void);
 /*
  * The options in force (those the plan was created with, with the launch
- * configuration the autotuner chose): fuse_update, half_spectrum and
- * tma_update are 1 where some group uses that form, multi_pass is the form in
- * force (0, 1 or 2), use_graph as set.  Not a synchronizing call.
+ * configuration the autotuner chose): fuse_update, half_spectrum, tma_update
+ * and tma_passes are 1 where some group uses that form, multi_pass is the form
+ * in force (0, 1 or 2), use_graph as set.  Not a synchronizing call.
  */
 spdba_status spdba_plan_get_config(const spdba_plan* plan, spdba_options* out);
 

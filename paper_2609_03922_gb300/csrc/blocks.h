@@ -51,6 +51,12 @@ template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdat
 // once at plan creation; launch shape from tma_update_prepare.
 bool tma_update_fits(const Geom& g);
 spdba_status make_box_map(void* map_out, const void* base, const Geom& g);
+// Tensor map (128 bytes at map_out, 64-byte aligned) over a 3-D array of 8-byte
+// elements: dims = {x, y, z} extents (x fastest), row and plane strides in
+// bytes, box = {x, y, z} extents of one copy (each <= 256; box x * 8 bytes a
+// multiple of 16).  SPDBA_ERR_UNSUPPORTED where the driver has no encoder.
+spdba_status tma_encode_3d(void* map_out, const void* base, const uint64_t dims[3], const uint64_t row_bytes,
+                           const uint64_t plane_bytes, const uint32_t box[3]);
 spdba_status tma_update_prepare(int* per_sm, int* nsm);
 spdba_status launch_ch_update_tma(const void* map_c, const void* map_g, const Geom& g, const CHUpdateArgs<float>& a,
                                   long long grid, cudaStream_t st);

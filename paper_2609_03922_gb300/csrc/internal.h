@@ -86,6 +86,27 @@ long long pair_tile_count(const Pass<float>& ps);
 // Pencils per tile of the pass kernels of length L (0 if none).
 template <typename T> int pass_tile_pencils(int64_t L);
 
+// ------------------------------------------------------------------ TMA z inverse
+// The Hermitian z inverse of the half-spectrum form with its tiles moved as
+// tensor boxes (fft_herm_tma.cu): three tensor maps over c_hat (direct tile,
+// mirror tile, the kx = 0 columns), the kernel, its shared memory and grid.
+constexpr int kHermTmaNT = 256;
+struct HermTma {
+    alignas(64) unsigned char map[3][128];
+    const void* func = nullptr;
+    size_t smem = 0;
+    long long grid = 0;
+    bool ok = false;
+};
+// Fills ht for the z inverse pass zinv over c_hat; SPDBA_ERR_UNSUPPORTED (ht.ok
+// false) where the shape has no TMA form (x rows not a whole number of tiles,
+// lengths without a kernel, no tensor-map encoder).
+spdba_status herm_tma_prepare(HermTma* ht, const Pass<float>& zinv, const void* c_hat);
+// Same results as launch_pass(zinv, in, out) bit for bit; `in` must be the
+// c_hat the maps were made for.  A wait that runs out adds 1 at *timeouts.
+spdba_status launch_herm_inv_tma(const HermTma& ht, const Pass<float>& zinv, const void* in, void* out,
+                                 unsigned long long* timeouts, cudaStream_t st);
+
 // ------------------------------------------------------------------ multi-size passes
 // One launch of a pass phase over every group of a batched complex64 plan: the
 // groups' tiles form one queue (group after group) that the persistent CTAs of

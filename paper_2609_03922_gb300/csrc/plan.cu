@@ -128,6 +128,8 @@ template <typename T> struct Group {
     uint8_t* col_live = nullptr;    // live x-frequency columns of the half array (the y forward skips the rest)
     int* pair_count = nullptr;
     long long pair_list_n = 0;      // capacity of pair_list
+    HermTma herm_tma;               // the half form's z inverse with TMA tile copies (complex64)
+    bool use_herm_tma = false;
     bool fused_update = false;      // the last forward pass carries the update (upd_pass)
     bool has_fused = false;         // upd_pass exists (else only the staged form)
     Pass<T> upd_pass;               // forward pass of the first axis with the update fused
@@ -429,6 +431,12 @@ static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* di
     SPDBA_CUDA(cudaMemsetAsync(r.half, 0, sizeof(cx_t<float>) * (size_t)r.half_n, st));
     hnl.p.mass_stride = (int)(sizeof(DevStats) / sizeof(double));
     r.h_inv_z = hz;
+    if (p->opt.tma_passes) {
+        // where the x rows are whole tiles the z inverse moves its tiles as tensor boxes
+        s = herm_tma_prepare(&r.herm_tma, hz, r.c_hat);
+        if (s == SPDBA_OK) r.use_herm_tma = true;
+        else if (s != SPDBA_ERR_UNSUPPORTED) return s;
+    }
     r.h_inv_y = hy_inv;
     r.h_nl = hnl;
     r.h_fwd_y = hy_fwd;
@@ -763,7 +771,15 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
         const double half_b = full_b * (double)(r.g.n[2] / 2 + 1) / (double)r.g.n[2];
         {
             ProfScope pr(p, K_FFT_PASS, full_b + half_b);
-            if ((s = launch_pass<T>(r.h_inv_z, r.c_hat, r.half, st)) != SPDBA_OK) return s;
+            bool tma = false;
+            if constexpr (std::is_same<T, float>::value) {
+                if (r.use_herm_tma) {
+                    tma = true;
+                    s = launch_herm_inv_tma(r.herm_tma, r.h_inv_z, r.c_hat, r.half, &r.stats[0].timeouts, st);
+                }
+            }
+            if (!tma) s = launch_pass<T>(r.h_inv_z, r.c_hat, r.half, st);
+            if (s != SPDBA_OK) return s;
         }
         {
             ProfScope pr(p, K_FFT_PASS, 2.0 * half_b);
@@ -1415,6 +1431,7 @@ extern "C" void spdba_options_default(spdba_options* o) {
     o->use_graph = 1;
     o->fuse_update = 1;
     o->half_spectrum = 1;
+    o->tma_passes = 1;
     o->dt = 0.01;
     o->kappa = 1.0;
     o->dx = 1.0;
@@ -1817,12 +1834,13 @@ extern "C" void spdba_tune_cache_clear(void) { tune_cache().clear(); }
 extern "C" spdba_status spdba_plan_get_config(const spdba_plan* p, spdba_options* out) {
     if (!p || !out) return fail(SPDBA_ERR_ARG, "spdba_plan_get_config: bad arguments");
     *out = p->opt;
-    int fuse = 0, half = 0, tma = 0;
+    int fuse = 0, half = 0, tma = 0, tmap = 0;
     auto scan = [&](auto& gs) {
         for (auto& g : gs) {
             fuse |= g->fused_update ? 1 : 0;
             half |= g->use_half ? 1 : 0;
             tma |= g->use_tma ? 1 : 0;
+            tmap |= g->use_half && g->use_herm_tma ? 1 : 0;
         }
     };
     scan(p->g32);
@@ -1830,6 +1848,7 @@ extern "C" spdba_status spdba_plan_get_config(const spdba_plan* p, spdba_options
     out->fuse_update = fuse;
     out->half_spectrum = half;
     out->tma_update = tma;
+    out->tma_passes = tmap;
     out->multi_pass = p->multi_sel;
     return SPDBA_OK;
 }

@@ -14,10 +14,9 @@
 // latency-bound; with the boxes in flight per SM the copy engine keeps enough
 // bytes outstanding to cover HBM latency.  Every wait is bounded: on timeout
 // the kernel records it in the run statistics and returns.
-#include <cuda.h>
-
 #include "blocks.h"
 #include "ch_math.cuh"
+#include "tma.cuh"
 
 namespace spdba {
 
@@ -32,46 +31,6 @@ struct TmaStage {
     float2 c[TMA_BOX_MODES];
     float2 g[TMA_BOX_MODES];
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// true once the barrier's phase with the given parity has completed
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok = 0;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tma_store_box(const CUtensorMap* map, int x, int y, int z, const void* src) {
-    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
-                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_but_newest() {
-    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_constant__ CUtensorMap map_c,
                                                              const __grid_constant__ CUtensorMap map_g, Geom g,
@@ -112,7 +71,7 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
     // this thread's modes of a box: m = threadIdx.x + TMA_NT * i share l1 and l2
     constexpr int PER = TMA_BOX_MODES / TMA_NT;   // 4
     const int l2 = threadIdx.x & 7, l1 = (threadIdx.x >> 3) & 7, l0base = threadIdx.x >> 6;
-    long long it = 0;
+    long long it = 0, it_abort = -1;
     for (long long w = blockIdx.x; w < cnt; w += gridDim.x, ++it) {
         const int s = (int)(it % TMA_STAGES);
         const unsigned parity = (unsigned)((it / TMA_STAGES) & 1);
@@ -141,7 +100,10 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
             }
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            it_abort = it;
+            break;
+        }
         const float2* c = stage[s].c;
         const float2* gg = stage[s].g;
 #pragma unroll
@@ -167,7 +129,16 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
     }
     if (threadIdx.x == 0) {
         bulk_wait_all();
-        if (s_abort && a.stats) atomicAdd(&a.stats[0].timeouts, 1ull);
+        if (it_abort >= 0) {
+            // let the loads still in flight land (bounded) before the CTA leaves:
+            // iterations it_abort .. it_abort + TMA_STAGES - 1 had theirs issued
+            for (int k = 0; k < TMA_STAGES; ++k) {
+                const long long it2 = it_abort + k;
+                if (blockIdx.x + it2 * gridDim.x < cnt)
+                    mbar_wait_bounded(&full[it2 % TMA_STAGES], (unsigned)((it2 / TMA_STAGES) & 1), spin_limit);
+            }
+            if (a.stats) atomicAdd(&a.stats[0].timeouts, 1ull);
+        }
     }
 }
 
@@ -176,7 +147,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-spdba_status make_box_map(void* map_out, const void* base, const Geom& g) {
+spdba_status tma_encode_3d(void* map_out, const void* base, const uint64_t dims[3], const uint64_t row_bytes,
+                           const uint64_t plane_bytes, const uint32_t box[3]) {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -187,16 +159,24 @@ spdba_status make_box_map(void* map_out, const void* base, const Geom& g) {
         encode = (EncodeTiledFn)fn;
     }
     if (((uintptr_t)base & 15) != 0) return fail(SPDBA_ERR_ARG, "TMA base address not 16-byte aligned");
-    const cuuint64_t dims[3] = {(cuuint64_t)g.n[2], (cuuint64_t)g.n[1], (cuuint64_t)g.n[0]};
-    const cuuint64_t strides[2] = {(cuuint64_t)(g.n[2] * 8), (cuuint64_t)(g.n[2] * g.n[1] * 8)};
-    const cuuint32_t box[3] = {TMA_BOX, TMA_BOX, TMA_BOX};
+    // 8-byte elements (one complex64 each); the innermost box row must be a multiple of 16 bytes
+    if ((box[0] * 8) % 16 != 0) return fail(SPDBA_ERR_ARG, "TMA box row not a multiple of 16 bytes");
+    const cuuint64_t d[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)plane_bytes};
+    const cuuint32_t b[3] = {box[0], box[1], box[2]};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
-                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        const_cast<void*>(base), d, strides, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SPDBA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return SPDBA_OK;
+}
+
+spdba_status make_box_map(void* map_out, const void* base, const Geom& g) {
+    const uint64_t dims[3] = {(uint64_t)g.n[2], (uint64_t)g.n[1], (uint64_t)g.n[0]};
+    const uint32_t box[3] = {TMA_BOX, TMA_BOX, TMA_BOX};
+    return tma_encode_3d(map_out, base, dims, (uint64_t)g.n[2] * 8, (uint64_t)(g.n[2] * g.n[1]) * 8, box);
 }
 
 bool tma_update_fits(const Geom& g) {

@@ -35,7 +35,8 @@ class spdba_options(ctypes.Structure):
                 ("control_every", ctypes.c_int32), ("components", ctypes.c_int32),
                 ("rcd_d_diag", ctypes.c_double), ("rcd_d_cross", ctypes.c_double), ("rcd_alpha", ctypes.c_double),
                 ("rcd_beta", ctypes.c_double), ("rcd_r", ctypes.c_double), ("rcd_a", ctypes.c_double),
-                ("tma_update", ctypes.c_int32), ("multi_pass", ctypes.c_int32)]
+                ("tma_update", ctypes.c_int32), ("multi_pass", ctypes.c_int32),
+                ("tma_passes", ctypes.c_int32)]
 
 
 class spdba_stats(ctypes.Structure):

@@ -137,3 +137,31 @@ def test_half_shapes_match_full_transforms(dims):
     assert any(np.any(m == 0) for m in mh.values())
     assert O.rel_l2(fh, ff) <= 2e-6
     assert O.rel_l2(sph, spf) <= 2e-6
+
+
+TMA_SHAPES = SHAPES + [(512, 128, 128), (256, 256, 256)]
+
+
+@pytest.mark.parametrize("dims", TMA_SHAPES)
+def test_tma_z_inverse_equals_cp_async_z_inverse(dims):
+    """The half form's z inverse with its direct and mirror tiles moved as TMA
+    boxes (where the x rows are whole tiles) gives the cp.async kernel's
+    values bit for bit, over steps with frozen, transition and active blocks."""
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 126)
+    from paper_2609_03922_gb300 import spdba
+    out, used = [], []
+    for tma in (1, 0):
+        plan = spdba.Plan(dims, (8, 8, 8), threshold=0.1, reassess=2, precision=0, half_spectrum=1, fuse_update=0,
+                          tma_passes=tma)
+        used.append(plan.get_config()["tma_passes"])
+        plan.set_field(np.ascontiguousarray(c0.astype(np.float32)))
+        plan.step(7)
+        out.append((plan.get_spectrum(), plan.get_mask(), plan.get_stats()))
+        plan.close()
+    assert used[1] == 0
+    # x rows of whole tiles: every shape here but the two whose rows (48 and 80
+    # entries) are not multiples of the z tile (64 and 32 pencils)
+    assert used[0] == (0 if dims in [(64, 256, 64), (128, 256, 128)] else 1)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2]["n_active"] == out[1][2]["n_active"]
