@@ -394,12 +394,18 @@ __global__ void active_kernel(Geom g, const double* __restrict__ msq, int msq_is
     active[b] = a ? 1 : 0;
 }
 
+// The face neighbours' flags are ORed without short-circuit, so that their
+// loads are independent and in flight together (a chain of dependent loads per
+// neighbour made the state kernel latency-bound).
 __device__ __forceinline__ bool has_active_nbr(const Geom& g, const uint8_t* active, const BCoord& c) {
     const int a0 = 3 - g.ndim;
-    for (int ax = a0; ax < 3; ++ax) {
-        if (active[bindex(g, bnbr(g, c, ax, -1))] || active[bindex(g, bnbr(g, c, ax, +1))]) return true;
+    unsigned any = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax < a0) continue;
+        any |= active[bindex(g, bnbr(g, c, ax, -1))] | active[bindex(g, bnbr(g, c, ax, +1))];
     }
-    return false;
+    return any != 0;
 }
 
 // TRANSITION iff not active and a face neighbour (periodic) is active; chi bit
@@ -418,13 +424,20 @@ __global__ void __launch_bounds__(CLS_NT) state_kernel(Geom g, const uint8_t* __
     uint8_t cb = 0;
     if (b < nb) {
         const BCoord c = bcoord(g, (int)b);
+        const bool nbr_active = transitions && has_active_nbr(g, active, c);
         if (active[b]) st = SPDBA_ACTIVE;
-        else if (transitions && has_active_nbr(g, active, c)) st = SPDBA_TRANSITION;
+        else if (nbr_active) st = SPDBA_TRANSITION;
         const int a0 = 3 - g.ndim;
-        for (int ax = a0; ax < 3; ++ax) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            if (ax < a0) continue;
+#pragma unroll
             for (int d = 0; d < 2; ++d) {
                 const BCoord cn = bnbr(g, c, ax, d == 0 ? -1 : +1);
-                bool frozen = !active[bindex(g, cn)] && !(transitions && has_active_nbr(g, active, cn));
+                // both loads issued unconditionally (transitions is uniform)
+                const unsigned act_n = active[bindex(g, cn)];
+                const bool nbr_n = transitions && has_active_nbr(g, active, cn);
+                const bool frozen = act_n == 0 && !nbr_n;
                 if (frozen) cb |= (uint8_t)(1u << (2 * (ax - a0) + d));
             }
         }

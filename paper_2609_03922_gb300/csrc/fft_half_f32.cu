@@ -127,9 +127,11 @@ __global__ void __launch_bounds__(1024) half_col_live_kernel(const uint8_t* __re
     __shared__ uint8_t s_col[64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int bx = warp; bx < nb2; bx += 32) {
-        bool live = false;
-        for (int r = lane; r < nrows && !live; r += 32) live = states[(long long)r * nb2 + bx] != 0;
-        const unsigned any = __ballot_sync(0xffffffffu, live);
+        // no early exit: the loads are independent, so several stay in flight
+        unsigned live = 0;
+#pragma unroll 8
+        for (int r = lane; r < nrows; r += 32) live |= states[(long long)r * nb2 + bx];
+        const unsigned any = __ballot_sync(0xffffffffu, live != 0);
         if (lane == 0) s_col[bx] = any != 0;
     }
     __syncthreads();
