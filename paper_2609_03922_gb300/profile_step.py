@@ -34,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--fuse", type=int, default=0, help="1: update fused into the last forward pass")
     ap.add_argument("--half", type=int, default=1, help="1: Hermitian half-spectrum transforms")
     ap.add_argument("--tma", type=int, default=0, help="1: staged update moved by TMA boxes")
+    ap.add_argument("--tma-passes", type=int, default=1, help="0: the z inverse copies its tiles by cp.async")
     ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
     ap.add_argument("--mean", type=float, default=0.1)
     ap.add_argument("--warm", type=int, default=500)
@@ -61,7 +62,8 @@ def main(argv=None):
         c0 = W.ch_initial_condition(dims, mean=args.mean, seed=W.BASE_SEED).astype(rdt)
     with spdba.Plan(dims, tuple(args.block), threshold=args.threshold, reassess=args.reassess, precision=prec,
                     mode=spdba.SPDBA_MODE_ADAPTIVE if args.mode == "adaptive" else spdba.SPDBA_MODE_REGULAR,
-                    fuse_update=args.fuse, half_spectrum=args.half, use_graph=0, tma_update=args.tma, **kw) as plan:
+                    fuse_update=args.fuse, half_spectrum=args.half, use_graph=0, tma_update=args.tma,
+                    tma_passes=args.tma_passes, **kw) as plan:
         plan.set_field(c0)
         plan.step(args.warm)
         plan.step(args.steps)
