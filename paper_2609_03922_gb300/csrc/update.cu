@@ -6,6 +6,8 @@
 // c_hat + sigma(k) (new - c_hat) (S1.1, Eq. S.1), FROZEN modes are never read.
 #include <math.h>
 
+#include <type_traits>
+
 #include "blocks.h"
 #include "ch_math.cuh"
 
@@ -115,6 +117,56 @@ __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
     }
 }
 
+// sp-DBA, complex64, 8^3 blocks of a single 3-D field: the warp-per-block
+// update with the block shape fixed at compile time.  Lane l keeps the mode
+// pair (x = 2 (l % 4), y = l / 4) of every z plane of the block, so its x and y
+// wavenumbers and transition coordinates are fixed, the eight planes are eight
+// independent row loads of ĉ and ĝ at a fixed stride, and no index is divided
+// at run time.  The same arithmetic as ch_list_kernel, bit for bit.
+__global__ void __launch_bounds__(256) ch_list8_kernel(Geom g, CHUpdateArgs<float> a) {
+    constexpr int B = 8;
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int cnt = *a.count;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
+        const unsigned long long nfi = a.stats[0].n_active + a.stats[0].n_transition;
+        const double nf = (double)nfi;
+        a.stats[0].ratio_sum += nf * (1.0 / (double)g.bpr());
+        a.stats[0].list_modes += nf * (double)(B * B * B);
+        a.stats[0].ctl_nf += nfi;       // an adaptive step of the control interval
+        a.stats[0].ctl_steps += 1;
+    }
+    const int l2 = (lane & 3) * 2, l1 = lane >> 2;
+    const int nb2 = (int)g.nb[2], nb1 = (int)g.nb[1];
+    const long long n2 = g.n[2], plane = g.n[1] * g.n[2];
+    for (long long w = warp0; w < cnt; w += nwarps) {
+        const int blk = a.list[w];
+        const int st = a.states[blk];
+        const unsigned ch = a.chi[blk];
+        const int q = blk / nb2;
+        const int b2 = blk - q * nb2, b0 = q / nb1, b1 = q - b0 * nb1;
+        const int x = b2 * B + l2, y = b1 * B + l1, z0 = b0 * B;
+        const float ky = a.k2ax[1][y], kx0 = a.k2ax[2][x], kx1 = a.k2ax[2][x + 1];
+        float2* cp = a.c_hat + (long long)z0 * plane + (long long)y * n2 + x;
+        const float2* gp = a.g_hat + (long long)z0 * plane + (long long)y * n2 + x;
+#pragma unroll
+        for (int l0 = 0; l0 < B; ++l0) {
+            const float4 cv = *reinterpret_cast<const float4*>(cp + l0 * plane);
+            const float4 gv = *reinterpret_cast<const float4*>(gp + l0 * plane);
+            const float kzy = a.k2ax[0][z0 + l0] + ky;
+            const float2 c0 = make_float2(cv.x, cv.y), c1 = make_float2(cv.z, cv.w);
+            float2 n0 = ch_new(c0, make_float2(gv.x, gv.y), kzy + kx0, a.dt, a.dtkappa);
+            float2 n1 = ch_new(c1, make_float2(gv.z, gv.w), kzy + kx1, a.dt, a.dtkappa);
+            if (st == SPDBA_TRANSITION) {
+                n0 = ch_blend<float>(c0, n0, a.taper, g, ch, l0, l1, l2);
+                n1 = ch_blend<float>(c1, n1, a.taper, g, ch, l0, l1, l2 + 1);
+            }
+            *reinterpret_cast<float4*>(cp + l0 * plane) = make_float4(n0.x, n0.y, n1.x, n1.y);
+        }
+    }
+}
+
 template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdateArgs<T>& a, int dense, cudaStream_t st) {
     if (dense) {
         long long npairs = g.modes() / 2;
@@ -125,7 +177,13 @@ template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdat
         long long nb = g.blocks();
         long long grid = (nb * 32 + 255) / 256;
         if (grid > 152 * 16) grid = 152 * 16;
-        ch_list_kernel<T><<<(unsigned)grid, 256, 0, st>>>(g, a);
+        bool fixed8 = false;
+        if constexpr (std::is_same<T, float>::value) {
+            fixed8 = g.ndim == 3 && g.runs() == 1 && g.b[0] == 8 && g.b[1] == 8 && g.b[2] == 8 &&
+                     g.blocks() < 0x7fffffffLL;
+            if (fixed8) ch_list8_kernel<<<(unsigned)grid, 256, 0, st>>>(g, a);
+        }
+        if (!fixed8) ch_list_kernel<T><<<(unsigned)grid, 256, 0, st>>>(g, a);
     }
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;
