@@ -418,6 +418,11 @@ template <typename T, int L, int P, int R> struct PairPlainOut {
     const uint8_t* tabm;
     int nbxd, nbxm, bxsd, bxsm;
     FastDiv fd_bp;
+    // z block rows of the outputs without a division per output: with NS a
+    // multiple of the z block edge bz, output m = j + r NS lies in row
+    // j / bz + r NS / bz and its mirror -m in row L / bz - r NS / bz - ceil(j / bz)
+    bool aligned;
+    int nsb, lb, bz;
     __device__ __forceinline__ PairPlainOut(const PassParams<T>& a, int t, bool masked_, const uint8_t* td,
                                             const uint8_t* tm)
         : masked(masked_), tabd(td), tabm(tm) {
@@ -439,11 +444,29 @@ template <typename T, int L, int P, int R> struct PairPlainOut {
             bxsd = (int)f.fd_b2.div((uint32_t)xd) - u.bxd0;
             bxsm = (int)f.fd_b2.div((uint32_t)xm) - u.bxm0;
             fd_bp = f.fd_bp;
+            bz = (int)f.fd_bp.d;
+            aligned = NS % bz == 0;
+            nsb = NS / bz;
+            lb = L / bz;
         }
     }
     __device__ __forceinline__ void pre() {}
     __device__ __forceinline__ void begin(int, int, int) {}
     __device__ __forceinline__ void emit(int, int, int j, C (&v)[R]) {
+        if (masked && aligned) {
+            const int bj = (int)fd_bp.div((uint32_t)j), cj = (int)fd_bp.div((uint32_t)(j + bz - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int m = j + r * NS;
+                if (tabd[(bj + r * nsb) * nbxd + bxsd] != SPDBA_FROZEN) pd[m * osJ] = v[r];
+                if (has_m) {
+                    const int mz = m == 0 ? 0 : L - m;
+                    const int bm = m == 0 ? 0 : lb - r * nsb - cj;
+                    if (tabm[bm * nbxm + bxsm] != SPDBA_FROZEN) pm[mz * osJ] = mk<C>(v[r].x, -v[r].y);
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int m = j + r * NS;
