@@ -69,9 +69,14 @@ __global__ void ch_dense_kernel(Geom g, CHUpdateArgs<T> a) {
     }
 }
 
-// sp-DBA: one warp per listed block, mode pairs along the fast axis.
+// sp-DBA: one warp per listed block, mode pairs along the fast axis.  Block
+// and mode coordinates are 32-bit (block maps and fields of a group hold
+// fewer than 2^31 entries along each axis product used here) and divided by
+// precomputed multiplicative inverses (fd_h: pairs per block row, fd_b1: the
+// block edge along axis 1; fd_nb2, fd_nb1: the block map's extents).
 template <typename T>
-__global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
+__global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a, FastDiv fd_h, FastDiv fd_b1, FastDiv fd_nb2,
+                               FastDiv fd_nb1) {
     const int lane = threadIdx.x & 31;
     const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -90,29 +95,32 @@ __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a) {
         }
     }
     const int H = B2 / 2;
-    const long long npair = nmodes / 2;
+    const int npair = (int)(nmodes / 2);
+    const long long n1 = g.n[1], n2 = g.n[2];
     for (long long w = warp0; w < cnt; w += nwarps) {
-        long long blk = a.list[w];
+        const int blk = a.list[w];
         const int st = a.states[blk];
         const unsigned ch = a.chi[blk];
-        const long long b2 = blk % g.nb[2], b1 = (blk / g.nb[2]) % g.nb[1], b0 = blk / (g.nb[2] * g.nb[1]);
-        for (long long m = lane; m < npair; m += 32) {
-            int l2 = (int)(m % H) * 2;
-            long long rr = m / H;
-            int l1 = (int)(rr % B1), l0 = (int)(rr / B1);
-            long long z = b0 * B0 + l0, y = b1 * B1 + l1, x = b2 * B2 + l2;
-            long long e = (z * g.n[1] + y) * g.n[2] + x;
+        const int q = (int)fd_nb2.div((uint32_t)blk);
+        const int b2 = blk - q * (int)g.nb[2];
+        const int b0 = (int)fd_nb1.div((uint32_t)q), b1 = q - b0 * (int)g.nb[1];
+        for (int m = lane; m < npair; m += 32) {
+            const int rr = (int)fd_h.div((uint32_t)m);
+            const int l2 = (m - rr * H) * 2;
+            const int l0 = (int)fd_b1.div((uint32_t)rr), l1 = rr - l0 * B1;
+            const int z = b0 * B0 + l0, y = b1 * B1 + l1, x = b2 * B2 + l2;
+            const long long e = ((long long)z * n1 + y) * n2 + x;
             T kzy = a.k2ax[0][z] + a.k2ax[1][y];
             cx_t<T> c0, c1, g0, g1;
             load2(a.c_hat + e, c0, c1);
             load2(a.g_hat + e, g0, g1);
             cx_t<T> n0 = ch_new(c0, g0, kzy + a.k2ax[2][x], a.dt, a.dtkappa);
-            cx_t<T> n1 = ch_new(c1, g1, kzy + a.k2ax[2][x + 1], a.dt, a.dtkappa);
+            cx_t<T> n1v = ch_new(c1, g1, kzy + a.k2ax[2][x + 1], a.dt, a.dtkappa);
             if (st == SPDBA_TRANSITION) {
                 n0 = ch_blend<T>(c0, n0, a.taper, g, ch, l0, l1, l2);
-                n1 = ch_blend<T>(c1, n1, a.taper, g, ch, l0, l1, l2 + 1);
+                n1v = ch_blend<T>(c1, n1v, a.taper, g, ch, l0, l1, l2 + 1);
             }
-            store2(a.c_hat + e, n0, n1);
+            store2(a.c_hat + e, n0, n1v);
         }
     }
 }
@@ -183,7 +191,14 @@ template <typename T> spdba_status launch_ch_update(const Geom& g, const CHUpdat
                      g.blocks() < 0x7fffffffLL;
             if (fixed8) ch_list8_kernel<<<(unsigned)grid, 256, 0, st>>>(g, a);
         }
-        if (!fixed8) ch_list_kernel<T><<<(unsigned)grid, 256, 0, st>>>(g, a);
+        if (!fixed8) {
+            FastDiv fd_h, fd_b1, fd_nb2, fd_nb1;
+            fd_h.init((uint32_t)(g.b[2] / 2));
+            fd_b1.init((uint32_t)g.b[1]);
+            fd_nb2.init((uint32_t)g.nb[2]);
+            fd_nb1.init((uint32_t)g.nb[1]);
+            ch_list_kernel<T><<<(unsigned)grid, 256, 0, st>>>(g, a, fd_h, fd_b1, fd_nb2, fd_nb1);
+        }
     }
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;
