@@ -309,6 +309,24 @@ const char* spdba_status_string(spdba_status s);
  */
 void spdba_debug_fail_alloc(int64_t k);
 int64_t spdba_debug_live_allocs(void);
+/*
+ * Host-side control of the device waits (no counterpart in the paper).  The
+ * TMA kernels (the half form's z inverse, the TMA list update) wait on
+ * mbarriers for their tile copies with an iteration limit; when a wait runs
+ * out the kernel counts it in the run's statistics, lets its copies in flight
+ * land (waiting again, with the default limit), and returns, and
+ * spdba_get_stats then reports SPDBA_ERR_TIMEOUT.
+ * spdba_debug_set_wait_limit(n): n >= 1 sets the first waits' limit to n
+ * polls for kernels launched from then on, n <= 0 restores the default
+ * (2^24 polls).  spdba_debug_stall_waits(1): the first wait of every CTA of
+ * those kernels targets a barrier nothing arrives on, so it runs out (after
+ * the limit, at most 4096 polls) while the real copies complete; 0 switches
+ * this off.  Graph
+ * segments captured earlier keep the settings they were captured with.
+ * Process-wide; for tests of the timeout path.
+ */
+void spdba_debug_set_wait_limit(int64_t n);
+void spdba_debug_stall_waits(int32_t on);
 
 /* ------------------------------------------------------------------------------ */
 /* Kernel-level entry points (device pointers, caller-owned buffers).               */

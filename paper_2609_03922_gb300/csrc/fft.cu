@@ -425,3 +425,19 @@ extern "C" const char* spdba_status_string(spdba_status s) {
 extern "C" void spdba_debug_fail_alloc(int64_t k) { spdba::g_fail_countdown.store(k > 0 ? (long long)k : 0); }
 
 extern "C" int64_t spdba_debug_live_allocs(void) { return (int64_t)spdba::g_live_allocs.load(); }
+
+namespace spdba {
+static std::atomic<long long> g_wait_limit{0};   // 0: the default
+long long wait_limit() {
+    const long long n = g_wait_limit.load();
+    return n > 0 ? n : kWaitLimit;
+}
+}  // namespace spdba
+
+namespace spdba {
+static std::atomic<int> g_stall_waits{0};
+int stall_waits() { return g_stall_waits.load(); }
+}  // namespace spdba
+
+extern "C" void spdba_debug_set_wait_limit(int64_t n) { spdba::g_wait_limit.store(n > 0 ? (long long)n : 0); }
+extern "C" void spdba_debug_stall_waits(int32_t on) { spdba::g_stall_waits.store(on ? 1 : 0); }

@@ -25,7 +25,6 @@
 
 namespace spdba {
 
-constexpr long long kHermSpinLimit = 1ll << 24;   // polls before a wait gives up
 
 // (direct + conj(mirror)) / 2 of element m of pencil p, from the tensor-box tiles
 template <int L, int P> struct HermInBox {
@@ -46,7 +45,7 @@ template <int L, int P, int NT>
 __global__ void __launch_bounds__(NT, 2)
     fft_herm_inv_tma_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                             const __grid_constant__ CUtensorMap map_c, PassParams<float> a,
-                            unsigned long long* timeouts, long long spin_limit) {
+                            unsigned long long* timeouts, long long spin_limit, int stall) {
     using C = float2;
     using LY = LayoutB<L, P>;
     constexpr int ZB = L <= 256 ? L : L / 2;   // z extent of one box
@@ -59,6 +58,7 @@ __global__ void __launch_bounds__(NT, 2)
     uint64_t* bar = reinterpret_cast<uint64_t*>(smC + 2 * L);   // fullA[0], fullA[1], fullB
     __shared__ C s_tw[L];
     __shared__ int s_abort;
+    __shared__ uint64_t s_never;   // a barrier nothing arrives on (stall: the timeout path under test)
     for (int j = threadIdx.x; j < L; j += NT) s_tw[j] = a.tw[j];   // visible after the loop's first barrier
     const HalfGeo& h = a.hg;
     const int M = h.N2 >> 1;
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(NT, 2)
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_init(&bar[2], 1);
+        mbar_init(&s_never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (t < ntiles) {
             issue_a(smA0, &bar[0], t);
@@ -117,7 +118,8 @@ __global__ void __launch_bounds__(NT, 2)
                 out_a[buf ^ 1] = true;
             }
             // the direct and mirror tiles of t
-            bool ok = mbar_wait_bounded(&bar[buf], ph_a[buf], spin_limit);
+            bool ok = stall ? mbar_wait_bounded(&s_never, 0u, spin_limit < 4096 ? spin_limit : 4096)
+                            : mbar_wait_bounded(&bar[buf], ph_a[buf], spin_limit);
             if (ok) {
                 ph_a[buf] ^= 1u;
                 out_a[buf] = false;
@@ -154,8 +156,8 @@ __global__ void __launch_bounds__(NT, 2)
     if (threadIdx.x == 0 && s_abort) {
         // copies still in flight land before the CTA leaves (bounded)
         for (int k = 0; k < 2; ++k)
-            if (out_a[k]) mbar_wait_bounded(&bar[k], ph_a[k], spin_limit);
-        if (out_b) mbar_wait_bounded(&bar[2], ph_b, spin_limit);
+            if (out_a[k]) mbar_wait_bounded(&bar[k], ph_a[k], kWaitLimit);
+        if (out_b) mbar_wait_bounded(&bar[2], ph_b, kWaitLimit);
         if (timeouts) atomicAdd(timeouts, 1ull);
     }
 }
@@ -214,8 +216,9 @@ spdba_status launch_herm_inv_tma(const HermTma& ht, const Pass<float>& zinv, con
     PassParams<float> p = zinv.p;
     p.in = reinterpret_cast<const float2*>(in);
     p.out = reinterpret_cast<float2*>(out);
-    long long spin = kHermSpinLimit;
-    void* args[] = {(void*)&ht.map[0], (void*)&ht.map[1], (void*)&ht.map[2], &p, &timeouts, &spin};
+    long long spin = wait_limit();
+    int stall = stall_waits();
+    void* args[] = {(void*)&ht.map[0], (void*)&ht.map[1], (void*)&ht.map[2], &p, &timeouts, &spin, &stall};
     SPDBA_CUDA(cudaLaunchKernel(ht.func, dim3((unsigned)ht.grid), dim3(kHermTmaNT), args, ht.smem, st));
     return SPDBA_OK;
 }

@@ -22,6 +22,14 @@ spdba_status cuda_fail(cudaError_t e, const char* what);
 // host without exhausting a GPU.
 cudaError_t dev_alloc(void** p, size_t bytes);
 void dev_free(void* p);
+// Iteration limit of a device wait on an mbarrier (the TMA kernels): the
+// default, also the limit of the waits that let a timed-out kernel's copies in
+// flight land before it returns; wait_limit() is the first waits' limit for
+// kernels launched now (spdba_debug_set_wait_limit).
+constexpr long long kWaitLimit = 1ll << 24;
+long long wait_limit();
+// Whether kernels launched now stall their first wait (spdba_debug_stall_waits).
+int stall_waits();
 #define SPDBA_CUDA(call)                                              \
     do {                                                              \
         cudaError_t e_ = (call);                                      \

@@ -25,7 +25,6 @@ constexpr int TMA_STAGES = 5;
 constexpr int TMA_BOX = 8;
 constexpr int TMA_BOX_MODES = TMA_BOX * TMA_BOX * TMA_BOX;           // 512
 constexpr unsigned TMA_BOX_BYTES = TMA_BOX_MODES * sizeof(float2);   // 4096
-constexpr long long TMA_SPIN_LIMIT = 1ll << 24;                      // polls before giving up
 
 struct TmaStage {
     float2 c[TMA_BOX_MODES];
@@ -34,13 +33,15 @@ struct TmaStage {
 
 __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_constant__ CUtensorMap map_c,
                                                              const __grid_constant__ CUtensorMap map_g, Geom g,
-                                                             CHUpdateArgs<float> a, long long spin_limit) {
+                                                             CHUpdateArgs<float> a, long long spin_limit,
+                                                             int stall) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // input stages (128-byte aligned), then two output boxes, then the barriers
     TmaStage* stage = reinterpret_cast<TmaStage*>(smem_raw);
     float2* outb = reinterpret_cast<float2*>(smem_raw + TMA_STAGES * sizeof(TmaStage));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + TMA_STAGES * sizeof(TmaStage) + 2 * TMA_BOX_BYTES);
     __shared__ int s_abort;
+    __shared__ uint64_t s_never;   // a barrier nothing arrives on (stall: the timeout path under test)
     const int cnt = *a.count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
         const unsigned long long nfi = a.stats[0].n_active + a.stats[0].n_transition;
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
     if (threadIdx.x == 0) {
         s_abort = 0;
         for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&full[s], 1);
+        mbar_init(&s_never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int s = 0; s < TMA_STAGES; ++s) {
             const long long w = blockIdx.x + (long long)s * gridDim.x;
@@ -91,13 +93,9 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
             // the output box written two iterations ago has been read by its store
             bulk_wait_read_but_newest();
             // bounded wait for the stage's two boxes
-            long long polls = 0;
-            while (!mbar_try_wait(&full[s], parity)) {
-                if (++polls > spin_limit) {
-                    s_abort = 1;
-                    break;
-                }
-            }
+            if (!(stall ? mbar_wait_bounded(&s_never, 0u, spin_limit < 4096 ? spin_limit : 4096)
+                        : mbar_wait_bounded(&full[s], parity, spin_limit)))
+                s_abort = 1;
         }
         __syncthreads();
         if (s_abort) {
@@ -135,7 +133,7 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
             for (int k = 0; k < TMA_STAGES; ++k) {
                 const long long it2 = it_abort + k;
                 if (blockIdx.x + it2 * gridDim.x < cnt)
-                    mbar_wait_bounded(&full[it2 % TMA_STAGES], (unsigned)((it2 / TMA_STAGES) & 1), spin_limit);
+                    mbar_wait_bounded(&full[it2 % TMA_STAGES], (unsigned)((it2 / TMA_STAGES) & 1), kWaitLimit);
             }
             if (a.stats) atomicAdd(&a.stats[0].timeouts, 1ull);
         }
@@ -207,7 +205,7 @@ spdba_status launch_ch_update_tma(const void* map_c, const void* map_g, const Ge
     if (grid < 1) grid = 1;
     ch_list_tma_kernel<<<(unsigned)grid, TMA_NT, tma_update_smem(), st>>>(
         *reinterpret_cast<const CUtensorMap*>(map_c), *reinterpret_cast<const CUtensorMap*>(map_g), g, a,
-        TMA_SPIN_LIMIT);
+        wait_limit(), stall_waits());
     SPDBA_CUDA(cudaGetLastError());
     return SPDBA_OK;
 }

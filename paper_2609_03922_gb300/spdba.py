@@ -97,6 +97,8 @@ SIGNATURES = {
     "spdba_last_error": (ctypes.c_char_p, []),
     "spdba_debug_fail_alloc": (None, [ctypes.c_int64]),
     "spdba_debug_live_allocs": (ctypes.c_int64, []),
+    "spdba_debug_set_wait_limit": (None, [ctypes.c_int64]),
+    "spdba_debug_stall_waits": (None, [ctypes.c_int32]),
     "spdba_status_string": (ctypes.c_char_p, [_S]),
     "spdba_fft_plan_create": (_S, [_PP, ctypes.c_int32, ctypes.c_int32, _I64P, ctypes.c_int64]),
     "spdba_fft_exec": (_S, [_P, _P, _P, ctypes.c_int32, _P]),

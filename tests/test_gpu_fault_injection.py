@@ -80,3 +80,48 @@ def test_failed_autotune_snapshot_leaves_the_plan_usable():
             assert L.spdba_debug_live_allocs() == live
             pl.step(10)
             assert np.all(np.isfinite(pl.get_field()))
+
+
+@pytest.mark.parametrize("kind", ["z_inverse", "list_update"])
+def test_tma_wait_timeout_is_reported_and_the_context_stays_usable(kind):
+    """The TMA kernels' mbarrier waits are bounded.  With the first wait of every
+    CTA pointed at a barrier nothing arrives on (a host switch), the wait runs
+    out after its limit, the kernel counts the timeout, lets its real copies
+    land and returns; spdba_get_stats then reports SPDBA_ERR_TIMEOUT.  The
+    context stays usable: with the switch off a new plan steps and its results
+    equal those of a plan that never saw a timeout."""
+    import workloads as W
+    from paper_2609_03922_gb300 import spdba
+    lib = spdba.lib()
+    if kind == "z_inverse":
+        dims, kw = (128, 128, 128), dict(half_spectrum=1, tma_passes=1)
+        key = "tma_passes"
+    else:
+        dims, kw = (64, 64, 64), dict(half_spectrum=0, tma_update=1)
+        key = "tma_update"
+    c0 = W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 7).astype(np.float32)
+
+    def run(steps):
+        with spdba.Plan(dims, (8, 8, 8), threshold=1e-2, reassess=2, precision=0, fuse_update=0, use_graph=0,
+                        **kw) as pl:
+            assert pl.get_config()[key] == 1
+            pl.set_field(c0)
+            pl.step(steps)
+            pl.sync()
+            try:
+                return pl.get_stats(), pl.get_spectrum(), None
+            except spdba.SpdbaError as e:
+                return None, None, e
+
+    try:
+        lib.spdba_debug_set_wait_limit(64)
+        lib.spdba_debug_stall_waits(1)
+        _, _, err = run(3)
+        assert err is not None and err.status == spdba.SPDBA_ERR_TIMEOUT
+    finally:
+        lib.spdba_debug_stall_waits(0)
+        lib.spdba_debug_set_wait_limit(0)
+    st_a, sp_a, err_a = run(6)
+    st_b, sp_b, err_b = run(6)
+    assert err_a is None and err_b is None and st_a["step"] == 6
+    assert np.array_equal(sp_a, sp_b)
