@@ -645,17 +645,20 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     steps = max(1, min(args.steps, REFERENCE_MAX_STEPS))
+    warm = max(0, min(args.warmup, REFERENCE_MAX_STEPS))
     import oracle as O
     import workloads as W
     c0 = W.ch_initial_condition(DIMS, mean=MEAN, amplitude=AMP, seed=W.BASE_SEED).astype(np.float32)
     cfg = O.CHConfig(DIMS, BLOCK, threshold=THRESHOLD, reassess=REASSESS, dt=DT, kappa=KAPPA)
+    if warm:
+        O.run_ch(c0.astype(np.float64), cfg, warm)   # untimed warm-up steps (same work, from c0)
     t0 = time.perf_counter()
     O.run_ch(c0.astype(np.float64), cfg, steps)
     el = time.perf_counter() - t0
     v = steps / el
     cores = O.num_threads()
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
-            "steps": steps, "warmup": 0, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(DIMS), "block": list(BLOCK)},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
