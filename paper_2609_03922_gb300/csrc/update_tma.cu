@@ -35,11 +35,11 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
                                                              const __grid_constant__ CUtensorMap map_g, Geom g,
                                                              CHUpdateArgs<float> a, long long spin_limit,
                                                              int stall) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_tma[];
     // input stages (128-byte aligned), then two output boxes, then the barriers
-    TmaStage* stage = reinterpret_cast<TmaStage*>(smem_raw);
-    float2* outb = reinterpret_cast<float2*>(smem_raw + TMA_STAGES * sizeof(TmaStage));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + TMA_STAGES * sizeof(TmaStage) + 2 * TMA_BOX_BYTES);
+    TmaStage* stage = reinterpret_cast<TmaStage*>(smem_tma);
+    float2* outb = reinterpret_cast<float2*>(smem_tma + TMA_STAGES * sizeof(TmaStage));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_tma + TMA_STAGES * sizeof(TmaStage) + 2 * TMA_BOX_BYTES);
     __shared__ int s_abort;
     __shared__ uint64_t s_never;   // a barrier nothing arrives on (stall: the timeout path under test)
     const int cnt = *a.count;
