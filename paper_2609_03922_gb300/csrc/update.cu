@@ -158,10 +158,16 @@ __global__ void __launch_bounds__(256) ch_list8_kernel(Geom g, CHUpdateArgs<floa
         const float ky = a.k2ax[1][y], kx0 = a.k2ax[2][x], kx1 = a.k2ax[2][x + 1];
         float2* cp = a.c_hat + (long long)z0 * plane + (long long)y * n2 + x;
         const float2* gp = a.g_hat + (long long)z0 * plane + (long long)y * n2 + x;
+        // the block's sixteen 16-byte loads of this lane are all issued before any store
+        float4 cvs[B], gvs[B];
 #pragma unroll
         for (int l0 = 0; l0 < B; ++l0) {
-            const float4 cv = *reinterpret_cast<const float4*>(cp + l0 * plane);
-            const float4 gv = *reinterpret_cast<const float4*>(gp + l0 * plane);
+            cvs[l0] = *reinterpret_cast<const float4*>(cp + l0 * plane);
+            gvs[l0] = *reinterpret_cast<const float4*>(gp + l0 * plane);
+        }
+#pragma unroll
+        for (int l0 = 0; l0 < B; ++l0) {
+            const float4 cv = cvs[l0], gv = gvs[l0];
             const float kzy = a.k2ax[0][z0 + l0] + ky;
             const float2 c0 = make_float2(cv.x, cv.y), c1 = make_float2(cv.z, cv.w);
             float2 n0 = ch_new(c0, make_float2(gv.x, gv.y), kzy + kx0, a.dt, a.dtkappa);
