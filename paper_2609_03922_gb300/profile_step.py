@@ -41,6 +41,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--model", choices=["ch", "rcd"], default="ch")
     ap.add_argument("--components", type=int, default=48, help="RCD: components M")
+    ap.add_argument("--predictor", type=int, default=0,
+                    help="1: attach the learned predictor (untrained weights, K = 20, J = 100) to a CH plan, "
+                         "so that its prediction kernels run at steps 20, 40, 60, 80")
     args = ap.parse_args(argv)
 
     import torch
@@ -64,6 +67,10 @@ def main(argv=None):
                     mode=spdba.SPDBA_MODE_ADAPTIVE if args.mode == "adaptive" else spdba.SPDBA_MODE_REGULAR,
                     fuse_update=args.fuse, half_spectrum=args.half, use_graph=0, tma_update=args.tma,
                     tma_passes=args.tma_passes, **kw) as plan:
+        if args.predictor:
+            m = tuple(d // b for d, b in zip(dims, args.block))
+            pred = spdba.Predictor(m, max_batch=1, params=spdba.predictor_init_params(0))   # outlives the plan's steps
+            plan.attach_predictor(pred, 20, 100, 0.5)
         plan.set_field(c0)
         plan.step(args.warm)
         plan.step(args.steps)
