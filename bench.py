@@ -212,6 +212,31 @@ def cufft_comparator(dev, reps=20):
     return out
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+# Each rank runs its own replica of the workload (no data-path collective);
+# only the timing crosses ranks: a barrier on both sides of a timed region and
+# the slowest rank's time, so that value = ranks x units / that time.
+def replica_barrier():
+    import torch.distributed as tdist
+    tdist.barrier()
+
+
+def replica_max(v, device):
+    """The maximum of v over the ranks of the default process group (v on
+    `device`: a CUDA device under NCCL, the CPU under gloo)."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, ms_slowest, world):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest rank."""
+    return world * units_per_rank / (ms_slowest / 1e3)
+
+
 def run_ours(args, rank, world, local_rank, parity=None):
     import torch
     from paper_2609_03922_gb300 import build as B
@@ -227,19 +252,13 @@ def run_ours(args, rank, world, local_rank, parity=None):
     c0_dev = torch.from_numpy(c0).to(dev)
     K, Wm = args.steps, args.warmup
     dist = world > 1
-    if dist:
-        import torch.distributed as tdist
 
     def barrier():
         if dist:
-            tdist.barrier()
+            replica_barrier()
 
     def max_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, dev) if dist else v
 
     def make(mode, fuse, **kw):
         return spdba.Plan(DIMS, BLOCK, threshold=THRESHOLD, reassess=REASSESS, precision=spdba.SPDBA_C64,
@@ -467,8 +486,8 @@ def run_ours(args, rank, world, local_rank, parity=None):
     cufft = cufft_comparator(dev)
 
     n = int(np.prod(DIMS))
-    value = world * K / (ms_ada / 1e3)
-    dense_value = world * K / (ms_dense / 1e3)
+    value = replica_throughput(K, ms_ada, world)
+    dense_value = replica_throughput(K, ms_dense, world)
     hbm, peak_kind = peaks()
     n_half = DIMS[0] * DIMS[1] * (DIMS[2] // 2 + 1)
 
@@ -591,7 +610,7 @@ def run_ours(args, rank, world, local_rank, parity=None):
                                  note="torch.fft (cuFFT) on the 256^3 field, median of 20; ours = the step's "
                                       "transform passes (z/y inverse, x pass with c^3 - c, y forward, z "
                                       "forward or z forward + update) from the profiled window"),
-        "e2e": {"value": world * K / (e2e / 1e3), "unit": "steps/s",
+        "e2e": {"value": replica_throughput(K, e2e, world), "unit": "steps/s",
                 "h2d_bytes_per_step": 4.0 * n / K, "d2h_bytes_per_step": 4.0 * n / K,
                 "note": ("set_field of each window's starting field (steps %s) from pinned host + %d steps + "
                          "get_field to pinned host; mean per window, median of %d" % (starts, K, reps_ada))},
