@@ -11,6 +11,8 @@ Example (256^3, complex64, the staged half-spectrum form, steps 500..509):
     python -m paper_2609_03922_gb300.profile_step --dims 256 256 256 --warm 500 --steps 10
 RCD (M components; dx = 0.5):
     python -m paper_2609_03922_gb300.profile_step --model rcd --components 48 --dims 128 128 128 --block 4 4 4
+A batched 2-D plan of several sizes, one launch per pass phase over all of them:
+    python -m paper_2609_03922_gb300.profile_step --sides 128 192 256 384 512 --fuse 1 --multi-pass 1
 """
 import argparse
 import json
@@ -41,6 +43,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--model", choices=["ch", "rcd"], default="ch")
     ap.add_argument("--components", type=int, default=48, help="RCD: components M")
+    ap.add_argument("--sides", type=int, nargs="*", default=None,
+                    help="2-D batched CH plan instead: one run of side s per value (16^2 blocks unless --block2 is given)")
+    ap.add_argument("--block2", type=int, nargs=2, default=[16, 16])
+    ap.add_argument("--multi-pass", type=int, default=0, help="batched 2-D plans: 1 or 2 = one launch per pass phase")
     ap.add_argument("--predictor", type=int, default=0,
                     help="1: attach the learned predictor (untrained weights, K = 20, J = 100) to a CH plan, "
                          "so that its prediction kernels run at steps 20, 40, 60, 80")
@@ -56,6 +62,19 @@ def main(argv=None):
     prec = spdba.SPDBA_C64 if args.precision == "c64" else spdba.SPDBA_C128
     rdt = np.float32 if prec == spdba.SPDBA_C64 else np.float64
     dims = tuple(args.dims)
+    if args.sides:
+        bd = [(sd, sd) for sd in args.sides]
+        c0s = [W.ch_initial_condition(d, mean=args.mean, seed=W.BASE_SEED + i).astype(rdt) for i, d in enumerate(bd)]
+        with spdba.Plan(None, tuple(args.block2), threshold=args.threshold, reassess=args.reassess, batch_dims=bd,
+                        precision=prec, fuse_update=args.fuse, use_graph=0, multi_pass=args.multi_pass) as plan:
+            for r, c0 in enumerate(c0s):
+                plan.set_field(c0, run=r)
+            plan.step(args.warm)
+            plan.step(args.steps)
+            plan.sync()
+            cfg = plan.get_config()
+        print(json.dumps({"sides": args.sides, "multi_pass": cfg["multi_pass"], "fuse_update": cfg["fuse_update"]}))
+        return
     kw = {}
     if args.model == "rcd":
         M = args.components
