@@ -21,6 +21,12 @@ Parity status of each piece (what pins it, see tests/test_oracle_*.py):
                                 control steps are full-activation steps (== Regular)
   nls_* ....................... CW exact solution, dispersion-only closed form,
                                 unitarity, forward/backward recovery
+  half-spectrum form (*_half) . numpy's rfftn / irfftn (incl. a stored kx = 0 plane that
+                                is not conjugate-symmetric), Eq. S.4 extension == full DFT,
+                                Regular half step == half of the full Regular step,
+                                hand-traced half maps (conjugate neighbours across kx = 0
+                                and past the Nyquist block) and their sigma, threshold 0 ==
+                                Regular bit for bit, untouched frozen modes
   rcd_* ....................... circulant eigenvalues in closed form, hand-computed
                                 reaction values, direct solve == eigen form,
                                 linearised single-mode growth matrix, threshold 0 ==
@@ -33,6 +39,10 @@ Paper conventions restated (section / equation of arXiv 2609.03922):
   * States: ACTIVE when the block's activation measure meets the threshold;
     TRANSITION when not active but a neighbouring block is active; FROZEN
     otherwise (Methods).
+  * Real fields may be stored as the half spectrum kx = 0 .. N/2 with the block map
+    on that half; a neighbour in the omitted half is activated through its
+    conjugate counterpart, X(-k) = conj X(k), and kx = 0 is a symmetry boundary
+    (S1.2, Eq. S.4).
   * Transition smoothing q_{n+1} = q_n + sigma(k) dq_raw with the taper
     w(i) = (1 - cos(pi i / (B-1))) / 2 and sigma the product of w over the
     faces whose neighbour is frozen (S1.1, Eq. S.1-S.3).
@@ -84,6 +94,9 @@ __all__ = [
     "rcd_diffusion_matrix", "rcd_interaction_matrix", "rcd_reaction", "rcd_homogeneous_state",
     "rcd_eigen", "rcd_update_direct", "rcd_update_eigen", "rcd_mode_amplitude_sq", "RCDConfig",
     "rcd_assess_states", "rcd_real_field", "rcd_new", "rcd_masked_step", "run_rcd",
+    "half_extent", "rfftn_half", "hermitian_extend", "ch_real_field_half", "half_block_counts",
+    "half_block_measures", "half_neighbour", "classify_half", "sigma_field_half", "k_squared_half",
+    "ch_regular_step_half", "ch_masked_step_half", "assess_states_half", "run_ch_half",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -472,6 +485,218 @@ def run_ch(c0, cfg, steps, start_step=0, c_hat=None, on_assess=None, states=None
         if controller is not None:
             controller.end_step(n, states)
     return c_hat, history
+
+
+# --------------------------------------------------------------------------------------
+# Half-spectrum (real-to-complex) storage of a real CH field, block states on the
+# stored half with conjugate neighbour activation (S1.2, Eq. S.4)
+# --------------------------------------------------------------------------------------
+def half_extent(n_last):
+    """Stored x frequencies of a real field along its last axis: kx = 0 .. N/2 (N even)."""
+    return n_last // 2 + 1
+
+
+def rfftn_half(x):
+    """The stored half of the DFT of a real field: X[..., kx] for kx = 0 .. N/2; the
+    omitted half follows from X(-k) = conj X(k) (Eq. S.4)."""
+    X = fftn(np.asarray(x, dtype=np.float64))
+    return np.ascontiguousarray(X[..., : half_extent(X.shape[-1])])
+
+
+def _negate_index(a, axes):
+    """a[j] -> a[(-j) mod N] along each of `axes`."""
+    for axis in axes:
+        a = np.roll(np.flip(a, axis=axis), 1, axis=axis)
+    return a
+
+
+def hermitian_extend(h, dims):
+    """Full spectrum of a half-stored one: kx = 0 .. N/2 as stored, kx = N/2+1 .. N-1 by
+    Eq. S.4, X(k_other, kx) = conj X(-k_other, N - kx)."""
+    dims = tuple(int(x) for x in dims)
+    m = dims[-1] // 2
+    full = np.zeros(dims, dtype=np.complex128)
+    full[..., : m + 1] = h
+    mirror = _negate_index(np.asarray(h)[..., 1:m][..., ::-1], range(len(dims) - 1))
+    full[..., m + 1:] = np.conj(mirror)
+    return full
+
+
+def ch_real_field_half(h, dims):
+    """c of a half-stored spectrum: Re(IFFT) of its Hermitian extension.  Where the stored
+    kx = 0 and kx = N/2 planes are not conjugate-symmetric within themselves, Re(.) keeps
+    their Hermitian part, as a complex-to-real transform does."""
+    return np.real(ifftn(hermitian_extend(h, dims)))
+
+
+def half_block_counts(dims, block):
+    """Block grid of the stored half spectrum: the full grid's counts on every axis but
+    the last; there the columns kx = 0 .. N/2 take N/(2B) + 1 blocks of B columns, the
+    last holding the column kx = N/2 alone (its other B - 1 columns are absent)."""
+    dims = tuple(int(x) for x in dims)
+    block = tuple(int(x) for x in block)
+    n, b = dims[-1], block[-1]
+    if n % (2 * b) != 0:
+        raise ValueError("the half map needs 2 B | N along the last axis (B=%d, N=%d)" % (b, n))
+    return tuple(block_counts(dims[:-1], block[:-1])) + (n // (2 * b) + 1,)
+
+
+def _pad_half(a, dims, block):
+    """A half-grid array padded along its last axis to whole blocks with zeros."""
+    nbs = half_block_counts(dims, block)
+    out = np.zeros(a.shape[:-1] + (nbs[-1] * block[-1],), dtype=a.dtype)
+    out[..., : a.shape[-1]] = a
+    return out
+
+
+def half_block_measures(h, dims, block):
+    """Per-block max |q|^2 and sum |q|^2 (FP64) on the half map (absent modes count as 0)."""
+    sq = _blockify(_pad_half(_mode_sq(h), dims, block), block)
+    axes = tuple(range(1, sq.ndim, 2))
+    return sq.max(axis=axes), sq.sum(axis=axes)
+
+
+def half_neighbour(idx, axis, d, nbs):
+    """Face neighbour (d = -1 / +1) along `axis` of block `idx` of a half map (S1.2).
+
+    Every axis but the last wraps periodically.  Along the last axis a neighbour inside
+    the stored half is taken directly; one in the omitted half -- left of kx = 0 or right
+    of the Nyquist block -- is replaced by its conjugate counterpart (Eq. S.4): the block
+    that holds most of the negated modes, i.e. the other axes' block indices mirrored
+    (b -> nb - 1 - b) with block 0 on the last axis (across kx = 0, the symmetry
+    boundary, whose partner block is then activated) or the block just below the Nyquist
+    block (past kx = N/2, whose conjugates kx = N/2 - B .. N/2 - 1 fill that block)."""
+    idx = list(idx)
+    last = len(nbs) - 1
+    if axis != last:
+        idx[axis] = (idx[axis] + d) % nbs[axis]
+        return tuple(idx)
+    v = idx[last] + d
+    if 0 <= v < nbs[last]:
+        idx[last] = v
+        return tuple(idx)
+    for a in range(last):
+        idx[a] = nbs[a] - 1 - idx[a]
+    idx[last] = 0 if v < 0 else nbs[last] - 2
+    return tuple(idx)
+
+
+def classify_half(measure, tau, force_dc=False, transitions=True):
+    """Block states of a half map: ACTIVE iff measure >= tau (the block holding k = 0
+    forced ACTIVE when force_dc, S6.1).  With transitions every ACTIVE block requests
+    activation of its face neighbours -- half_neighbour, so a neighbour in the omitted
+    half is replaced by its conjugate counterpart (S1.2) -- and each requested block
+    that is not ACTIVE becomes TRANSITION; the rest are FROZEN.  (Past the Nyquist
+    block the relation is not symmetric: the block requested there does not request
+    the Nyquist block back.)"""
+    active = np.asarray(measure, dtype=np.float64) >= tau
+    if force_dc:
+        active.flat[0] = True
+    states = np.where(active, STATE_ACTIVE, STATE_FROZEN).astype(np.uint8)
+    if transitions:
+        nbs = active.shape
+        for idx in zip(*np.nonzero(active)):
+            for axis in range(len(nbs)):
+                for d in (-1, 1):
+                    nb = half_neighbour(idx, axis, d, nbs)
+                    if not active[nb]:
+                        states[nb] = STATE_TRANSITION
+    return states
+
+
+def sigma_field_half(states, dims, block):
+    """Per-mode sigma on the stored half grid (S1.1, Eq. S.1-S.3 with the half map's
+    neighbours): 1 in ACTIVE blocks, 0 in FROZEN ones, and in TRANSITION blocks the
+    product over faces whose neighbour (half_neighbour) is FROZEN of w(i) (lower face)
+    or w(B-1-i) (upper face), i the mode's position in the block."""
+    states = np.asarray(states)
+    nbs = states.shape
+    d = states.ndim
+    w = [taper(b) for b in block]
+    sigma = np.zeros(tuple(nb * b for nb, b in zip(nbs, block)), dtype=np.float64)
+    for bidx in np.ndindex(*nbs):
+        st = states[bidx]
+        sl = tuple(slice(i * b, (i + 1) * b) for i, b in zip(bidx, block))
+        if st == STATE_ACTIVE:
+            sigma[sl] = 1.0
+        elif st == STATE_TRANSITION:
+            local = np.ones(tuple(block), dtype=np.float64)
+            for axis in range(d):
+                shape = [1] * d
+                shape[axis] = block[axis]
+                if states[half_neighbour(bidx, axis, -1, nbs)] == STATE_FROZEN:
+                    local = local * w[axis].reshape(shape)
+                if states[half_neighbour(bidx, axis, +1, nbs)] == STATE_FROZEN:
+                    local = local * w[axis][::-1].reshape(shape)
+            sigma[sl] = local
+    return np.ascontiguousarray(sigma[..., : half_extent(dims[-1])])
+
+
+def k_squared_half(dims, dx=1.0):
+    """|k|^2 on the stored half grid (kx = 0 .. N/2)."""
+    return np.ascontiguousarray(k_squared(dims, dx)[..., : half_extent(dims[-1])])
+
+
+def _ch_new_half(h, dims, k2h, dt, kappa):
+    c = ch_real_field_half(h, dims)
+    g_hat = rfftn_half(c * c * c - c)
+    return (h - dt * k2h * g_hat) / (1.0 + dt * kappa * k2h * k2h)
+
+
+def ch_regular_step_half(h, dims, k2h, dt, kappa):
+    """Regular step on the stored half (the same update as ch_regular_step, mode by mode)."""
+    return _ch_new_half(h, dims, k2h, dt, kappa)
+
+
+def ch_masked_step_half(h, states, dims, block, k2h, dt, kappa, sigma=None):
+    """sp-DBA step on the stored half with half-map states (S1.1, Eq. S.1; S1.2)."""
+    new = _ch_new_half(h, dims, k2h, dt, kappa)
+    if sigma is None:
+        sigma = sigma_field_half(states, dims, block)
+    st = np.ascontiguousarray(_state_field(states, block)[..., : half_extent(dims[-1])])
+    out = np.where(st == STATE_ACTIVE, new, h)
+    tr = st == STATE_TRANSITION
+    out[tr] = h[tr] + sigma[tr] * (new[tr] - h[tr])
+    return out
+
+
+def assess_states_half(h, cfg, exclude_dc, threshold=None):
+    """Measure, threshold and classify a half-stored spectrum; returns (states, tau, measure)."""
+    maxsq, sumsq = half_block_measures(h, cfg.dims, cfg.block)
+    measure = np.sqrt(maxsq if cfg.measure == MEASURE_MAXAMP else sumsq)
+    tau = threshold_value(h, cfg.threshold if threshold is None else threshold, cfg.tau_rule, exclude_dc)
+    states = classify_half(measure, tau, force_dc=cfg.force_dc, transitions=cfg.transitions)
+    return states, tau, measure
+
+
+def run_ch_half(c0, cfg, steps, start_step=0, h=None, on_assess=None, states=None, controller=None):
+    """run_ch with the spectrum stored as its half (kx = 0 .. N/2) and block states on the
+    half map; returns (h, history).  Same schedule (reassessment, refresh, warm-up,
+    dynamic control) and callbacks as run_ch."""
+    dims = cfg.dims
+    k2h = k_squared_half(dims)
+    if h is None:
+        h = rfftn_half(c0)
+    if controller is None and getattr(cfg, "target_ratio", 0.0) > 0:
+        controller = ThresholdController(cfg, np.prod(half_block_counts(dims, cfg.block)))
+    history = []
+    for n in range(start_step, start_step + steps):
+        if cfg.mode == 0:
+            h = ch_regular_step_half(h, dims, k2h, cfg.dt, cfg.kappa)
+            continue
+        thr = controller.begin_step(n) if controller is not None else None
+        if states is None or n % cfg.reassess == 0:
+            states, tau, _ = assess_states_half(h, cfg, exclude_dc=True, threshold=thr)
+            if on_assess is not None:
+                repl = on_assess(n, h, states, tau)
+                if repl is not None:
+                    states = repl
+            history.append((n, states.copy(), tau))
+        eff = effective_states(states, n, cfg)
+        h = ch_masked_step_half(h, eff, dims, cfg.block, k2h, cfg.dt, cfg.kappa)
+        if controller is not None:
+            controller.end_step(n, states)
+    return h, history
 
 
 # --------------------------------------------------------------------------------------
