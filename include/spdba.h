@@ -122,6 +122,20 @@ typedef struct spdba_options {
                                are a whole number of tiles; 0: per-thread cp.async copies.  Same
                                values bit for bit.  A bounded wait that runs out makes
                                spdba_get_stats return SPDBA_ERR_TIMEOUT. */
+    int32_t half_storage;   /* 3-D CH complex64 (each 3-D run is its own group), 2 B2 | N2:
+                               1 = store the spectrum of the real field as its half
+                               kx = 0 .. N2/2 (S1.2): the block map covers that half (N2/(2 B2) + 1
+                               x-blocks, the last holding kx = N2/2 alone), an ACTIVE block's
+                               neighbour in the omitted half is activated through its conjugate
+                               counterpart X(-k) = conj X(k) (Eq. S.4; the other axes' block
+                               indices mirrored, b -> nb - 1 - b, x-block 0 across kx = 0 and
+                               x-block N2/(2 B2) - 1 past the Nyquist block), and every transform
+                               and the update run on the stored half.  c is the complex-to-real
+                               inverse of the stored half (the kx = 0 and N2/2 planes contribute
+                               their Hermitian part).  spdba_get/set_spectrum then take
+                               N0 x N1 x (N2/2 + 1) values and spdba_get_mask / spdba_get_activity
+                               N0/B0 x N1/B1 x (N2/(2 B2) + 1) blocks.  0 (default) = full
+                               spectrum.  SPDBA_ERR_UNSUPPORTED where the plan does not qualify. */
 } spdba_options;
 
 /* Per-run statistics, refreshed at each reassessment. */

@@ -344,8 +344,27 @@ __device__ __forceinline__ BCoord bcoord(const Geom& g, int b) {
 __device__ __forceinline__ int bindex(const Geom& g, const BCoord& c) {
     return (c.c[0] * (int)g.nb[1] + c.c[1]) * (int)g.nb[2] + c.c[2];
 }
-// face neighbour along `axis` (periodic wrap of the block index)
+// The block across the face of c along `axis` (dir -1 / +1): periodic wrap of
+// the block index; on a half map (g.hx > 0) the x neighbour left of kx = 0 or
+// right of the Nyquist block lies in the omitted half and is replaced by its
+// conjugate counterpart, X(-k) = conj X(k) (S1.2, Eq. S.4): the other field
+// axes' block indices mirrored (b -> nb - 1 - b), x-block 0 (across kx = 0,
+// the symmetry boundary) or hx - 2 (whose modes are the conjugates of those
+// right of kx = N/2).
+__device__ __forceinline__ void mirror_other_axes(const Geom& g, BCoord& c) {
+    for (int a = 3 - g.ndim; a < 2; ++a) c.c[a] = (int)g.nb[a] - 1 - c.c[a];
+}
 __device__ __forceinline__ BCoord bnbr(const Geom& g, BCoord c, int axis, int dir) {
+    if (axis == 2 && g.hx > 0) {
+        const int v = c.c[2] + dir;
+        if (v >= 0 && v < g.hx) {
+            c.c[2] = v;
+        } else {
+            mirror_other_axes(g, c);
+            c.c[2] = v < 0 ? 0 : g.hx - 2;
+        }
+        return c;
+    }
     const int n = (int)g.nb[axis];
     int v = c.c[axis] + dir;
     v = v < 0 ? v + n : (v >= n ? v - n : v);
@@ -397,13 +416,45 @@ __global__ void active_kernel(Geom g, const double* __restrict__ msq, int msq_is
 // The face neighbours' flags are ORed without short-circuit, so that their
 // loads are independent and in flight together (a chain of dependent loads per
 // neighbour made the state kernel latency-bound).
+//
+// An ACTIVE block requests activation of the block across each of its faces
+// (bnbr); c is TRANSITION when one of them requests it.  On a periodic map
+// these are c's own face neighbours.  On a half map the x sources of a live
+// block are: x - 1, or across kx = 0 its mirrored partner in x-block 0; x + 1
+// below the Nyquist block (the Nyquist block's request goes to its conjugate
+// counterpart instead); and, for x-block hx - 2, the mirrored Nyquist block,
+// whose request past kx = N/2 lands there.
 __device__ __forceinline__ bool has_active_nbr(const Geom& g, const uint8_t* active, const BCoord& c) {
     const int a0 = 3 - g.ndim;
     unsigned any = 0;
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
+    for (int ax = 0; ax < 2; ++ax) {
         if (ax < a0) continue;
         any |= active[bindex(g, bnbr(g, c, ax, -1))] | active[bindex(g, bnbr(g, c, ax, +1))];
+    }
+    if (g.hx > 0) {
+        const int x = c.c[2];
+        BCoord s = c;
+        if (x > 0) {
+            s.c[2] = x - 1;
+        } else {
+            mirror_other_axes(g, s);
+            s.c[2] = 0;
+        }
+        any |= active[bindex(g, s)];
+        if (x < g.hx - 1) {
+            s = c;
+            s.c[2] = x + 1;
+            any |= active[bindex(g, s)];
+        }
+        if (x == g.hx - 2) {
+            s = c;
+            mirror_other_axes(g, s);
+            s.c[2] = g.hx - 1;
+            any |= active[bindex(g, s)];
+        }
+    } else {
+        any |= active[bindex(g, bnbr(g, c, 2, -1))] | active[bindex(g, bnbr(g, c, 2, +1))];
     }
     return any != 0;
 }
@@ -441,6 +492,7 @@ __global__ void __launch_bounds__(CLS_NT) state_kernel(Geom g, const uint8_t* __
                 if (frozen) cb |= (uint8_t)(1u << (2 * (ax - a0) + d));
             }
         }
+        if (g.hx > 0 && c.c[2] >= g.hx) st = 0, cb = 0;   // padding x-blocks of a half map
         states[b] = (uint8_t)st;
         chi[b] = cb;
     }

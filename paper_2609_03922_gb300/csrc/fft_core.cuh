@@ -110,6 +110,11 @@ template <typename T> struct CHFuse {
 // holds x frequencies 0 .. N2/2 in rows of NHP >= N2/2 + 1 entries (the rest 0).
 struct HalfGeo {
     int N0 = 1, N1 = 1, N2 = 2, NHP = 2;
+    // the half array is the stored spectrum itself (half-spectrum storage):
+    // the x pass keeps only the real parts of the kx = 0 and kx = N2/2 entries,
+    // as a complex-to-real transform does (their planes need not be
+    // conjugate-symmetric within themselves)
+    int r2c = 0;
     FastDiv fd_N2, fd_NHP, fd_M;   // fd_M: division by N2 / 2
 };
 
@@ -887,10 +892,10 @@ __device__ __forceinline__ bool tile_live(const PassParams<T>& a, long long q0) 
 template <typename T, int NT> __device__ __forceinline__ void ch_update_stats(const CHFuse<T>& f, int dense) {
     const Geom& g = f.g;
     if (blockIdx.x != 0 || !f.stats) return;
-    const double inv = 1.0 / (double)g.bpr();
+    const double inv = 1.0 / (double)g.live_bpr();
     const long long bm = g.block_modes();
     for (long long r = threadIdx.x; r < g.runs(); r += NT) {
-        double nf = dense ? (double)g.bpr() : (double)(f.stats[r].n_active + f.stats[r].n_transition);
+        double nf = dense ? (double)g.live_bpr() : (double)(f.stats[r].n_active + f.stats[r].n_transition);
         f.stats[r].ratio_sum += nf * inv;
         if (!dense) {
             f.stats[r].list_modes += nf * (double)bm;

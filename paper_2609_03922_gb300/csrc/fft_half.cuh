@@ -190,10 +190,12 @@ template <typename T, int L, class LY> struct SmemOut {
 };
 
 // Packed input element k of transform pencil pp: X1[k] + i X2[k] from rows
-// 2 pp and 2 pp + 1, extended past N2/2 by conjugate symmetry.
+// 2 pp and 2 pp + 1, extended past N2/2 by conjugate symmetry (with r2c, the
+// imaginary parts at k = 0 and N2/2 dropped).
 template <typename T, int L> struct PairPackIn {
     const cx_t<T>* rw;
     int nhp;
+    bool r2c;
     __device__ __forceinline__ cx_t<T> operator()(int pp, int k) const {
         const cx_t<T>* r1 = rw + (2 * pp) * nhp;
         const cx_t<T>* r2 = r1 + nhp;
@@ -201,6 +203,7 @@ template <typename T, int L> struct PairPackIn {
         if (k <= L / 2) {
             x1 = r1[k];
             x2 = r2[k];
+            if (r2c && (k == 0 || k == L / 2)) x1.y = x2.y = (T)0;
         } else {
             x1 = r1[L - k];
             x2 = r2[L - k];
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(NT, L == 384 ? 1 : 512 / NT) fft_nl_half_kerne
         // g = c^3 - c on both rows, forward
         ChNlPairMid<T> mid{a.nl_scale, (T)0};
         SmemOut<T, L, LY> so{tb};
-        PairPackIn<T, L> in{rw, NHP};
+        PairPackIn<T, L> in{rw, NHP, a.hg.r2c != 0};
         transform_pair_in<T, L, PP, NT, +1, -1, LY>(tb, a.tw, in, mid, so);
         __syncthreads();
         // separate the two rows' half spectra (padding entries zero), straight

@@ -12,6 +12,11 @@ struct Geom {
     int ndim = 0;
     long long n[3] = {1, 1, 1};
     int b[3] = {1, 1, 1};
+    // Half map (hx > 0): the blocks of the stored half kx = 0 .. N/2 of a real
+    // field's spectrum, hx x-blocks of it (the last holding the column kx =
+    // N/2), any x-blocks past them padding; neighbours in the omitted half are
+    // conjugate counterparts (S1.2).  hx = 0: a full, periodic map.
+    int hx = 0;
     long long nb[3] = {1, 1, 1};
     __host__ __device__ long long modes() const { return n[0] * n[1] * n[2]; }
     __host__ __device__ long long blocks() const { return nb[0] * nb[1] * nb[2]; }
@@ -26,6 +31,8 @@ struct Geom {
         return ndim == 3 ? n[0] * n[1] * n[2] : ndim == 2 ? n[1] * n[2] : n[2];
     }
     __host__ __device__ long long runs() const { return blocks() / bpr(); }
+    // blocks of a run that hold modes (the padding x-blocks of a half map excluded)
+    __host__ __device__ long long live_bpr() const { return hx > 0 ? bpr() / nb[2] * hx : bpr(); }
 };
 // Device statistics of one run (mirrors spdba_stats, accumulated on the device).
 struct DevStats {

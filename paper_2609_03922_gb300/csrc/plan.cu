@@ -25,6 +25,28 @@ template <typename T> __global__ void real_to_complex_kernel(const T* __restrict
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         c[i] = mk<cx_t<T>>(r[i], (T)0);
 }
+// Full spectrum (N0 x N1 x N2) of a half-stored one (kx = 0 .. N2/2 in rows of
+// NHP entries): kx > N2/2 from X(k) = conj X(-k) (Eq. S.4).
+template <typename T>
+__global__ void half_storage_extend_kernel(const cx_t<T>* __restrict__ h, cx_t<T>* __restrict__ full, int N0, int N1,
+                                           int N2, int NHP) {
+    const long long n = (long long)N0 * N1 * N2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % N2);
+        const long long zy = i / N2;
+        const int y = (int)(zy % N1), z = (int)(zy / N1);
+        cx_t<T> v;
+        if (x <= N2 / 2) {
+            v = h[zy * NHP + x];
+        } else {
+            const int my = y == 0 ? 0 : N1 - y, mz = z == 0 ? 0 : N0 - z;
+            v = h[((long long)mz * N1 + my) * NHP + (N2 - x)];
+            v.y = -v.y;
+        }
+        full[i] = v;
+    }
+}
+
 template <typename T> __global__ void complex_real_part_kernel(const cx_t<T>* __restrict__ c, T* __restrict__ r, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         r[i] = c[i].x;
@@ -130,6 +152,14 @@ template <typename T> struct Group {
     long long pair_list_n = 0;      // capacity of pair_list
     HermTma herm_tma;               // the half form's z inverse with TMA tile copies (complex64)
     bool use_herm_tma = false;
+    // Half-spectrum storage (3-D complex64 CH, S1.2): c_hat holds the stored half
+    // kx = 0 .. N2/2 of the real field's spectrum in rows of hs_nhp entries (the
+    // rest zero), g is the half map (g.hx live x-blocks); the passes run
+    // h_inv_z, h_inv_y, h_nl, h_fwd_y and h_upd (fused) or h_mirror (plain z
+    // forward) + the staged update, all in `work`
+    bool hs = false;
+    long long hs_n = 0;             // elements of the stored half (N0 * N1 * hs_nhp)
+    int64_t hs_nhp = 0;
     bool fused_update = false;      // the last forward pass carries the update (upd_pass)
     bool has_fused = false;         // upd_pass exists (else only the staged form)
     Pass<T> upd_pass;               // forward pass of the first axis with the update fused
@@ -447,9 +477,90 @@ static spdba_status setup_half(spdba_plan* p, Group<float>& r, const int64_t* di
     return SPDBA_OK;
 }
 
+// A 3-D complex64 CH run with half-spectrum storage: the stored half of the
+// spectrum, its block map with conjugate neighbours (S1.2, Eq. S.4), and the
+// transforms between the stored half and the update, all on x frequencies
+// 0 .. N2/2 (rows padded to NHP, a multiple of the y pass tile and of B2).
+static spdba_status group_init_ch_hs(spdba_plan* p, Group<float>& r, const int64_t* dims, const int32_t* block) {
+    cudaStream_t st = p->st;
+    spdba_status s;
+    const int64_t N0 = dims[0], N1 = dims[1], N2 = dims[2];
+    const int B2 = block[2];
+    if (B2 < 1 || N2 % (2 * B2) != 0)
+        return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum storage needs 2 B2 | N2 (B2 = %d, N2 = %lld)", B2,
+                    (long long)N2);
+    const int Py = pass_tile_pencils<float>(N1);
+    if (Py == 0) return fail(SPDBA_ERR_UNSUPPORTED, "no y pass for %lld points", (long long)N1);
+    int64_t q = Py;
+    while (q % B2 != 0) q += Py;   // a multiple of both
+    const int64_t M = N2 / 2;
+    const int64_t NHP = ((M + 1 + q - 1) / q) * q;
+    const int64_t dh[3] = {N0, N1, NHP};
+    if ((s = make_geom(&r.g, 3, dh, block)) != SPDBA_OK) return s;
+    r.g.hx = (int)(M / B2 + 1);
+    r.ndim = 3;
+    r.batch = 1;
+    r.n = N0 * N1 * N2;
+    for (int a = 0; a < 3; ++a) r.dims[a] = dims[a];
+    r.hs = true;
+    r.hs_nhp = NHP;
+    r.hs_n = N0 * N1 * NHP;
+    if (r.hs_n >= 0x7fffffffLL) return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum storage over 2^31 modes");
+    if ((s = group_buffers<float>(p, r)) != SPDBA_OK) return s;
+    for (int ax = 0; ax < 3; ++ax) {
+        std::vector<float> k2 = k2_table<float>(dims[ax], p->opt.dx);
+        if (ax == 2) k2.resize((size_t)NHP, 0.f);   // x frequencies 0 .. N2/2, then padding
+        if ((s = upload(r, &r.k2ax[ax], k2, st)) != SPDBA_OK) return s;
+        if ((s = upload(r, &r.taper[ax], taper_table<float>(r.g.b[ax]), st)) != SPDBA_OK) return s;
+    }
+    TwiddleCache<float>& tw = p->tw32;
+    if ((s = r.fft1.init(3, dims, 1, tw, st)) != SPDBA_OK) return s;
+    HalfGeo hg;
+    hg.N0 = (int)N0; hg.N1 = (int)N1; hg.N2 = (int)N2; hg.NHP = (int)NHP;
+    hg.fd_N2.init((uint32_t)N2);
+    hg.fd_NHP.init((uint32_t)NHP);
+    hg.fd_M.init((uint32_t)M);
+    hg.r2c = 1;
+    if ((s = make_axis_pass<float>(&r.h_inv_z, 3, dh, 1, 0, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+    if ((s = make_axis_pass<float>(&r.h_inv_y, 3, dh, 1, 1, +1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+    if ((s = make_half_pass(&r.h_nl, PASS_NL_HALF, hg, tw, st)) != SPDBA_OK) return s;
+    r.h_nl.p.mass_stride = (int)(sizeof(DevStats) / sizeof(double));
+    if ((s = make_axis_pass<float>(&r.h_fwd_y, 3, dh, 1, 1, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+    if ((s = make_axis_pass<float>(&r.h_mirror, 3, dh, 1, 0, -1, PASS_PLAIN, tw, st)) != SPDBA_OK) return s;
+    Pass<float> up;
+    s = make_axis_pass<float>(&up, 3, dh, 1, 0, -1, PASS_CH_UPDATE, tw, st);
+    // the fused update's tiles must lie within one x row, and its state table fit
+    if (s == SPDBA_OK && NHP % up.P == 0 && (N0 / r.g.b[0]) * (int64_t)upd_table_cols(up.P, r.g.b[2]) <= kUpdTable) {
+        fill_fuse<float>(p, r, up.p.fu);
+        r.h_upd = up;
+        r.has_fused = true;
+        r.fused_update = p->opt.fuse_update != 0;
+    } else if (s != SPDBA_OK && s != SPDBA_ERR_UNSUPPORTED) {
+        return s;
+    }
+    if (tma_update_fits(r.g)) {
+        int per_sm = 0, nsm = 0;
+        if ((s = make_box_map(r.tma_map_c, r.c_hat, r.g)) != SPDBA_OK) return s;
+        if ((s = make_box_map(r.tma_map_g, r.work, r.g)) != SPDBA_OK) return s;
+        if ((s = tma_update_prepare(&per_sm, &nsm)) != SPDBA_OK) return s;
+        r.tma_grid = (long long)per_sm * nsm;
+        r.tma_ok = true;
+        r.use_tma = p->opt.tma_update != 0;
+    }
+    return SPDBA_OK;
+}
+
 template <typename T>
 static spdba_status group_init_ch(spdba_plan* p, Group<T>& r, int ndim, const int64_t* dims, const int32_t* block,
                                   long long batch) {
+    if (p->opt.half_storage) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (ndim != 3 || batch != 1)
+                return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum storage is built for 3-D runs");
+            return group_init_ch_hs(p, r, dims, block);
+        }
+        return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum storage is built for complex64");
+    }
     cudaStream_t st = p->st;
     spdba_status s = ndim == 3 ? make_geom(&r.g, ndim, dims, block)
                                : make_geom_batched(&r.g, ndim, dims, block, batch);
@@ -649,7 +760,7 @@ static spdba_status group_init_rcd(spdba_plan* p, Group<T>& r, int ndim, const i
 template <typename T> static spdba_status group_assess(spdba_plan* p, Group<T>& r) {
     cudaStream_t st = p->st;
     spdba_status s;
-    ProfScope ps(p, K_ASSESS, (double)sizeof(cx_t<T>) * (double)(r.batch * r.n));
+    ProfScope ps(p, K_ASSESS, (double)sizeof(cx_t<T>) * (double)(r.hs ? r.hs_n : r.batch * r.n));
     const bool ch = p->opt.model == SPDBA_MODEL_CH;
     // gmax is zero here: it starts zeroed and every classification zeroes it after use
     double* sumsq = p->opt.measure == SPDBA_MEASURE_ENERGY ? r.sumsq : nullptr;
@@ -725,7 +836,7 @@ static bool all_active_step(const spdba_plan* p, int64_t step) {
 
 // The control decision of a group's runs, before the step's reassessment.
 template <typename T> static spdba_status group_control(spdba_plan* p, Group<T>& r) {
-    control_kernel<<<1, 256, 0, p->st>>>(r.stats, r.batch, r.g.bpr(), p->opt.target_ratio, p->opt.control_eta);
+    control_kernel<<<1, 256, 0, p->st>>>(r.stats, r.batch, r.g.live_bpr(), p->opt.target_ratio, p->opt.control_eta);
     SPDBA_CUDA(cudaGetLastError());
     p->launches += 1;
     return SPDBA_OK;
@@ -763,6 +874,48 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
         }
     }
     const int dense = !adaptive || all_active_step(p, r.step);
+    if (r.hs) {
+        // half-spectrum storage: z, y inverse, x (nonlinearity), y and z forward on
+        // the stored half, then the update (fused into the z forward or staged).
+        // Profiled bytes are algorithmic: x frequencies 0 .. N2/2.
+        const double hb = sizeof(cx_t<T>) * (double)(r.dims[0] * r.dims[1] * (r.dims[2] / 2 + 1));
+        {
+            ProfScope pr(p, K_FFT_PASS, 2.0 * hb);
+            if ((s = launch_pass<T>(r.h_inv_z, r.c_hat, r.work, st)) != SPDBA_OK) return s;
+        }
+        {
+            ProfScope pr(p, K_FFT_PASS, 2.0 * hb);
+            if ((s = launch_pass<T>(r.h_inv_y, r.work, r.work, st)) != SPDBA_OK) return s;
+        }
+        Pass<T> nl = r.h_nl;
+        if (reassess) {
+            nl.p.mass = &r.stats[0].mass;
+            zero_strided_kernel<<<1, 256, 0, st>>>(&r.stats[0].mass, r.batch, nl.p.mass_stride);
+            p->launches += 1;
+        }
+        {
+            ProfScope pr(p, K_FUSED_NL, 2.0 * hb);
+            if ((s = launch_pass<T>(nl, r.work, r.work, st)) != SPDBA_OK) return s;
+        }
+        {
+            ProfScope pr(p, K_FFT_PASS, 2.0 * hb);
+            if ((s = launch_pass<T>(r.h_fwd_y, r.work, r.work, st)) != SPDBA_OK) return s;
+        }
+        p->launches += 5;
+        if (r.fused_update) {
+            Pass<T> ps = r.h_upd;
+            ps.p.fu.dense = dense;
+            ProfScope pr(p, K_FFT_UPDATE, 3.0 * hb);
+            if ((s = launch_pass<T>(ps, r.work, r.work, st)) != SPDBA_OK) return s;
+            r.step += 1;
+            return SPDBA_OK;
+        }
+        {
+            ProfScope pr(p, K_FFT_ZFWD, 2.0 * hb);
+            if ((s = launch_pass<T>(r.h_mirror, r.work, r.work, st)) != SPDBA_OK) return s;
+        }
+        return ch_staged_update<T>(p, r, dense);
+    }
     if (r.use_half) {
         // Hermitian half-spectrum form: z (from c_hat), y, x (nonlinearity), y, z (update).
         // Profiled bytes are algorithmic: x frequencies 0 .. N2/2 of the half array
@@ -1321,6 +1474,16 @@ static spdba_status run_set_field(spdba_plan* p, Group<T>& r, long long sub, con
         SPDBA_CUDA(cudaMemcpyAsync(r.real, src, sizeof(T) * r.n, kind, st));
         real_to_complex_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(r.real, wslot, r.n);
         if ((s = r.fft1.exec(wslot, slot, SPDBA_FORWARD, st)) != SPDBA_OK) return s;
+        if (r.hs) {
+            // keep the half kx = 0 .. N2/2 of the full spectrum, rows padded with zeros
+            const size_t es = sizeof(cx_t<T>);
+            const int64_t N2 = r.dims[2];
+            SPDBA_CUDA(cudaMemsetAsync(r.work, 0, es * (size_t)r.hs_n, st));
+            SPDBA_CUDA(cudaMemcpy2DAsync(r.work, es * (size_t)r.hs_nhp, r.c_hat, es * (size_t)N2,
+                                         es * (size_t)(N2 / 2 + 1), (size_t)(r.dims[0] * r.dims[1]),
+                                         cudaMemcpyDeviceToDevice, st));
+            SPDBA_CUDA(cudaMemcpyAsync(r.c_hat, r.work, es * (size_t)r.hs_n, cudaMemcpyDeviceToDevice, st));
+        }
     } else if (!r.long_nls) {
         SPDBA_CUDA(cudaMemcpyAsync(wslot, src, sizeof(cx_t<T>) * r.n, kind, st));
         if ((s = r.fft1.exec(wslot, slot, SPDBA_FORWARD, st)) != SPDBA_OK) return s;
@@ -1358,7 +1521,13 @@ static spdba_status run_get_field(spdba_plan* p, Group<T>& r, long long sub, voi
         complex_real_part_kernel<T><<<grid_for(tot, 256), 256, 0, st>>>(r.work, r.real, tot);
         SPDBA_CUDA(cudaMemcpyAsync(dst, r.real, sizeof(T) * tot, kind, st));
     } else if (p->opt.model == SPDBA_MODEL_CH) {
-        if ((s = r.fft1.exec(slot, wslot, SPDBA_INVERSE, st)) != SPDBA_OK) return s;
+        if (r.hs) {
+            half_storage_extend_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(
+                r.c_hat, r.work, (int)r.dims[0], (int)r.dims[1], (int)r.dims[2], (int)r.hs_nhp);
+            if ((s = r.fft1.exec(r.work, wslot, SPDBA_INVERSE, st)) != SPDBA_OK) return s;
+        } else if ((s = r.fft1.exec(slot, wslot, SPDBA_INVERSE, st)) != SPDBA_OK) {
+            return s;
+        }
         complex_real_part_kernel<T><<<grid_for(r.n, 256), 256, 0, st>>>(wslot, r.real, r.n);
         SPDBA_CUDA(cudaMemcpyAsync(dst, r.real, sizeof(T) * r.n, kind, st));
     } else if (!r.long_nls) {
@@ -1386,6 +1555,23 @@ static spdba_status copy_spectrum(spdba_plan* p, Group<T>& r, long long sub, voi
     cx_t<T>* slot = r.c_hat + sub * r.n;
     cx_t<T>* wslot = r.work + sub * r.n;
     spdba_status s;
+    if (r.hs) {
+        // the stored half, N0 * N1 rows of N2/2 + 1 entries (rows of hs_nhp on the device)
+        const size_t es = sizeof(cx_t<T>);
+        const size_t w = es * (size_t)(r.dims[2] / 2 + 1), pitch = es * (size_t)r.hs_nhp;
+        const size_t rows = (size_t)(r.dims[0] * r.dims[1]);
+        if (get) {
+            SPDBA_CUDA(cudaMemcpy2DAsync(buf, w, r.c_hat, pitch, w, rows,
+                                         on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+            SPDBA_CUDA(cudaStreamSynchronize(st));
+        } else {
+            SPDBA_CUDA(cudaMemsetAsync(r.c_hat, 0, es * (size_t)r.hs_n, st));
+            SPDBA_CUDA(cudaMemcpy2DAsync(r.c_hat, pitch, buf, w, w, rows,
+                                         on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+            r.assessed = false;
+        }
+        return SPDBA_OK;
+    }
     if (get) {
         const cx_t<T>* from = slot;
         if (r.long_nls) {
@@ -1473,6 +1659,9 @@ static spdba_status check_opts(const spdba_options* o, int ndim) {
     if (o->tau_rule != SPDBA_TAU_REL_MAX && o->tau_rule != SPDBA_TAU_ABS) return fail(SPDBA_ERR_ARG, "bad tau rule");
     if (o->refresh_every < 0 || o->warmup_steps < 0) return fail(SPDBA_ERR_ARG, "negative refresh/warm-up");
     if (o->multi_pass < 0 || o->multi_pass > 2) return fail(SPDBA_ERR_ARG, "multi_pass must be 0, 1 or 2");
+    if (o->half_storage < 0 || o->half_storage > 1) return fail(SPDBA_ERR_ARG, "half_storage must be 0 or 1");
+    if (o->half_storage && (o->model != SPDBA_MODEL_CH || ndim != 3))
+        return fail(SPDBA_ERR_UNSUPPORTED, "half-spectrum storage is built for 3-D Cahn-Hilliard plans");
     if (o->model == SPDBA_MODEL_CH && (ndim < 2 || ndim > 3)) return fail(SPDBA_ERR_UNSUPPORTED, "CH plans are 2-D or 3-D");
     if (o->model == SPDBA_MODEL_NLS && ndim != 1) return fail(SPDBA_ERR_UNSUPPORTED, "NLS plans are 1-D");
     return SPDBA_OK;
@@ -1692,8 +1881,8 @@ static std::map<std::string, TunedConfig>& tune_cache() {
 static std::string plan_signature(spdba_plan* p) {
     std::string k;
     char buf[96];
-    snprintf(buf, sizeof buf, "p%d m%d md%d f%d h%d s%d|", p->precision, p->opt.model, p->opt.mode,
-             p->opt.fuse_update, p->opt.half_spectrum, p->st == 0 ? 0 : 1);
+    snprintf(buf, sizeof buf, "p%d m%d md%d f%d h%d hs%d s%d|", p->precision, p->opt.model, p->opt.mode,
+             p->opt.fuse_update, p->opt.half_spectrum, p->opt.half_storage, p->st == 0 ? 0 : 1);
     k += buf;
     auto add_groups = [&](auto& gs) {
         for (auto& g : gs) {
@@ -1849,6 +2038,9 @@ extern "C" spdba_status spdba_plan_get_config(const spdba_plan* p, spdba_options
     out->half_spectrum = half;
     out->tma_update = tma;
     out->tma_passes = tmap;
+    int hs = 0;
+    for (auto& g : p->g32) hs |= g->hs ? 1 : 0;
+    out->half_storage = hs;
     out->multi_pass = p->multi_sel;
     return SPDBA_OK;
 }
@@ -1874,6 +2066,15 @@ extern "C" spdba_status spdba_set_spectrum(spdba_plan* p, int32_t run, const voi
 
 template <typename T>
 static spdba_status get_mask_t(spdba_plan* p, Group<T>& r, long long sub, uint8_t* dst, int64_t nb) {
+    if (r.hs) {
+        // the half map's live x-blocks, row by row
+        if (nb != r.g.live_bpr())
+            return fail(SPDBA_ERR_ARG, "mask size %lld != %lld blocks", (long long)nb, r.g.live_bpr());
+        SPDBA_CUDA(cudaMemcpy2DAsync(dst, (size_t)r.g.hx, r.states, (size_t)r.g.nb[2], (size_t)r.g.hx,
+                                     (size_t)(r.g.nb[0] * r.g.nb[1]), cudaMemcpyDeviceToHost, p->st));
+        SPDBA_CUDA(cudaStreamSynchronize(p->st));
+        return SPDBA_OK;
+    }
     if (nb != r.g.bpr()) return fail(SPDBA_ERR_ARG, "mask size %lld != %lld blocks", (long long)nb, r.g.bpr());
     SPDBA_CUDA(cudaMemcpyAsync(dst, r.states + sub * r.g.bpr(), (size_t)nb, cudaMemcpyDeviceToHost, p->st));
     SPDBA_CUDA(cudaStreamSynchronize(p->st));
@@ -1892,7 +2093,7 @@ template <typename T> static spdba_status get_stats_t(spdba_plan* p, Group<T>& r
     SPDBA_CUDA(cudaStreamSynchronize(p->st));
     out->step = r.step;
     out->assessments = (int64_t)d.assessments;
-    out->nblocks = r.g.bpr();
+    out->nblocks = r.g.live_bpr();
     out->n_active = (int64_t)d.n_active;
     out->n_transition = (int64_t)d.n_transition;
     out->tau = d.tau;
@@ -1982,6 +2183,13 @@ static spdba_status get_activity_t(spdba_plan* p, Group<T>& r, long long sub, do
     // with a predictor attached, the last exact scan is kept in the snapshot
     const double* src = r.has_snap ? r.snap_maxsq : r.maxsq;
     const double* tsrc = r.has_snap ? r.snap_tau : r.tau;
+    if (maxsq && r.hs) {
+        // the half map's live x-blocks, row by row
+        const size_t es = sizeof(double);
+        SPDBA_CUDA(cudaMemcpy2DAsync(maxsq, es * (size_t)r.g.hx, src, es * (size_t)r.g.nb[2], es * (size_t)r.g.hx,
+                                     (size_t)(r.g.nb[0] * r.g.nb[1]), kind, p->st));
+        maxsq = nullptr;
+    }
     if (maxsq) SPDBA_CUDA(cudaMemcpyAsync(maxsq, src + sub * bpr, sizeof(double) * bpr, kind, p->st));
     if (tau) SPDBA_CUDA(cudaMemcpyAsync(tau, tsrc + sub, sizeof(double), kind, p->st));
     SPDBA_CUDA(cudaStreamSynchronize(p->st));
@@ -2001,6 +2209,7 @@ template <typename T> static spdba_status attach_t(spdba_plan* p, spdba_predicto
     if (p->opt.target_ratio > 0)
         return fail(SPDBA_ERR_STATE, "a predictor does not attach to a plan under dynamic threshold control");
     Group<T>& r = *gs[0];
+    if (r.hs) return fail(SPDBA_ERR_UNSUPPORTED, "a predictor attaches to a plan with full-spectrum storage");
     if (!spdba_predictor_map_matches(pr, r.g.nb[0], r.g.nb[1], r.g.nb[2]))
         return fail(SPDBA_ERR_ARG, "predictor block map does not match the plan's");
     const long long nb = r.g.blocks();

@@ -84,7 +84,7 @@ __global__ void ch_list_kernel(Geom g, CHUpdateArgs<T> a, FastDiv fd_h, FastDiv 
     const int B0 = g.b[0], B1 = g.b[1], B2 = g.b[2];
     const long long nmodes = (long long)B0 * B1 * B2;
     if (blockIdx.x == 0 && a.stats) {
-        const double inv = 1.0 / (double)g.bpr();
+        const double inv = 1.0 / (double)g.live_bpr();
         for (long long r = threadIdx.x; r < g.runs(); r += blockDim.x) {
             const unsigned long long nfi = a.stats[r].n_active + a.stats[r].n_transition;
             double nf = (double)nfi;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) ch_list8_kernel(Geom g, CHUpdateArgs<floa
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
         const unsigned long long nfi = a.stats[0].n_active + a.stats[0].n_transition;
         const double nf = (double)nfi;
-        a.stats[0].ratio_sum += nf * (1.0 / (double)g.bpr());
+        a.stats[0].ratio_sum += nf * (1.0 / (double)g.live_bpr());
         a.stats[0].list_modes += nf * (double)(B * B * B);
         a.stats[0].ctl_nf += nfi;       // an adaptive step of the control interval
         a.stats[0].ctl_steps += 1;

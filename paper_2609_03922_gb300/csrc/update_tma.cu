@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(TMA_NT) ch_list_tma_kernel(const __grid_consta
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
         const unsigned long long nfi = a.stats[0].n_active + a.stats[0].n_transition;
         const double nf = (double)nfi;
-        a.stats[0].ratio_sum += nf * (1.0 / (double)g.bpr());
+        a.stats[0].ratio_sum += nf * (1.0 / (double)g.live_bpr());
         a.stats[0].list_modes += nf * (double)TMA_BOX_MODES;
         a.stats[0].ctl_nf += nfi;
         a.stats[0].ctl_steps += 1;

@@ -36,7 +36,8 @@ class spdba_options(ctypes.Structure):
                 ("rcd_d_diag", ctypes.c_double), ("rcd_d_cross", ctypes.c_double), ("rcd_alpha", ctypes.c_double),
                 ("rcd_beta", ctypes.c_double), ("rcd_r", ctypes.c_double), ("rcd_a", ctypes.c_double),
                 ("tma_update", ctypes.c_int32), ("multi_pass", ctypes.c_int32),
-                ("tma_passes", ctypes.c_int32)]
+                ("tma_passes", ctypes.c_int32),
+                ("half_storage", ctypes.c_int32)]
 
 
 class spdba_stats(ctypes.Structure):
@@ -253,9 +254,17 @@ class Plan:
         check(lib().spdba_get_field(self._p, run, p, dev))
         return out
 
+    def spectrum_shape(self, run=0):
+        """Shape of a run's stored spectrum: with half-spectrum storage the last axis
+        keeps x frequencies 0 .. N2/2."""
+        shape = self.field_shape(run)
+        if self.opts.half_storage:
+            shape = shape[:-1] + (shape[-1] // 2 + 1,)
+        return shape
+
     def get_spectrum(self, out=None, run=0):
         if out is None:
-            out = np.empty(self.field_shape(run), dtype=self.complex_dtype)
+            out = np.empty(self.spectrum_shape(run), dtype=self.complex_dtype)
         p, dev = _ptr(out)
         check(lib().spdba_get_spectrum(self._p, run, p, dev))
         return out
@@ -267,7 +276,10 @@ class Plan:
     def nblocks_shape(self, run=0):
         if self.opts.model == SPDBA_MODEL_NLS and self.block[0] <= 0:
             return (-self.block[0],)
-        return tuple(d // b for d, b in zip(self.run_dims[run], self.block))
+        shape = tuple(d // b for d, b in zip(self.run_dims[run], self.block))
+        if self.opts.half_storage:
+            shape = shape[:-1] + (self.run_dims[run][-1] // (2 * self.block[-1]) + 1,)
+        return shape
 
     def get_mask(self, run=0):
         shape = self.nblocks_shape(run)
