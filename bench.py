@@ -64,34 +64,30 @@ def prof_every(k):
 
 
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels
-# on the 256^3 field, one launch each at step 505 of the staged half-spectrum
-# run (cold L2 at the start of each launch; profiles/ch3d256_step_kernels.md):
+# on the 256^3 field with half-spectrum storage, one launch each at step 505 of
+# the staged run (cold L2 at the start of each launch;
+# profiles/ch3d256_half_storage_step_kernels.md):
 TOUCHED_BYTES = {
-    # z forward + fused update of the half-spectrum form (an early, mostly active step): 250.95 MB read, 87.26 MB written
-    "fft_update": 250.95e6 + 87.26e6,
-    # paired z forward of the staged form with block states: 52.03 MB read, 6.57 MB written
-    "fft_z_forward": 52.03e6 + 6.57e6,
-    # x pass (two real rows per transform): 75.53 MB read, 14.72 MB written
-    "fft_fused_nl": 75.53e6 + 14.72e6,
-    # list-driven update (per-warp loads): 82.58 MB read, 4.32 MB written
-    "update_list": 82.58e6 + 4.32e6,
-    # y forward pruned to the live x-frequency columns: 58.78 MB read, 4.07 MB written
-    "fft_y_forward_pruned": 58.78e6 + 4.07e6,
-    # z inverse (TMA tiles) 149.88 + 37.45 and y inverse 75.55 + 14.80 MB, averaged (the staged form's plain passes)
-    "fft_pass": (149.88e6 + 37.45e6 + 75.55e6 + 14.80e6) / 2,
-    # activity scan (rows kernel, per-lane screen): 134.25 MB read, 3.30 MB written
-    "assess": 134.25e6 + 3.30e6,
+    # x pass (two real rows per transform): 75.53 MB read, 14.34 MB written
+    "fft_fused_nl": 75.53e6 + 14.34e6,
+    # z inverse 75.56 + 20.36 MB and y inverse 75.55 + 11.44 MB on the stored half, averaged
+    "fft_pass": (75.56e6 + 20.36e6 + 75.55e6 + 11.44e6) / 2,
+    # y forward pruned to the live x columns: 58.78 MB read, 2.29 MB written
+    "fft_y_forward_pruned": 58.78e6 + 2.29e6,
+    # z forward pruned to the live z pencils: 38.63 MB read, 0.12 MB written (its output stays in L2
+    # for the list update)
+    "fft_z_forward": 38.63e6 + 0.12e6,
+    # list-driven update of the half map's non-frozen blocks: 41.67 MB read, 0.02 MB written
+    "update_list": 41.67e6 + 0.02e6,
 }
 TOUCHED_NOTE = {
-    "fft_update": "ncu DRAM read + write of one launch (an early, mostly active step)",
-    "fft_z_forward": "ncu DRAM read + write of one launch at step 505 (cold L2; part of the output is still in L2 "
-                     "when the launch ends)",
     "fft_fused_nl": "ncu DRAM read + write of one launch at step 505 (cold L2)",
-    "update_list": "ncu DRAM read + write of one launch at step 505",
-    "fft_y_forward_pruned": "ncu DRAM read + write of one launch at step 505",
-    "fft_pass": "ncu DRAM read + write per launch, averaged over the z inverse and the y inverse (cold L2)",
-    "assess": "ncu DRAM read + write of one scan at step 510 (the scan launch only; the classification's three "
-              "small launches are in the same kind)",
+    "fft_pass": "ncu DRAM read + write per launch at step 505, averaged over the z inverse and the y inverse "
+                "(cold L2)",
+    "fft_y_forward_pruned": "ncu DRAM read + write of one launch at step 505 (cold L2)",
+    "fft_z_forward": "ncu DRAM read + write of one launch at step 505 (cold L2)",
+    "update_list": "ncu DRAM read + write of one launch at step 505 (cold L2; most writes leave the launch "
+                   "in L2)",
 }
 CONTROL_TARGETS = (0.05, 0.1, 0.2)   # dynamic threshold control targets (S1.3: 5-20 %)
 CONTROL_EVERY = 50                   # control interval (S3.2, S4.2, S5.3)
@@ -260,9 +256,11 @@ def run_ours(args, rank, world, local_rank, parity=None):
     def max_over_ranks(v):
         return replica_max(v, dev) if dist else v
 
-    def make(mode, fuse, **kw):
+    def make(mode, fuse, hs=1, **kw):
+        """A plan of the workload; hs = 1: the spectrum stored as its half with the block
+        map on that half (S1.2), the form the line reports; 0: the full spectrum."""
         return spdba.Plan(DIMS, BLOCK, threshold=THRESHOLD, reassess=REASSESS, precision=spdba.SPDBA_C64,
-                          mode=mode, dt=DT, kappa=KAPPA, fuse_update=fuse, **kw)
+                          mode=mode, dt=DT, kappa=KAPPA, fuse_update=fuse, half_storage=hs, **kw)
 
     def prepare(plan):
         """From c0 to step TUNE_AT (blocks have frozen there), where the plan's
@@ -281,7 +279,7 @@ def run_ours(args, rank, world, local_rank, parity=None):
         for s in starts:
             plan.step(s - at)
             at = s
-            snap = torch.empty(DIMS, dtype=torch.complex64, device=dev)
+            snap = torch.empty(plan.spectrum_shape(), dtype=torch.complex64, device=dev)
             plan.get_spectrum(snap)
             snaps.append(snap)
         return tune, snaps
@@ -401,6 +399,35 @@ def run_ours(args, rank, world, local_rank, parity=None):
     rel_ada_dense = float(((field_ada.double() - field_dense.double()).norm() / field_dense.double().norm()).item())
     dense.close()
 
+    # ---- the same workload with the full spectrum stored (block map on the full
+    # spectrum): the same windows and whole runs, each plan autotuned at step TUNE_AT
+    full_form = {}
+    f_fields = {}
+    for name, mode in (("adaptive", spdba.SPDBA_MODE_ADAPTIVE), ("dense", spdba.SPDBA_MODE_REGULAR)):
+        pl = make(mode, 1, hs=0)
+        tune_f, snap_f = prepare(pl)
+        ms_w, _, _, _ = window(pl, snap_f)
+        ms_run, _ = full_run(pl)
+        st_f = pl.get_stats()
+        f_f = torch.empty(DIMS, dtype=torch.float32, device=dev)
+        pl.get_field(f_f)
+        f_fields[name] = f_f
+        full_form[name] = {"steps_per_s": replica_throughput(K, ms_w, world),
+                           "full_run_steps_per_s": world * FULL_RUN / (ms_run / 1e3),
+                           "mean_nonfrozen_ratio": st_f["active_ratio_sum"] / max(1, st_f["step"]),
+                           "autotune_chosen": tune_f["candidates"][tune_f["chosen"]]}
+        pl.close()
+        del snap_f
+    fd_ = f_fields["dense"].double()
+    full_form["rel_l2_adaptive_vs_dense"] = float(((f_fields["adaptive"].double() - fd_).norm() / fd_.norm()).item())
+    full_form["rel_l2_dense_vs_half_storage_dense"] = float(
+        ((fd_ - field_dense.double()).norm() / field_dense.double().norm()).item())
+    full_form["adaptive_over_dense"] = full_form["adaptive"]["steps_per_s"] / full_form["dense"]["steps_per_s"]
+    full_form["note"] = ("c_hat stored as the full complex spectrum, block map on it (transforms on the Hermitian "
+                         "half); same windows (%d steps from the states at steps %s) and whole %d-step runs"
+                         % (K, snapshot_steps(K), FULL_RUN))
+    del f_fields, fd_
+
     # ---- dynamic threshold control (the paper's comparison mode): whole runs at
     # fixed target shares of non-frozen blocks, against the dense run
     control = {}
@@ -475,7 +502,7 @@ def run_ours(args, rank, world, local_rank, parity=None):
         ada.get_field(f)
         mask = ada.get_mask()
         with spdba.Plan(PARITY_SMALL, BLOCK, threshold=THRESHOLD, reassess=REASSESS, precision=spdba.SPDBA_C64,
-                        dt=DT, kappa=KAPPA) as sm:
+                        dt=DT, kappa=KAPPA, half_storage=1) as sm:
             c0s = W.ch_initial_condition(PARITY_SMALL, mean=MEAN, amplitude=AMP, seed=W.BASE_SEED).astype(np.float32)
             sm.set_field(c0s)
             sm.step(FULL_RUN)
@@ -501,17 +528,16 @@ def run_ours(args, rank, world, local_rank, parity=None):
             l = max(1, v["launches"])
             t_s = v["total_ms"] / l / 1e3
             alg = v["bytes"] / l
-            if k == "fft_z_forward":
-                alg = 8.0 * n_half + 8.0 * n * ratio
-                dense_b = 8.0 * n_half + 8.0 * n
-            elif k == "fft_update":
-                alg = 8.0 * n_half + 16.0 * n * ratio
-                dense_b = 8.0 * n_half + 16.0 * n
+            if k == "fft_update":
+                # reads the y forward's output, reads and writes c_hat of the non-frozen blocks
+                alg = 8.0 * n_half + 16.0 * n_half * ratio
+                dense_b = 24.0 * n_half
             elif k == "update_list":
-                dense_b = 24.0 * n
-            elif k == "fft_y_forward_pruned":
-                # the y forward of the staged form skips dead x-frequency columns: the
-                # profile records its dense bytes; the moved share is not known on the host
+                dense_b = 24.0 * n_half
+            elif k in ("fft_y_forward_pruned", "fft_z_forward"):
+                # the forward passes of adaptive steps skip the x columns / z pencils no
+                # non-frozen block reads: the profile records their dense bytes; the moved
+                # share is not known on the host
                 dense_b = alg
                 alg = None
             else:
@@ -540,14 +566,12 @@ def run_ours(args, rank, world, local_rank, parity=None):
                 "algorithmic_bytes_per_launch": v["algorithmic_bytes"],
                 "avg_us": v["avg_us"]}
 
-    half = bool(tune["candidates"][tune["chosen"]]["half_spectrum"])
-    labels = {"fft_update": "z forward FFT pass + fused CH update (L=256, c64)",
-              "fft_z_forward": "z forward FFT pass, paired half pencils (L=256, c64)",
-              "update_list": "list-driven CH update of the non-frozen blocks (c64)",
-              "fft_fused_nl": ("x pass: two real rows per transform, c^3 - c (L=256, c64)" if half
-                               else "x pass: inverse, c^3 - c, forward (L=256, c64)"),
-              "fft_pass": "FFT passes (z inverse, y inverse, and y forward where not pruned; Stockham, L=256, c64)",
-              "assess": "activity scan + classification (every R steps)"}
+    labels = {"fft_update": "z forward FFT pass on the stored half + fused CH update (L=256, c64)",
+              "fft_z_forward": "z forward FFT pass on the stored half, pruned to live pencils (L=256, c64)",
+              "update_list": "list-driven CH update of the half map's non-frozen blocks (c64)",
+              "fft_fused_nl": "x pass: two real rows per transform, c^3 - c (L=256, c64)",
+              "fft_pass": "FFT passes on the stored half (z inverse, y inverse; Stockham, L=256, c64)",
+              "assess": "activity scan of the stored half + classification on the half map (every R steps)"}
     roofs = {k: roof(k, kinds, lab) for k, lab in labels.items()}
     # the dominant kernel: the longest average launch among the step's kernels that run once per step
     cands = [(kinds[k]["avg_us"], roofs[k]) for k in ("fft_update", "fft_z_forward", "update_list", "fft_fused_nl")
@@ -575,7 +599,10 @@ def run_ours(args, rank, world, local_rank, parity=None):
                    "reassess": REASSESS, "dt": DT, "kappa": KAPPA, "ic": "0.1+U[-0.05,0.05] seed 1234",
                    "timed": ("%d steps from each of the run's states at steps %s (plans autotuned at step %d); "
                              "mean per window, the set repeated %d times, median" % (K, starts, TUNE_AT, reps_ada)),
-                   "l2": "working set larger than L2 (c_hat 134 MB + half-spectrum workspace 75 MB per replica)",
+                   "l2": "working set larger than L2 (stored half 75.5 MB + workspace 75.5 MB per replica, "
+                         "L2 129 MB)",
+                   "spectrum_storage": "half: x frequencies 0 .. N/2, block map on the half with conjugate "
+                                       "neighbour activation (S1.2, Eq. S.4)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "dense_steps_per_s": dense_value,
         "adaptive_over_dense": value / dense_value,
@@ -588,6 +615,7 @@ def run_ours(args, rank, world, local_rank, parity=None):
                      "rel_l2_adaptive_vs_dense": rel_ada_dense,
                      "kernels": kinds_full,
                      "note": "each plan in the configuration its autotuner chose at step %d" % TUNE_AT},
+        "full_storage_form": full_form,
         "threshold_control": {"targets": control, "control_every": CONTROL_EVERY, "eta": CONTROL_ETA,
                               "initial_threshold": THRESHOLD,
                               "note": "dynamic threshold control (S1.3); whole %d-step runs from c0, each plan "
@@ -622,10 +650,11 @@ def run_ours(args, rank, world, local_rank, parity=None):
 
 # ------------------------------------------------------------------ the oracle (CPU baseline and parity)
 def oracle_job(full_steps, small_dims, small_steps, threads):
-    """The FP64 CPU oracle on the same workload, in a process of its own: the
-    first `full_steps` adaptive steps of the 256^3 run from c0 (timed: the CPU
-    baseline), then the whole run at `small_dims` (same parameters) for the
-    parity of a full run.  Returns the oracle's fields and last block states."""
+    """The FP64 CPU oracle on the same workload (half-spectrum storage, block map
+    on the half), in a process of its own: the first `full_steps` adaptive steps
+    of the 256^3 run from c0 (timed: the CPU baseline), then the whole run at
+    `small_dims` (same parameters) for the parity of a full run.  Returns the
+    oracle's fields and last block states."""
     os.environ["OMP_NUM_THREADS"] = str(threads)
     import oracle as O
     import workloads as W
@@ -636,9 +665,9 @@ def oracle_job(full_steps, small_dims, small_steps, threads):
         c0 = W.ch_initial_condition(dims, mean=MEAN, amplitude=AMP, seed=W.BASE_SEED).astype(np.float32)
         cfg = O.CHConfig(dims, BLOCK, threshold=THRESHOLD, reassess=REASSESS, dt=DT, kappa=KAPPA)
         t0 = time.perf_counter()
-        c_hat, hist = O.run_ch(c0.astype(np.float64), cfg, steps)
+        h, hist = O.run_ch_half(c0.astype(np.float64), cfg, steps)
         el = time.perf_counter() - t0
-        out[key] = {"field": O.ch_real_field(c_hat), "mask": hist[-1][1], "steps": steps, "seconds": el}
+        out[key] = {"field": O.ch_real_field_half(h, dims), "mask": hist[-1][1], "steps": steps, "seconds": el}
     out["cores"] = O.num_threads()
     return out
 
@@ -670,9 +699,9 @@ def run_reference(args, rank, world):
     c0 = W.ch_initial_condition(DIMS, mean=MEAN, amplitude=AMP, seed=W.BASE_SEED).astype(np.float32)
     cfg = O.CHConfig(DIMS, BLOCK, threshold=THRESHOLD, reassess=REASSESS, dt=DT, kappa=KAPPA)
     if warm:
-        O.run_ch(c0.astype(np.float64), cfg, warm)   # untimed warm-up steps (same work, from c0)
+        O.run_ch_half(c0.astype(np.float64), cfg, warm)   # untimed warm-up steps (same work, from c0)
     t0 = time.perf_counter()
-    O.run_ch(c0.astype(np.float64), cfg, steps)
+    O.run_ch_half(c0.astype(np.float64), cfg, steps)
     el = time.perf_counter() - t0
     v = steps / el
     cores = O.num_threads()
@@ -681,7 +710,8 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(DIMS), "block": list(BLOCK)},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": "first %d adaptive steps of the 256^3 run from c0 (FP64 oracle)" % steps},
+                             "sample": "first %d adaptive steps of the 256^3 run from c0 (FP64 oracle, "
+                                       "half-spectrum storage)" % steps},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
             unsigned mask = 0;
 #pragma unroll
             for (int k = 0; k < 2 * K2; ++k)
-                if (p32[k] >= cut) mask |= 1u << k;
+                if (p32[k] >= cut && nonzero_mode(v[k])) mask |= 1u << k;   // exact zeros cannot raise the max
             while (mask) {
                 const int i = __ffs(mask) - 1;
                 mask &= mask - 1;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) block_activity_kernel(Geom g, const cx_t<
 #pragma unroll
                 for (int k = 1; k < 2 * K2; ++k)
                     if (i == k) c = v[k];
-                if (nonzero_mode(c)) mxnd = fmax(mxnd, mode_sq(c));
+                mxnd = fmax(mxnd, mode_sq(c));
             }
         }
         mx = fmax(mxnd, Ddc);
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
         unsigned mask = 0;
 #pragma unroll
         for (int k = 0; k < 2 * U; ++k)
-            if (p[k] >= cut) mask |= 1u << k;
+            if (p[k] >= cut && nonzero_mode(v[k])) mask |= 1u << k;   // exact zeros (padding) cannot raise the max
         while (mask) {
             const int i = __ffs(mask) - 1;
             mask &= mask - 1;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(ROWACT_NT) block_activity_rows_kernel(Geom g, 
 #pragma unroll
             for (int k = 1; k < 2 * U; ++k)
                 if (i == k) c = v[k];
-            if (nonzero_mode(c)) D = fmax(D, mode_sq(c));
+            D = fmax(D, mode_sq(c));
         }
     }
     // combine the G lanes of one block (aligned lane groups), then the row groups

@@ -142,6 +142,36 @@ __global__ void __launch_bounds__(1024) half_col_live_kernel(const uint8_t* __re
     }
 }
 
+// Pencil liveness of the half-spectrum storage form under the half map's
+// states: zlive[y * NHP + x] = some block of z pencil (y, x) is not FROZEN
+// (the z forward's outputs are read only by the update of non-frozen blocks);
+// xlive[x] = some z pencil of column x is live (the y forward's outputs in the
+// other columns are read by no live z pencil).  xlive is zero on entry.
+__global__ void __launch_bounds__(256) hs_live_kernel(const uint8_t* __restrict__ states, int nb0, int nb1, int nb2,
+                                                      int B1, int B2, int N1, int NHP, uint8_t* __restrict__ zlive,
+                                                      uint8_t* __restrict__ xlive) {
+    const long long n = (long long)N1 * NHP;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / NHP), x = (int)(i - (long long)y * NHP);
+        const long long b0 = (long long)(y / B1) * nb2 + x / B2;
+        unsigned live = 0;
+#pragma unroll 8
+        for (int bz = 0; bz < nb0; ++bz) live |= states[(long long)bz * nb1 * nb2 + b0];
+        zlive[i] = live != 0;
+        if (live) xlive[x] = 1;
+    }
+}
+
+spdba_status launch_hs_live(const Geom& g, const uint8_t* states, uint8_t* zlive, uint8_t* xlive, cudaStream_t st) {
+    const long long n = g.n[1] * g.n[2];
+    SPDBA_CUDA(cudaMemsetAsync(xlive, 0, (size_t)g.n[2], st));
+    const long long grid = std::min<long long>((n + 255) / 256, 152 * 8);
+    hs_live_kernel<<<(unsigned)grid, 256, 0, st>>>(states, (int)g.nb[0], (int)g.nb[1], (int)g.nb[2], g.b[1], g.b[2],
+                                                   (int)g.n[1], (int)g.n[2], zlive, xlive);
+    SPDBA_CUDA(cudaGetLastError());
+    return SPDBA_OK;
+}
+
 spdba_status launch_half_col_live(const Geom& g, const uint8_t* states, int N2, int NHP, uint8_t* col_live,
                                   cudaStream_t st) {
     if (g.nb[2] > 64) return fail(SPDBA_ERR_UNSUPPORTED, "more than 64 block columns");

@@ -87,6 +87,9 @@ spdba_status launch_pair_live_list(const Pass<float>& ps, int* list, int* count,
 // Live x-frequency columns of the half array for the paired z forward (one
 // byte per column, NHP of them) from a single 3-D run's block states.
 
+// Half-spectrum storage: live z pencils (zlive, N1 x NHP) and x columns (xlive,
+// NHP) of the stored half under the half map's states (g: that map).
+spdba_status launch_hs_live(const Geom& g, const uint8_t* states, uint8_t* zlive, uint8_t* xlive, cudaStream_t st);
 spdba_status launch_half_col_live(const Geom& g, const uint8_t* states, int N2, int NHP, uint8_t* col_live,
                                   cudaStream_t st);
 // Tiles of a paired z forward pass.

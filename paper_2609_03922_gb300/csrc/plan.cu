@@ -160,6 +160,8 @@ template <typename T> struct Group {
     bool hs = false;
     long long hs_n = 0;             // elements of the stored half (N0 * N1 * hs_nhp)
     int64_t hs_nhp = 0;
+    uint8_t* hs_zlive = nullptr;    // live z pencils (N1 * hs_nhp) and x columns (hs_nhp) under the states:
+    uint8_t* hs_xlive = nullptr;    // the z and y forward passes skip the rest on adaptive steps
     bool fused_update = false;      // the last forward pass carries the update (upd_pass)
     bool has_fused = false;         // upd_pass exists (else only the staged form)
     Pass<T> upd_pass;               // forward pass of the first axis with the update fused
@@ -538,6 +540,10 @@ static spdba_status group_init_ch_hs(spdba_plan* p, Group<float>& r, const int64
     } else if (s != SPDBA_OK && s != SPDBA_ERR_UNSUPPORTED) {
         return s;
     }
+    if ((s = r.alloc(&r.hs_zlive, (size_t)(N1 * NHP))) != SPDBA_OK) return s;
+    if ((s = r.alloc(&r.hs_xlive, (size_t)NHP)) != SPDBA_OK) return s;
+    SPDBA_CUDA(cudaMemsetAsync(r.hs_zlive, 1, (size_t)(N1 * NHP), st));
+    SPDBA_CUDA(cudaMemsetAsync(r.hs_xlive, 1, (size_t)NHP, st));
     if (tma_update_fits(r.g)) {
         int per_sm = 0, nsm = 0;
         if ((s = make_box_map(r.tma_map_c, r.c_hat, r.g)) != SPDBA_OK) return s;
@@ -871,6 +877,10 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
                     return s;
                 p->launches += 1;
             }
+            if (r.hs_zlive) {
+                if ((s = launch_hs_live(r.g, r.states, r.hs_zlive, r.hs_xlive, st)) != SPDBA_OK) return s;
+                p->launches += 1;
+            }
         }
     }
     const int dense = !adaptive || all_active_step(p, r.step);
@@ -898,8 +908,12 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
             if ((s = launch_pass<T>(nl, r.work, r.work, st)) != SPDBA_OK) return s;
         }
         {
-            ProfScope pr(p, K_FFT_PASS, 2.0 * hb);
-            if ((s = launch_pass<T>(r.h_fwd_y, r.work, r.work, st)) != SPDBA_OK) return s;
+            // adaptive steps: the y forward skips the x columns and the z forward
+            // the z pencils that no non-frozen block reads (outputs never used)
+            Pass<T> yf = r.h_fwd_y;
+            if (!dense) yf.p.col_live = r.hs_xlive;
+            ProfScope pr(p, dense ? K_FFT_PASS : K_FFT_YFWD, 2.0 * hb);
+            if ((s = launch_pass<T>(yf, r.work, r.work, st)) != SPDBA_OK) return s;
         }
         p->launches += 5;
         if (r.fused_update) {
@@ -911,8 +925,10 @@ template <typename T> static spdba_status group_ch_step(spdba_plan* p, Group<T>&
             return SPDBA_OK;
         }
         {
+            Pass<T> zf = r.h_mirror;
+            if (!dense) zf.p.col_live = r.hs_zlive;
             ProfScope pr(p, K_FFT_ZFWD, 2.0 * hb);
-            if ((s = launch_pass<T>(r.h_mirror, r.work, r.work, st)) != SPDBA_OK) return s;
+            if ((s = launch_pass<T>(zf, r.work, r.work, st)) != SPDBA_OK) return s;
         }
         return ch_staged_update<T>(p, r, dense);
     }

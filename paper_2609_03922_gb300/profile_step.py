@@ -9,6 +9,8 @@ library's kernels; this module only drives the plan.
 
 Example (256^3, complex64, the staged half-spectrum form, steps 500..509):
     python -m paper_2609_03922_gb300.profile_step --dims 256 256 256 --warm 500 --steps 10
+The same with the spectrum stored as its half (block map on the half, S1.2):
+    python -m paper_2609_03922_gb300.profile_step --dims 256 256 256 --warm 500 --steps 10 --half-storage 1
 RCD (M components; dx = 0.5):
     python -m paper_2609_03922_gb300.profile_step --model rcd --components 48 --dims 128 128 128 --block 4 4 4
 A batched 2-D plan of several sizes, one launch per pass phase over all of them:
@@ -37,6 +39,8 @@ def main(argv=None):
     ap.add_argument("--half", type=int, default=1, help="1: Hermitian half-spectrum transforms")
     ap.add_argument("--tma", type=int, default=0, help="1: staged update moved by TMA boxes")
     ap.add_argument("--tma-passes", type=int, default=1, help="0: the z inverse copies its tiles by cp.async")
+    ap.add_argument("--half-storage", type=int, default=0,
+                    help="1: the spectrum stored as its half kx = 0 .. N2/2 with the block map on that half")
     ap.add_argument("--precision", choices=["c64", "c128"], default="c64")
     ap.add_argument("--mean", type=float, default=0.1)
     ap.add_argument("--warm", type=int, default=500)
@@ -85,7 +89,7 @@ def main(argv=None):
     with spdba.Plan(dims, tuple(args.block), threshold=args.threshold, reassess=args.reassess, precision=prec,
                     mode=spdba.SPDBA_MODE_ADAPTIVE if args.mode == "adaptive" else spdba.SPDBA_MODE_REGULAR,
                     fuse_update=args.fuse, half_spectrum=args.half, use_graph=0, tma_update=args.tma,
-                    tma_passes=args.tma_passes, **kw) as plan:
+                    tma_passes=args.tma_passes, half_storage=args.half_storage, **kw) as plan:
         if args.predictor:
             m = tuple(d // b for d, b in zip(dims, args.block))
             pred = spdba.Predictor(m, max_batch=1, params=spdba.predictor_init_params(0))   # outlives the plan's steps
