@@ -79,6 +79,8 @@ TOUCHED_BYTES = {
     "fft_z_forward": 38.63e6 + 0.12e6,
     # list-driven update of the half map's non-frozen blocks: 41.67 MB read, 0.02 MB written
     "update_list": 41.67e6 + 0.02e6,
+    # activity scan of the stored half (rows kernel, per-lane screen): 75.52 MB read, 0.56 MB written
+    "assess": 75.52e6 + 0.56e6,
 }
 TOUCHED_NOTE = {
     "fft_fused_nl": "ncu DRAM read + write of one launch at step 505 (cold L2)",
@@ -88,6 +90,8 @@ TOUCHED_NOTE = {
     "fft_z_forward": "ncu DRAM read + write of one launch at step 505 (cold L2)",
     "update_list": "ncu DRAM read + write of one launch at step 505 (cold L2; most writes leave the launch "
                    "in L2)",
+    "assess": "ncu DRAM read + write of one scan at step 510 (the scan launch only; the classification's three "
+              "small launches and the pencil-liveness launch are in the same kind)",
 }
 CONTROL_TARGETS = (0.05, 0.1, 0.2)   # dynamic threshold control targets (S1.3: 5-20 %)
 CONTROL_EVERY = 50                   # control interval (S3.2, S4.2, S5.3)
