@@ -186,3 +186,48 @@ def test_half_storage_where_it_applies():
         spdba.Plan((64, 64, 64), B, half_storage=1, precision=1)           # complex128
     with spdba.Plan((64, 64, 64), B) as p:
         assert p.get_config()["half_storage"] == 0
+
+
+def test_half_storage_threshold_control_lockstep():
+    """Dynamic threshold control (S1.3) with half-spectrum storage: the ratio of
+    non-frozen blocks is counted over the half map's live blocks, so the GPU's
+    coefficient sequence equals the oracle controller's (fed the GPU's states)
+    bit for bit; states through the oracle's half-map classifier, the field
+    against the oracle's half form run with the GPU's states."""
+    dims = (64, 64, 64)
+    steps, R = 240, 5
+    kw = dict(target_ratio=0.2, control_every=20, control_eta=0.05)
+    c0 = _f32(W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 706))
+    cfg = O.CHConfig(dims, B, threshold=1e-6, reassess=R, **kw)
+    masks, spectra, coef = {}, {}, {}
+    plan = _plan(dims, threshold=1e-6, reassess=R, **kw)
+    plan.set_field(c0)
+    for s in range(steps):
+        if s % R == 0:
+            spectra[s] = plan.get_spectrum()
+            plan.step(1)
+            masks[s] = plan.get_mask()
+            coef[s] = plan.get_stats()["threshold"]
+        else:
+            plan.step(1)
+    field = plan.get_field()
+    stats = plan.get_stats()
+    plan.close()
+    nb = int(np.prod(O.half_block_counts(dims, B)))
+    assert stats["nblocks"] == nb
+    ctl = O.ThresholdController(cfg, nb)
+    cur = None
+    for s in range(steps):
+        thr = ctl.begin_step(s)
+        if s in masks:
+            assert coef[s] == thr, "step %d: GPU coefficient %.17g, oracle %.17g" % (s, coef[s], thr)
+            _, tau, meas = O.assess_states_half(spectra[s].astype(np.complex128), cfg, exclude_dc=True,
+                                                threshold=thr)
+            ok, nties = states_within_tie_band(masks[s], meas, tau, cfg, classifier=O.classify_half)
+            assert ok, "step %d: GPU states differ from the oracle's (%d tie-band blocks)" % (s, nties)
+            cur = masks[s]
+        ctl.end_step(s, cur)
+    assert stats["controls"] == len(ctl.log) == steps // 20 - 1
+    assert stats["threshold"] == ctl.threshold and ctl.threshold > 1e-6
+    ref_h, _ = O.run_ch_half(c0.astype(np.float64), cfg, steps, on_assess=lambda n, h, st, tau: masks.get(n))
+    assert O.rel_l2(field, O.ch_real_field_half(ref_h, dims)) <= 2e-5
