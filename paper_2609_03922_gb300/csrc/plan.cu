@@ -1847,6 +1847,14 @@ template <typename T> static spdba_status snap_take(spdba_plan* p, Group<T>& r, 
         sn.bufs.push_back({r.pair_list, sizeof(int) * (size_t)r.pair_list_n});
         sn.bufs.push_back({r.pair_count, sizeof(int)});
     }
+    // the forward passes' liveness follows the states in force: a tuning started
+    // between reassessments resumes with the states of the snapshot, so their
+    // liveness is restored with them
+    if (r.col_live) sn.bufs.push_back({r.col_live, (size_t)r.h_fwd_y.p.I});
+    if (r.hs_zlive) {
+        sn.bufs.push_back({r.hs_zlive, (size_t)(r.g.n[1] * r.g.n[2])});
+        sn.bufs.push_back({r.hs_xlive, (size_t)r.g.n[2]});
+    }
     for (auto& b : sn.bufs) {
         void* q = nullptr;
         cudaError_t e = dev_alloc(&q, b.second);

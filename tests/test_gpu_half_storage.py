@@ -231,3 +231,46 @@ def test_half_storage_threshold_control_lockstep():
     assert stats["threshold"] == ctl.threshold and ctl.threshold > 1e-6
     ref_h, _ = O.run_ch_half(c0.astype(np.float64), cfg, steps, on_assess=lambda n, h, st, tau: masks.get(n))
     assert O.rel_l2(field, O.ch_real_field_half(ref_h, dims)) <= 2e-5
+
+
+@pytest.mark.parametrize("hs", [1, 0])
+def test_autotune_between_reassessments_keeps_results(hs):
+    """Tuned at step 17 with R = 5 (between reassessments, blocks frozen): the
+    trial steps pass a reassessment, so the forward passes' pencil and column
+    liveness must come back with the snapshot's states.  The next steps equal an
+    untuned plan's bit for bit (every candidate of these forms gives the same
+    values: fused, staged, TMA staged, graph replay, direct launches)."""
+    import torch
+    from paper_2609_03922_gb300 import spdba
+    dims = (128, 128, 128)
+    c0 = _f32(W.ch_initial_condition(dims, mean=0.1, seed=W.BASE_SEED + 707))
+    kw = dict(threshold=1e-2, reassess=5, precision=0)
+    if hs:
+        kw["half_storage"] = 1
+    else:
+        kw["half_spectrum"] = 1
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        plan = spdba.Plan(dims, B, **kw)
+        plan.set_field(c0)
+        plan.step(17)
+        before = (plan.get_spectrum(), plan.get_mask())
+        rep = plan.autotune(4)
+        after = (plan.get_spectrum(), plan.get_mask())
+        plan.step(13)
+        tuned = (plan.get_spectrum(), plan.get_mask())
+        chosen = rep["candidates"][rep["chosen"]]
+        plan.close()
+        ref = spdba.Plan(dims, B, **kw)
+        ref.set_field(c0)
+        ref.step(30)
+        untuned = (ref.get_spectrum(), ref.get_mask())
+        ref.close()
+    side.synchronize()
+    assert np.any(before[1] == O.STATE_FROZEN)
+    assert np.array_equal(after[0], before[0]) and np.array_equal(after[1], before[1])
+    if hs or chosen["half_spectrum"] == 1:
+        assert np.array_equal(tuned[0], untuned[0]), chosen
+        assert np.array_equal(tuned[1], untuned[1]), chosen
+    else:
+        assert O.rel_l2(tuned[0], untuned[0]) <= 1e-5, chosen
