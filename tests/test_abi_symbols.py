@@ -54,3 +54,39 @@ def test_host_only_calls(lib):
     assert lib.spdba_plan_create(ctypes.byref(p), 2, dims, blk, 1e-6, 10, ctypes.byref(o)) == spdba.SPDBA_ERR_UNSUPPORTED
     assert b"not 2^a 3^b" in lib.spdba_last_error()
     assert lib.spdba_step(None, 1) == spdba.SPDBA_ERR_ARG
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the header's layout: every
+    field's offset and each structure's size, as the C compiler lays them out
+    (a field appended on one side only would shift the rest silently)."""
+    import shutil
+    import subprocess
+    from paper_2609_03922_gb300 import spdba
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [spdba.spdba_options, spdba.spdba_stats, spdba.spdba_tune_report, spdba.spdba_kernel_time]
+    lines = ['#include <stdio.h>', '#include "spdba.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in st._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "size")] == ctypes_sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, "%s.%s" % (name, f)
+
+
+def ctypes_sizeof(st):
+    import ctypes
+    return ctypes.sizeof(st)
