@@ -254,23 +254,24 @@ __global__ void __launch_bounds__(NT, L == 384 ? 1 : 512 / NT) fft_nl_half_kerne
         transform_pair_in<T, L, PP, NT, +1, -1, LY>(tb, a.tw, in, mid, so);
         __syncthreads();
         // separate the two rows' half spectra (padding entries zero), straight
-        // to the output rows (consecutive threads, consecutive entries)
+        // to the output rows: one loop over all (pair, entry) items, so that
+        // every trip keeps all threads busy (consecutive threads, consecutive
+        // entries of a row)
         {
             C* dst = a.out + q0 * NHP;
-#pragma unroll
-            for (int pp = 0; pp < PP; ++pp) {
-                for (int k = threadIdx.x; k < NHP; k += NT) {
-                    C g1 = mk<C>((T)0, (T)0), g2 = g1;
-                    if (k <= M) {
-                        const C w = tb[LY::idx(pp, k)];
-                        C v = tb[LY::idx(pp, k == 0 ? 0 : L - k)];
-                        v.y = -v.y;                                               // conj W[-k]
-                        g1 = mk<C>((T)0.5 * (w.x + v.x), (T)0.5 * (w.y + v.y));
-                        g2 = mk<C>((T)0.5 * (w.y - v.y), (T)-0.5 * (w.x - v.x));  // (w - v) / (2i)
-                    }
-                    dst[(2 * pp) * NHP + k] = g1;
-                    dst[(2 * pp + 1) * NHP + k] = g2;
+            for (int it = threadIdx.x; it < PP * NHP; it += NT) {
+                const int pp = (int)a.hg.fd_NHP.div((uint32_t)it);
+                const int k = it - pp * NHP;
+                C g1 = mk<C>((T)0, (T)0), g2 = g1;
+                if (k <= M) {
+                    const C w = tb[LY::idx(pp, k)];
+                    C v = tb[LY::idx(pp, k == 0 ? 0 : L - k)];
+                    v.y = -v.y;                                               // conj W[-k]
+                    g1 = mk<C>((T)0.5 * (w.x + v.x), (T)0.5 * (w.y + v.y));
+                    g2 = mk<C>((T)0.5 * (w.y - v.y), (T)-0.5 * (w.x - v.x));  // (w - v) / (2i)
                 }
+                dst[(2 * pp) * NHP + k] = g1;
+                dst[(2 * pp + 1) * NHP + k] = g2;
             }
         }
         if (a.mass != nullptr) {
